@@ -1,0 +1,188 @@
+/*
+ * rsf.h -- C ABI of the GB300 recursive skeletonization factorization (RSF)
+ * library for Gaussian-process log-likelihoods and scores on 2-D points.
+ *
+ * Method: Minden, Damle, Ho, Ying, "Fast spatial Gaussian process maximum
+ * likelihood estimation via skeletonization factorizations".
+ *   - model and objective: Sec. 1, Eqs. (normaldist), (loglikelihood),
+ *     (gradient);
+ *   - factorization F ~ Sigma: Sec. 2, Def. (ID), Sec. 2.1 block equations,
+ *     Eq. (rskelf), Sec. 2.3.1 Eq. (proxyid) (modified proxy trick);
+ *   - apply / solve / square root / log-determinant: Sec. 2.3.2, Table 1;
+ *   - trace by weak peeling: Sec. 3, Eq. (lowrankapprox);
+ *   - log-likelihood and score: Sec. 4, Algorithm 1.
+ *
+ * Conventions shared by every entry point:
+ *   - points: DEVICE pointer, n x 2 row-major fp64 (x0 y0 x1 y1 ...),
+ *     caller-owned, read only during the call;
+ *   - vectors (z, B, alpha): DEVICE pointers in the caller's original point
+ *     order; B is column-major n x nrhs with leading dimension ldb >= n;
+ *   - theta = {l, s2, nug}: host array of 3 doubles; the covariance is
+ *     K(x_i, x_j) = s2 * k(|x_i - x_j| / l) + nug * delta_ij (nugget on equal
+ *     indices);
+ *   - stream: a cudaStream_t passed as void* (NULL = legacy default stream);
+ *     all work of a handle runs on the stream it was built with;
+ *   - every call returns an rsf_status and never aborts, traps or prints.
+ *     On error the outputs are left unchanged, handles stay valid (or NULL),
+ *     and rsf_last_error() returns a message (thread-local, valid until the
+ *     next call on that thread).  Device-side failures (non-positive pivot,
+ *     NaN/Inf) are recorded in a device status word and reported by the
+ *     call that synchronises next.
+ *   - memory: handles own all device memory they allocate (stream-ordered
+ *     cudaMallocAsync on the handle's stream) and release it in
+ *     rsf_destroy / rsf_tree_destroy.
+ */
+#ifndef RSF_H
+#define RSF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RSF_OK = 0,
+  RSF_EINVAL = 1,    /* bad argument or unsupported combination */
+  RSF_ENOMEM = 2,    /* device allocation failed */
+  RSF_ENOTPD = 3,    /* Cholesky of a diagonal block met a non-positive pivot */
+  RSF_ENUMERIC = 4,  /* NaN / Inf produced */
+  RSF_ETIMEOUT = 5,  /* a bounded device wait gave up */
+  RSF_ECUDA = 6      /* a CUDA runtime call failed */
+} rsf_status;
+
+/* Kernel families (Sec. 1 Eqs. (matern), (rationalquadratic); Sec. 5.5
+ * Eq. (diffkernels)). */
+typedef enum {
+  RSF_MATERN12 = 0,  /* s2 exp(-r/l) */
+  RSF_MATERN32 = 1,  /* s2 (1 + a) exp(-a), a = sqrt(3) r / l */
+  RSF_MATERN52 = 2,  /* s2 (1 + a + a^2/3) exp(-a), a = sqrt(5) r / l */
+  RSF_MATERN1 = 3,   /* s2 x K_1(x), x = sqrt(2) r / l (not built yet: EINVAL) */
+  RSF_RQ = 4         /* s2 (1 + r^2 / (2 alpha l^2))^-alpha */
+} rsf_family;
+
+/* Matrix selector: Sigma or one of its theta-derivatives (Sec. 1, below
+ * Eq. (gradient)). */
+typedef enum { RSF_SIGMA = 0, RSF_D_L = 1, RSF_D_S2 = 2, RSF_D_NUG = 3 } rsf_which;
+
+/* Operations of rsf_solve (Sec. 2.3.2): F^-1, F, F^1/2, (F^1/2)^T, F^-1/2,
+ * (F^-1/2)^T.  Only RSF_OP_APPLY is defined for derivative factorizations. */
+typedef enum {
+  RSF_OP_INV = 0, RSF_OP_APPLY = 1, RSF_OP_SQRT = 2, RSF_OP_SQRT_T = 3,
+  RSF_OP_INV_SQRT = 4, RSF_OP_INV_SQRT_T = 5
+} rsf_op;
+
+typedef struct {
+  int family;    /* rsf_family */
+  double alpha;  /* RQ shape parameter (ignored otherwise) */
+} rsf_kernel;
+
+/* Tuning knobs.  n_occ and n_prox default to the paper's 64 and 256 (Sec. 5);
+ * the near-field radius and proxy annulus (in units of the box side) are
+ * this library's reading of Sec. 2.3.1, which gives no radii. */
+typedef struct {
+  int n_occ;        /* max points per leaf box (64) */
+  int n_prox;       /* proxy points per box (256) */
+  int n_rings;      /* rings of the proxy annulus (8); n_prox % n_rings == 0 */
+  double r_near;    /* near field: active DOFs within r_near * side (1.0) */
+  double r_in;      /* proxy annulus inner radius / side (1.0) */
+  double r_out;     /* proxy annulus outer radius / side (2.0) */
+  int oversample;   /* peeling oversampling c (10), Sec. 3.1 */
+  int q0;           /* peeling: minimum initial sample count at level 1 (64) */
+  uint64_t seed;    /* Philox4x32-10 key of the peeling test matrices (0) */
+} rsf_opts;
+
+typedef struct rsf_tree_s* rsf_tree;
+typedef struct rsf_handle_s* rsf_handle;
+
+/* Summary of a factorization, for reporting. */
+typedef struct {
+  int64_t n;
+  int levels;            /* L + 1 (levels 0..L) */
+  int64_t boxes;         /* skeletonized boxes plus the root */
+  int root_size;         /* DOFs left in the root block */
+  int max_rank;          /* largest skeleton |S| */
+  int max_active;        /* largest |I| */
+  int64_t factor_entries;/* entries of T, E and the diagonal blocks */
+  double flops;          /* algorithmic fp64 flops of the factorization */
+  double kernel_evals;   /* kernel evaluations during the factorization */
+} rsf_info_t;
+
+/* Fills *o with the defaults listed above. */
+void rsf_opts_default(rsf_opts* o);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* rsf_last_error(void);
+
+/* Quadtree of Sec. 2.1 / Remark (tree) over `points` (device, n x 2).
+ * Split while a box holds more than opts->n_occ points; children in Morton
+ * order.  The tree keeps its own copy of the points (tree order) and may be
+ * reused by rsf_build_on_tree for any kernel and theta.  opts may be NULL. */
+rsf_status rsf_tree_build(const double* points, int64_t n, const rsf_opts* opts,
+                          void* stream, rsf_tree* out);
+void rsf_tree_destroy(rsf_tree t);
+
+/* RSF of Sigma (which = RSF_SIGMA, Cholesky of the diagonal blocks) or of a
+ * derivative matrix dSigma/dtheta_k (which = RSF_D_L / RSF_D_S2; diagonal
+ * blocks kept for application, Remark (indefinite)).  tol is the relative ID
+ * tolerance (Def. ID).  The handle owns all factor memory. */
+rsf_status rsf_build(const double* points, int64_t n, const rsf_kernel* kernel,
+                     const double* theta, int which, double tol,
+                     const rsf_opts* opts, void* stream, rsf_handle* out);
+rsf_status rsf_build_on_tree(rsf_tree tree, const rsf_kernel* kernel,
+                             const double* theta, int which, double tol,
+                             const rsf_opts* opts, rsf_handle* out);
+
+/* log|F| = 2 log|C| (Sec. 2.3.2) to *out (host).  Synchronises the stream.
+ * RSF_EINVAL for derivative factorizations. */
+rsf_status rsf_logdet(rsf_handle h, double* out);
+
+/* In place B <- op(F) B for B (device, column-major n x nrhs, ld ldb >= n,
+ * original point order).  Stream-ordered (does not synchronise). */
+rsf_status rsf_solve(rsf_handle h, double* B, int64_t ldb, int nrhs, int op);
+
+/* Trace by weak peeling (Sec. 3) to *trace (host): Tr(F^-1) when Fk is NULL,
+ * else Tr((F^-1 Fk + Fk F^-1)/2) (Algorithm 1).  tol_peel is the relative
+ * cut-off of the sibling-block ranks.  Synchronises. */
+rsf_status rsf_peel_trace(rsf_handle F, rsf_handle Fk, double tol_peel,
+                          const rsf_opts* opts, double* trace);
+
+/* Log-likelihood from a factorization of Sigma (Algorithm 1, first part):
+ * alpha = F^-1 z, quad = z^T alpha, loglik = -quad/2 - log|F|/2 - n/2 log 2pi.
+ * z (device, n), alpha_out (device, n, or NULL), loglik/quad host (quad may be
+ * NULL).  Synchronises. */
+rsf_status gp_loglik(rsf_handle F, const double* z, double* alpha_out,
+                     double* loglik, double* quad);
+
+/* Score (Algorithm 1, loop over theta) given F ~ Sigma and alpha = F^-1 z:
+ * builds F_l ~ dSigma/dl on F's tree, peels Tr(F^-1) and
+ * Tr((F^-1 F_l + F_l F^-1)/2), and uses Sigma = s2 Sigma_s2 + nug I for the
+ * variance component.  score (host, 3) = (g_l, g_s2, g_nug); terms (host, 6,
+ * or NULL) = (quad_l, quad_s2, quad_nug, trace_l, trace_s2, trace_nug). */
+rsf_status gp_score(rsf_handle F, const double* alpha, double tol_fact,
+                    double tol_peel, const rsf_opts* opts, double* score,
+                    double* terms);
+
+/* Algorithm 1 end to end: tree, F, loglik and (when score != NULL) the
+ * score.  points, z device; loglik, score (3), terms (6, or NULL) host. */
+rsf_status gp_loglik_and_score(const double* points, const double* z, int64_t n,
+                               const rsf_kernel* kernel, const double* theta,
+                               double tol_fact, double tol_peel,
+                               const rsf_opts* opts, void* stream,
+                               double* loglik, double* score, double* terms);
+
+/* Factorization summary (host struct). */
+rsf_status rsf_get_info(rsf_handle h, rsf_info_t* info);
+
+/* Number of this library's kernel launches since the counter was last reset
+ * (host-side count of launches issued). */
+int64_t rsf_launch_count(int reset);
+
+/* Frees a handle and all its device memory.  Safe on NULL. */
+void rsf_destroy(rsf_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSF_H */

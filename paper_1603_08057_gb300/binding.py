@@ -1,0 +1,258 @@
+"""Thin ctypes binding of the C-ABI library ``librsf.so`` (include/rsf.h).
+
+Argument marshalling only: every step of the computation runs in the
+library's CUDA kernels.  PyTorch supplies device memory (float64 CUDA tensors)
+and the current CUDA stream.  There is no CPU fallback: if the library is not
+built, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(HERE, "librsf.so")
+
+# rsf_family, rsf_which, rsf_op (include/rsf.h)
+MATERN12, MATERN32, MATERN52, MATERN1, RQ = 0, 1, 2, 3, 4
+SIGMA, D_L, D_S2, D_NUG = 0, 1, 2, 3
+OP_INV, OP_APPLY, OP_SQRT, OP_SQRT_T, OP_INV_SQRT, OP_INV_SQRT_T = range(6)
+STATUS = {0: "RSF_OK", 1: "RSF_EINVAL", 2: "RSF_ENOMEM", 3: "RSF_ENOTPD",
+          4: "RSF_ENUMERIC", 5: "RSF_ETIMEOUT", 6: "RSF_ECUDA"}
+
+EXPORTS = ["rsf_opts_default", "rsf_last_error", "rsf_tree_build", "rsf_tree_destroy",
+           "rsf_build", "rsf_build_on_tree", "rsf_logdet", "rsf_solve", "rsf_peel_trace",
+           "gp_loglik", "gp_score", "gp_loglik_and_score", "rsf_get_info",
+           "rsf_launch_count", "rsf_destroy"]
+
+
+class RsfKernel(C.Structure):
+    _fields_ = [("family", C.c_int), ("alpha", C.c_double)]
+
+
+class RsfOpts(C.Structure):
+    _fields_ = [("n_occ", C.c_int), ("n_prox", C.c_int), ("n_rings", C.c_int),
+                ("r_near", C.c_double), ("r_in", C.c_double), ("r_out", C.c_double),
+                ("oversample", C.c_int), ("q0", C.c_int), ("seed", C.c_uint64)]
+
+
+class RsfInfo(C.Structure):
+    _fields_ = [("n", C.c_int64), ("levels", C.c_int), ("boxes", C.c_int64),
+                ("root_size", C.c_int), ("max_rank", C.c_int), ("max_active", C.c_int),
+                ("factor_entries", C.c_int64), ("flops", C.c_double),
+                ("kernel_evals", C.c_double)]
+
+
+class RsfError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Loads the library (built in-tree by ``build.build()``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIBPATH):
+            raise RuntimeError(f"{LIBPATH} is missing: run paper_1603_08057_gb300.build.build() first")
+        L = C.CDLL(LIBPATH)
+        vp, dp, i64, ip = C.c_void_p, C.POINTER(C.c_double), C.c_int64, C.c_int
+        L.rsf_last_error.restype = C.c_char_p
+        L.rsf_opts_default.argtypes = [C.POINTER(RsfOpts)]
+        L.rsf_opts_default.restype = None
+        L.rsf_tree_build.argtypes = [vp, i64, C.POINTER(RsfOpts), vp, C.POINTER(vp)]
+        L.rsf_tree_destroy.argtypes = [vp]
+        L.rsf_tree_destroy.restype = None
+        L.rsf_build.argtypes = [vp, i64, C.POINTER(RsfKernel), dp, ip, C.c_double,
+                                C.POINTER(RsfOpts), vp, C.POINTER(vp)]
+        L.rsf_build_on_tree.argtypes = [vp, C.POINTER(RsfKernel), dp, ip, C.c_double,
+                                        C.POINTER(RsfOpts), C.POINTER(vp)]
+        L.rsf_logdet.argtypes = [vp, dp]
+        L.rsf_solve.argtypes = [vp, vp, i64, ip, ip]
+        L.rsf_peel_trace.argtypes = [vp, vp, C.c_double, C.POINTER(RsfOpts), dp]
+        L.gp_loglik.argtypes = [vp, vp, vp, dp, dp]
+        L.gp_score.argtypes = [vp, vp, C.c_double, C.c_double, C.POINTER(RsfOpts), dp, dp]
+        L.gp_loglik_and_score.argtypes = [vp, vp, i64, C.POINTER(RsfKernel), dp, C.c_double,
+                                          C.c_double, C.POINTER(RsfOpts), vp, dp, dp, dp]
+        L.rsf_get_info.argtypes = [vp, C.POINTER(RsfInfo)]
+        L.rsf_launch_count.argtypes = [ip]
+        L.rsf_launch_count.restype = C.c_int64
+        L.rsf_destroy.argtypes = [vp]
+        L.rsf_destroy.restype = None
+        for name in EXPORTS:
+            if name not in ("rsf_opts_default", "rsf_last_error", "rsf_tree_destroy",
+                            "rsf_launch_count", "rsf_destroy"):
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(code):
+    if code != 0:
+        raise RsfError(code, lib().rsf_last_error().decode())
+
+
+def opts(**kw) -> RsfOpts:
+    o = RsfOpts()
+    lib().rsf_opts_default(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _dev(t: torch.Tensor, shape=None) -> torch.Tensor:
+    if not (t.is_cuda and t.dtype == torch.float64):
+        raise TypeError("expected a float64 CUDA tensor")
+    t = t.contiguous()
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"expected shape {shape}, got {tuple(t.shape)}")
+    return t
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _theta(theta):
+    th = [float(v) for v in (theta.tolist() if isinstance(theta, torch.Tensor) else theta)]
+    return (C.c_double * 3)(*th)
+
+
+def launch_count(reset=False) -> int:
+    return int(lib().rsf_launch_count(1 if reset else 0))
+
+
+class Tree:
+    """rsf_tree_build: quadtree over a (n, 2) float64 CUDA tensor."""
+
+    def __init__(self, points: torch.Tensor, o: RsfOpts | None = None):
+        self.points = _dev(points)
+        self.n = self.points.shape[0]
+        self.h = C.c_void_p()
+        _check(lib().rsf_tree_build(self.points.data_ptr(), self.n, C.byref(o) if o else None,
+                                    _stream(), C.byref(self.h)))
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.rsf_tree_destroy(self.h)
+            self.h = None
+
+
+class Factorization:
+    """rsf_build / rsf_build_on_tree: RSF of Sigma (which=SIGMA) or of
+    dSigma/dtheta (which=D_L, D_S2)."""
+
+    def __init__(self, points_or_tree, family, theta, which=SIGMA, tol=1e-9, alpha=0.0,
+                 o: RsfOpts | None = None):
+        self.kernel = RsfKernel(family, alpha)
+        self.h = C.c_void_p()
+        th = _theta(theta)
+        if isinstance(points_or_tree, Tree):
+            self.tree = points_or_tree
+            self.n = self.tree.n
+            _check(lib().rsf_build_on_tree(self.tree.h, C.byref(self.kernel), th, which, tol,
+                                           C.byref(o) if o else None, C.byref(self.h)))
+        else:
+            pts = _dev(points_or_tree)
+            self.n = pts.shape[0]
+            self.tree = None
+            _check(lib().rsf_build(pts.data_ptr(), self.n, C.byref(self.kernel), th, which, tol,
+                                   C.byref(o) if o else None, _stream(), C.byref(self.h)))
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.rsf_destroy(self.h)
+            self.h = None
+
+    def logdet(self) -> float:
+        v = C.c_double()
+        _check(lib().rsf_logdet(self.h, C.byref(v)))
+        return v.value
+
+    def solve(self, B: torch.Tensor, op=OP_INV) -> torch.Tensor:
+        """op(F) B for B (n,) or (n, nrhs); returns a new tensor."""
+        vec = B.dim() == 1
+        X = _dev(B).reshape(self.n, -1)
+        # column-major n x nrhs = transpose of a row-major nrhs x n array
+        Xc = X.t().contiguous()
+        _check(lib().rsf_solve(self.h, Xc.data_ptr(), self.n, Xc.shape[0], op))
+        out = Xc.t()
+        return out.reshape(-1) if vec else out.contiguous()
+
+    def info(self) -> dict:
+        i = RsfInfo()
+        _check(lib().rsf_get_info(self.h, C.byref(i)))
+        return {k: getattr(i, k) for k, _ in RsfInfo._fields_}
+
+    def loglik(self, z: torch.Tensor):
+        """gp_loglik: returns (loglik, quad, alpha = F^-1 z)."""
+        z = _dev(z, (self.n,))
+        a = torch.empty_like(z)
+        ll, q = C.c_double(), C.c_double()
+        _check(lib().gp_loglik(self.h, z.data_ptr(), a.data_ptr(), C.byref(ll), C.byref(q)))
+        return ll.value, q.value, a
+
+    def score(self, alpha: torch.Tensor, tol_fact=1e-9, tol_peel=1e-6, o: RsfOpts | None = None):
+        """gp_score: returns (score (3,), terms (6,)) as float64 CPU tensors."""
+        a = _dev(alpha, (self.n,))
+        g = (C.c_double * 3)()
+        t = (C.c_double * 6)()
+        _check(lib().gp_score(self.h, a.data_ptr(), tol_fact, tol_peel, C.byref(o) if o else None, g, t))
+        return torch.tensor(list(g), dtype=torch.float64), torch.tensor(list(t), dtype=torch.float64)
+
+
+def peel_trace(F: Factorization, Fk: Factorization | None, tol_peel=1e-6, o: RsfOpts | None = None) -> float:
+    v = C.c_double()
+    _check(lib().rsf_peel_trace(F.h, Fk.h if Fk is not None else None, tol_peel,
+                                C.byref(o) if o else None, C.byref(v)))
+    return v.value
+
+
+def loglik_and_score(points, z, family, theta, tol_fact=1e-9, tol_peel=1e-6, alpha=0.0,
+                     o: RsfOpts | None = None, want_score=True):
+    """gp_loglik_and_score: Algorithm 1 end to end.  Returns (loglik, score,
+    terms); score and terms are None when want_score is False."""
+    pts = _dev(points)
+    n = pts.shape[0]
+    zz = _dev(z, (n,))
+    k = RsfKernel(family, alpha)
+    ll = C.c_double()
+    g = (C.c_double * 3)()
+    t = (C.c_double * 6)()
+    _check(lib().gp_loglik_and_score(pts.data_ptr(), zz.data_ptr(), n, C.byref(k), _theta(theta),
+                                     tol_fact, tol_peel, C.byref(o) if o else None, _stream(),
+                                     C.byref(ll), g if want_score else None, t if want_score else None))
+    if not want_score:
+        return ll.value, None, None
+    return ll.value, torch.tensor(list(g), dtype=torch.float64), torch.tensor(list(t), dtype=torch.float64)
+
+
+class GPLogLikelihood(torch.autograd.Function):
+    """Differentiable Gaussian-process log-likelihood in theta = (l, s2, nug).
+
+    forward: RSF of Sigma, l = -z^T F^-1 z / 2 - log|F| / 2 - n/2 log 2pi;
+    backward: the score from the peeled traces and a second solve
+    (Algorithm 1), times the incoming gradient.  theta is a float64 CPU
+    tensor; points and z are float64 CUDA tensors (constants)."""
+
+    @staticmethod
+    def forward(ctx, theta, points, z, family, alpha, tol_fact, tol_peel, o):
+        F = Factorization(points, family, theta.detach().cpu(), SIGMA, tol_fact, alpha, o)
+        ll, _, a = F.loglik(z)
+        ctx.F, ctx.a, ctx.tols, ctx.o = F, a, (tol_fact, tol_peel), o
+        return torch.tensor(ll, dtype=torch.float64)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        g, _ = ctx.F.score(ctx.a, ctx.tols[0], ctx.tols[1], ctx.o)
+        ctx.F = None
+        return grad_out * g, None, None, None, None, None, None, None
+
+
+def gp_loglik(theta, points, z, family=MATERN32, alpha=0.0, tol_fact=1e-9, tol_peel=1e-6, o=None):
+    return GPLogLikelihood.apply(theta, points, z, family, alpha, tol_fact, tol_peel, o)

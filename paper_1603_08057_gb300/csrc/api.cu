@@ -1,0 +1,378 @@
+// C ABI (include/rsf.h): argument checks, handle management, the
+// log-likelihood (Algorithm 1, first part) and the score (Algorithm 1, loop
+// over theta) on top of the factorization, solve and peeling drivers.
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <stdexcept>
+
+#include "internal.cuh"
+
+namespace rsf {
+
+int64_t g_launches = 0;
+
+namespace {
+thread_local std::string g_err;
+
+struct Exception {
+  rsf_status code;
+  std::string msg;
+};
+}  // namespace
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+void fail(rsf_status code, const std::string& msg) { throw Exception{code, msg}; }
+
+// Trees handed out through the C ABI; handles share ownership.
+static std::mutex g_tree_mu;
+static std::map<rsf_tree_s*, std::shared_ptr<rsf_tree_s>> g_trees;
+
+// z (user order, device, n x q column-major ld) <-> tree-order row-major.
+__global__ void to_tree_kernel(const double* __restrict__ B, int64_t ldb, int q, const int* __restrict__ perm,
+                               int64_t n, double* __restrict__ X) {
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n * q) return;
+  int64_t p = g / q;
+  int c = (int)(g % q);
+  X[g] = B[(int64_t)perm[p] + (int64_t)c * ldb];
+}
+__global__ void from_tree_kernel(const double* __restrict__ X, int64_t n, int q, const int* __restrict__ perm,
+                                 double* __restrict__ B, int64_t ldb) {
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n * q) return;
+  int64_t p = g / q;
+  int c = (int)(g % q);
+  B[(int64_t)perm[p] + (int64_t)c * ldb] = X[g];
+}
+
+// Scalars slots
+enum { S_QUAD = 0, S_LOGDET, S_LOGLIK, S_AA, S_QL, S_QF, S_TNUG, S_TL, S_G0, S_G1, S_G2,
+       S_T0, S_T1, S_T2, S_T3, S_T4, S_T5, S_NSLOTS };
+
+// Eq. (loglikelihood): l = -quad/2 - log|F|/2 - n/2 log(2 pi)
+__global__ void loglik_kernel(double* sc, int64_t n) {
+  if (threadIdx.x == 0 && blockIdx.x == 0)
+    sc[S_LOGLIK] = -0.5 * sc[S_QUAD] - 0.5 * sc[S_LOGDET] - 0.5 * (double)n * log(2.0 * 3.141592653589793);
+}
+
+// Eq. (gradient) with Sigma = s2 Sigma_s2 + nug I:
+//   g_l   = (a^T F_l a - Tr_l)/2
+//   g_s2  = ((a^T F a - nug a^T a) - (n - nug Tr(F^-1)))/(2 s2)
+//   g_nug = (a^T a - Tr(F^-1))/2
+__global__ void score_kernel(double* sc, int64_t n, double s2, double nug) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double ql = sc[S_QL], qs = (sc[S_QF] - nug * sc[S_AA]) / s2, qn = sc[S_AA];
+  double tl = sc[S_TL], ts = ((double)n - nug * sc[S_TNUG]) / s2, tn = sc[S_TNUG];
+  sc[S_T0] = ql; sc[S_T1] = qs; sc[S_T2] = qn;
+  sc[S_T3] = tl; sc[S_T4] = ts; sc[S_T5] = tn;
+  sc[S_G0] = 0.5 * ql - 0.5 * tl;
+  sc[S_G1] = 0.5 * qs - 0.5 * ts;
+  sc[S_G2] = 0.5 * qn - 0.5 * tn;
+}
+
+// log|F| = sum of the per-box parts (fixed order)
+__global__ void sum_logdet_kernel(const double* __restrict__ parts, int n, double* __restrict__ out) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) s += parts[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+static rsf_opts resolve_opts(const rsf_opts* o) {
+  rsf_opts r;
+  rsf_opts_default(&r);
+  if (o) r = *o;
+  return r;
+}
+
+static void check_kernel(const rsf_kernel* k, const double* theta) {
+  RSF_CHECK(k != nullptr && theta != nullptr, RSF_EINVAL, "kernel and theta must not be NULL");
+  RSF_CHECK(k->family == RSF_MATERN12 || k->family == RSF_MATERN32 || k->family == RSF_MATERN52 ||
+                k->family == RSF_RQ,
+            RSF_EINVAL, "unsupported kernel family");
+  RSF_CHECK(k->family != RSF_RQ || k->alpha > 0.0, RSF_EINVAL, "RQ needs alpha > 0");
+  RSF_CHECK(theta[0] > 0.0 && theta[1] > 0.0 && theta[2] >= 0.0, RSF_EINVAL, "theta must satisfy l > 0, s2 > 0, nug >= 0");
+}
+
+static rsf_handle_s* make_handle(std::shared_ptr<rsf_tree_s> tree, const rsf_kernel* kernel, const double* theta,
+                                 int which, double tol, const rsf_opts& o) {
+  check_kernel(kernel, theta);
+  RSF_CHECK(which >= RSF_SIGMA && which <= RSF_D_S2, RSF_EINVAL, "which must be SIGMA, D_L or D_S2");
+  RSF_CHECK(tol > 0.0 && tol < 1.0, RSF_EINVAL, "tol must be in (0, 1)");
+  auto h = std::make_unique<rsf_handle_s>();
+  h->tree = tree;
+  h->tree_raw = tree.get();
+  h->opts = o;
+  h->tol = tol;
+  h->stream = tree->t.stream;
+  h->spd = (which == RSF_SIGMA);
+  h->kp.family = kernel->family;
+  h->kp.alpha = kernel->alpha;
+  h->kp.l = theta[0];
+  h->kp.s2 = theta[1];
+  h->kp.nug = theta[2];
+  h->kp.which = which;
+  factorize(h.get());
+  check_status(h.get());
+  return h.release();
+}
+
+}  // namespace rsf
+
+using namespace rsf;
+
+#define API_BEGIN try {
+#define API_END                                     \
+  }                                                 \
+  catch (const rsf::Exception& e) {                 \
+    rsf::set_error(e.msg);                          \
+    return e.code;                                  \
+  }                                                 \
+  catch (const std::bad_alloc&) {                   \
+    rsf::set_error("host allocation failed");       \
+    return RSF_ENOMEM;                              \
+  }                                                 \
+  catch (const std::exception& e) {                 \
+    rsf::set_error(e.what());                       \
+    return RSF_EINVAL;                              \
+  }                                                 \
+  rsf::set_error("");                               \
+  return RSF_OK;
+
+extern "C" {
+
+void rsf_opts_default(rsf_opts* o) {
+  if (!o) return;
+  o->n_occ = 64;
+  o->n_prox = 256;
+  o->n_rings = 8;
+  o->r_near = 1.0;
+  o->r_in = 1.0;
+  o->r_out = 2.0;
+  o->oversample = 10;
+  o->q0 = 64;
+  o->seed = 0;
+}
+
+const char* rsf_last_error(void) { return g_err.c_str(); }
+
+rsf_status rsf_tree_build(const double* points, int64_t n, const rsf_opts* opts, void* stream, rsf_tree* out) {
+  API_BEGIN
+  RSF_CHECK(points && out, RSF_EINVAL, "points and out must not be NULL");
+  auto t = build_tree(points, n, resolve_opts(opts), (cudaStream_t)stream);
+  std::lock_guard<std::mutex> lk(g_tree_mu);
+  g_trees[t.get()] = t;
+  *out = t.get();
+  API_END
+}
+
+void rsf_tree_destroy(rsf_tree t) {
+  if (!t) return;
+  std::lock_guard<std::mutex> lk(g_tree_mu);
+  g_trees.erase(t);
+}
+
+rsf_status rsf_build(const double* points, int64_t n, const rsf_kernel* kernel, const double* theta, int which,
+                     double tol, const rsf_opts* opts, void* stream, rsf_handle* out) {
+  API_BEGIN
+  RSF_CHECK(points && out, RSF_EINVAL, "points and out must not be NULL");
+  rsf_opts o = resolve_opts(opts);
+  check_kernel(kernel, theta);
+  auto t = build_tree(points, n, o, (cudaStream_t)stream);
+  *out = make_handle(t, kernel, theta, which, tol, o);
+  API_END
+}
+
+rsf_status rsf_build_on_tree(rsf_tree tree, const rsf_kernel* kernel, const double* theta, int which, double tol,
+                             const rsf_opts* opts, rsf_handle* out) {
+  API_BEGIN
+  RSF_CHECK(tree && out, RSF_EINVAL, "tree and out must not be NULL");
+  std::shared_ptr<rsf_tree_s> t;
+  {
+    std::lock_guard<std::mutex> lk(g_tree_mu);
+    auto it = g_trees.find(tree);
+    RSF_CHECK(it != g_trees.end(), RSF_EINVAL, "unknown tree");
+    t = it->second;
+  }
+  rsf_opts o = resolve_opts(opts);
+  o.n_occ = t->opts.n_occ;
+  *out = make_handle(t, kernel, theta, which, tol, o);
+  API_END
+}
+
+rsf_status rsf_logdet(rsf_handle h, double* out) {
+  API_BEGIN
+  RSF_CHECK(h && out, RSF_EINVAL, "handle and out must not be NULL");
+  RSF_CHECK(h->spd, RSF_EINVAL, "log-determinant of a derivative factorization is not defined here");
+  DBuf d;
+  d.alloc(sizeof(double), h->stream);
+  LAUNCH(sum_logdet_kernel, 1, 256, 0, h->stream, h->logdet_parts.as<double>(), (int)h->nboxes_total, d.as<double>());
+  double v = 0;
+  d2h(&v, d.as<double>(), 1, h->stream);
+  check_status(h);
+  *out = v;
+  API_END
+}
+
+rsf_status rsf_solve(rsf_handle h, double* B, int64_t ldb, int nrhs, int op) {
+  API_BEGIN
+  RSF_CHECK(h && B, RSF_EINVAL, "handle and B must not be NULL");
+  const int64_t n = h->tree_raw->t.n;
+  RSF_CHECK(nrhs >= 1 && ldb >= n, RSF_EINVAL, "need nrhs >= 1 and ldb >= n");
+  RSF_CHECK(op >= RSF_OP_INV && op <= RSF_OP_INV_SQRT_T, RSF_EINVAL, "unknown op");
+  RSF_CHECK(h->spd || op == RSF_OP_APPLY, RSF_EINVAL, "only APPLY is defined for a derivative factorization");
+  cudaStream_t s = h->stream;
+  const int* perm = h->tree_raw->t.perm.as<int>();
+  DBuf X, Y;
+  X.alloc(sizeof(double) * n * nrhs, s);
+  Y.alloc(sizeof(double) * n * nrhs, s);
+  LAUNCH(to_tree_kernel, cdiv(n * nrhs, 256), 256, 0, s, B, ldb, nrhs, perm, n, X.as<double>());
+  solve_rows(h, op, X.as<double>(), Y.as<double>(), nrhs);
+  LAUNCH(from_tree_kernel, cdiv(n * nrhs, 256), 256, 0, s, Y.as<double>(), n, nrhs, perm, B, ldb);
+  API_END
+}
+
+rsf_status rsf_peel_trace(rsf_handle F, rsf_handle Fk, double tol_peel, const rsf_opts* opts, double* trace) {
+  API_BEGIN
+  RSF_CHECK(F && trace, RSF_EINVAL, "F and trace must not be NULL");
+  RSF_CHECK(F->spd, RSF_EINVAL, "F must factor Sigma");
+  RSF_CHECK(!Fk || Fk->tree_raw == F->tree_raw, RSF_EINVAL, "F and Fk must share a tree");
+  RSF_CHECK(tol_peel > 0.0 && tol_peel < 1.0, RSF_EINVAL, "tol_peel must be in (0, 1)");
+  rsf_opts o = resolve_opts(opts);
+  double t = peel_trace(F, Fk, tol_peel, o, nullptr);
+  check_status(F);
+  if (Fk) check_status(Fk);
+  *trace = t;
+  API_END
+}
+
+rsf_status gp_loglik(rsf_handle F, const double* z, double* alpha_out, double* loglik, double* quad) {
+  API_BEGIN
+  RSF_CHECK(F && z && loglik, RSF_EINVAL, "F, z and loglik must not be NULL");
+  RSF_CHECK(F->spd, RSF_EINVAL, "F must factor Sigma");
+  cudaStream_t s = F->stream;
+  const int64_t n = F->tree_raw->t.n;
+  const int* perm = F->tree_raw->t.perm.as<int>();
+  DBuf zt, at, sc;
+  zt.alloc(sizeof(double) * n, s);
+  at.alloc(sizeof(double) * n, s);
+  sc.alloc(sizeof(double) * S_NSLOTS, s);
+  sc.zero();
+  LAUNCH(to_tree_kernel, cdiv(n, 256), 256, 0, s, z, n, 1, perm, n, zt.as<double>());
+  solve_rows(F, RSF_OP_INV, zt.as<double>(), at.as<double>(), 1);
+  dot_into(zt.as<double>(), at.as<double>(), n, sc.as<double>() + S_QUAD, s);
+  LAUNCH(sum_logdet_kernel, 1, 256, 0, s, F->logdet_parts.as<double>(), (int)F->nboxes_total,
+         sc.as<double>() + S_LOGDET);
+  LAUNCH(loglik_kernel, 1, 32, 0, s, sc.as<double>(), n);
+  if (alpha_out) LAUNCH(from_tree_kernel, cdiv(n, 256), 256, 0, s, at.as<double>(), n, 1, perm, alpha_out, n);
+  double h[S_NSLOTS];
+  d2h(h, sc.as<double>(), S_NSLOTS, s);
+  check_status(F);
+  *loglik = h[S_LOGLIK];
+  if (quad) *quad = h[S_QUAD];
+  API_END
+}
+
+rsf_status gp_score(rsf_handle F, const double* alpha, double tol_fact, double tol_peel, const rsf_opts* opts,
+                    double* score, double* terms) {
+  API_BEGIN
+  RSF_CHECK(F && alpha && score, RSF_EINVAL, "F, alpha and score must not be NULL");
+  RSF_CHECK(F->spd, RSF_EINVAL, "F must factor Sigma");
+  RSF_CHECK(tol_peel > 0.0 && tol_peel < 1.0, RSF_EINVAL, "tol_peel must be in (0, 1)");
+  cudaStream_t s = F->stream;
+  const int64_t n = F->tree_raw->t.n;
+  const int* perm = F->tree_raw->t.perm.as<int>();
+  rsf_opts o = resolve_opts(opts);
+  rsf_kernel k{F->kp.family, F->kp.alpha};
+  double theta[3] = {F->kp.l, F->kp.s2, F->kp.nug};
+  std::unique_ptr<rsf_handle_s> Fl(make_handle(F->tree, &k, theta, RSF_D_L, tol_fact, o));
+  DBuf at, ft, sc;
+  at.alloc(sizeof(double) * n, s);
+  ft.alloc(sizeof(double) * n, s);
+  sc.alloc(sizeof(double) * S_NSLOTS, s);
+  sc.zero();
+  LAUNCH(to_tree_kernel, cdiv(n, 256), 256, 0, s, alpha, n, 1, perm, n, at.as<double>());
+  dot_into(at.as<double>(), at.as<double>(), n, sc.as<double>() + S_AA, s);
+  solve_rows(Fl.get(), RSF_OP_APPLY, at.as<double>(), ft.as<double>(), 1);
+  dot_into(at.as<double>(), ft.as<double>(), n, sc.as<double>() + S_QL, s);
+  solve_rows(F, RSF_OP_APPLY, at.as<double>(), ft.as<double>(), 1);
+  dot_into(at.as<double>(), ft.as<double>(), n, sc.as<double>() + S_QF, s);
+  peel_trace(F, nullptr, tol_peel, o, sc.as<double>() + S_TNUG);
+  peel_trace(F, Fl.get(), tol_peel, o, sc.as<double>() + S_TL);
+  LAUNCH(score_kernel, 1, 32, 0, s, sc.as<double>(), n, F->kp.s2, F->kp.nug);
+  double h[S_NSLOTS];
+  d2h(h, sc.as<double>(), S_NSLOTS, s);
+  check_status(F);
+  check_status(Fl.get());
+  for (int i = 0; i < 3; i++) score[i] = h[S_G0 + i];
+  if (terms)
+    for (int i = 0; i < 6; i++) terms[i] = h[S_T0 + i];
+  API_END
+}
+
+rsf_status gp_loglik_and_score(const double* points, const double* z, int64_t n, const rsf_kernel* kernel,
+                               const double* theta, double tol_fact, double tol_peel, const rsf_opts* opts,
+                               void* stream, double* loglik, double* score, double* terms) {
+  API_BEGIN
+  RSF_CHECK(points && z && loglik, RSF_EINVAL, "points, z and loglik must not be NULL");
+  rsf_opts o = resolve_opts(opts);
+  check_kernel(kernel, theta);
+  cudaStream_t s = (cudaStream_t)stream;
+  auto t = build_tree(points, n, o, s);
+  std::unique_ptr<rsf_handle_s> F(make_handle(t, kernel, theta, RSF_SIGMA, tol_fact, o));
+  DBuf alpha;
+  alpha.alloc(sizeof(double) * n, s);
+  double ll = 0;
+  rsf_status st = gp_loglik(F.get(), z, alpha.as<double>(), &ll, nullptr);
+  if (st != RSF_OK) fail(st, g_err);
+  if (score) {
+    double g[3], tm[6];
+    st = gp_score(F.get(), alpha.as<double>(), tol_fact, tol_peel, &o, g, tm);
+    if (st != RSF_OK) fail(st, g_err);
+    for (int i = 0; i < 3; i++) score[i] = g[i];
+    if (terms)
+      for (int i = 0; i < 6; i++) terms[i] = tm[i];
+  }
+  *loglik = ll;
+  API_END
+}
+
+rsf_status rsf_get_info(rsf_handle h, rsf_info_t* info) {
+  API_BEGIN
+  RSF_CHECK(h && info, RSF_EINVAL, "handle and info must not be NULL");
+  info->n = h->tree_raw->t.n;
+  info->levels = (int)h->levels.size();
+  int64_t nb = 0;
+  for (auto& l : h->levels) nb += l.nb;
+  info->boxes = nb;
+  info->root_size = h->levels.empty() ? 0 : (int)h->levels[0].nrows;
+  info->max_rank = h->max_rank;
+  info->max_active = h->max_active;
+  info->factor_entries = h->factor_entries;
+  info->flops = h->flops;
+  info->kernel_evals = h->kevals;
+  API_END
+}
+
+int64_t rsf_launch_count(int reset) {
+  int64_t v = g_launches;
+  if (reset) g_launches = 0;
+  return v;
+}
+
+void rsf_destroy(rsf_handle h) {
+  if (!h) return;
+  cudaStream_t s = h->stream;
+  delete h;
+  cudaStreamSynchronize(s);
+}
+
+}  // extern "C"

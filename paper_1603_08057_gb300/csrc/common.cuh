@@ -1,0 +1,119 @@
+// Shared infrastructure of the RSF library: error handling, stream-ordered
+// device buffers, the device status word and launch accounting.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/rsf.h"
+
+namespace rsf {
+
+// ---------------------------------------------------------------- errors
+struct Error {
+  rsf_status code;
+  std::string msg;
+};
+
+void set_error(const std::string& msg);
+[[noreturn]] void fail(rsf_status code, const std::string& msg);
+
+#define RSF_CUDA(call)                                                        \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess)                                                    \
+      ::rsf::fail(e_ == cudaErrorMemoryAllocation ? RSF_ENOMEM : RSF_ECUDA,  \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));        \
+  } while (0)
+
+#define RSF_CHECK(cond, code, msg)                  \
+  do {                                              \
+    if (!(cond)) ::rsf::fail((code), (msg));        \
+  } while (0)
+
+// Launch accounting: every kernel launch of the library goes through LAUNCH,
+// which counts it and checks the launch error.
+extern int64_t g_launches;
+#define LAUNCH(kernel, grid, block, smem, stream, ...)                       \
+  do {                                                                        \
+    dim3 g_ = (grid);                                                         \
+    if (g_.x > 0 && g_.y > 0 && g_.z > 0) {                                   \
+      kernel<<<g_, (block), (smem), (stream)>>>(__VA_ARGS__);                 \
+      ::rsf::g_launches++;                                                    \
+      RSF_CUDA(cudaGetLastError());                                           \
+    }                                                                         \
+  } while (0)
+
+// Device status word written by kernels on numerical failure:
+// [0] code (rsf_status), [1] level, [2] box, [3] detail.
+struct DevStatus {
+  int code, level, box, detail;
+};
+
+__device__ __forceinline__ void report(DevStatus* st, int code, int level, int box, int detail) {
+  if (atomicCAS(&st->code, 0, code) == 0) {
+    st->level = level;
+    st->box = box;
+    st->detail = detail;
+  }
+}
+
+// ---------------------------------------------------------- device memory
+// Stream-ordered allocation; the owner frees on the same stream.
+struct DBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaStream_t s = nullptr;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept { *this = std::move(o); }
+  DBuf& operator=(DBuf&& o) noexcept {
+    if (this != &o) {
+      release();
+      p = o.p; bytes = o.bytes; s = o.s;
+      o.p = nullptr; o.bytes = 0;
+    }
+    return *this;
+  }
+  ~DBuf() { release(); }
+  void alloc(size_t nbytes, cudaStream_t stream) {
+    release();
+    s = stream;
+    bytes = nbytes;
+    if (nbytes == 0) return;
+    RSF_CUDA(cudaMallocAsync(&p, nbytes, stream));
+  }
+  void zero() {
+    if (bytes) RSF_CUDA(cudaMemsetAsync(p, 0, bytes, s));
+  }
+  void release() {
+    if (p) cudaFreeAsync(p, s);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+template <class T>
+inline void h2d(T* dst, const T* src, size_t count, cudaStream_t s) {
+  if (count) RSF_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyHostToDevice, s));
+}
+template <class T>
+inline void d2h(T* dst, const T* src, size_t count, cudaStream_t s) {
+  if (count) RSF_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyDeviceToHost, s));
+}
+// Upload a host vector into a fresh device buffer.
+template <class T>
+inline void upload(DBuf& b, const std::vector<T>& v, cudaStream_t s) {
+  b.alloc(v.size() * sizeof(T), s);
+  h2d(b.as<T>(), v.data(), v.size(), s);
+}
+inline void sync(cudaStream_t s) { RSF_CUDA(cudaStreamSynchronize(s)); }
+
+inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+}  // namespace rsf

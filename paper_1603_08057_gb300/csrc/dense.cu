@@ -1,0 +1,616 @@
+// Batched ragged fp64 dense kernels: see dense.cuh.
+#include <algorithm>
+#include <cfloat>
+
+#include "dense.cuh"
+
+namespace rsf {
+
+// ===================================================================== GEMM
+// Tile BM x BN = 64 x 32, BK = 16, 128 threads; each thread owns a 4 x 4
+// register tile (rows tm + 16 i, cols tn + 8 j).  fp64 FMA.
+constexpr int BM = 64, BN = 32, BK = 16, GT = 128;
+
+__device__ __forceinline__ int find_prob(const int* prefix, int nprob, int tile) {
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= tile) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(GT) gemm_kernel(const GemmDesc* __restrict__ descs,
+                                                  const int* __restrict__ prefix, int nprob,
+                                                  GemmBases bases) {
+  const int p = find_prob(prefix, nprob, blockIdx.x);
+  const GemmDesc d = descs[p];
+  const int M = d.M >= 0 ? d.M : bases.M;
+  const int N = d.N, K = d.K;
+  const int n0 = (blockIdx.x - prefix[p]) * BN;
+  const int m0 = blockIdx.y * BM;
+  if (m0 >= M || n0 >= N) return;
+  if (d.lowC && n0 > m0 + BM - 1) return;
+  const int lda = d.lda >= 0 ? d.lda : bases.ld;
+  const int ldb = d.ldb >= 0 ? d.ldb : bases.ld;
+  const int ldc = d.ldc >= 0 ? d.ldc : bases.ld;
+  const double* __restrict__ A = bases.p[d.abase] + d.a * bases.sc[d.abase];
+  const double* __restrict__ B = bases.p[d.bbase] + d.b * bases.sc[d.bbase];
+  double* __restrict__ C = bases.p[d.cbase] + d.c * bases.sc[d.cbase];
+  int k0 = 0, k1 = K;
+  if (d.triB == 1) k0 = min(n0, K);
+  if (d.triB == 2) k1 = min(K, n0 + BN);
+
+  __shared__ double sA[BK][BM + 1];
+  __shared__ double sB[BK][BN + 1];
+  const int t = threadIdx.x;
+  const int tm = t & 15, tn = t >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
+
+  for (int kb = k0; kb < k1; kb += BK) {
+    // A tile: BM x BK of op(A)
+#pragma unroll
+    for (int r = 0; r < (BM * BK) / GT; r++) {
+      int idx = t + r * GT;
+      int mm, kk;
+      if (!d.ta) { mm = idx % BM; kk = idx / BM; } else { kk = idx % BK; mm = idx / BK; }
+      int gm = m0 + mm, gk = kb + kk;
+      double v = 0.0;
+      if (gm < M && gk < k1) v = d.ta ? A[gk + (int64_t)gm * lda] : A[gm + (int64_t)gk * lda];
+      sA[kk][mm] = v;
+    }
+    // B tile: BK x BN of op(B)
+#pragma unroll
+    for (int r = 0; r < (BN * BK) / GT; r++) {
+      int idx = t + r * GT;
+      int nn, kk;
+      if (!d.tb) { kk = idx % BK; nn = idx / BK; } else { nn = idx % BN; kk = idx / BN; }
+      int gn = n0 + nn, gk = kb + kk;
+      double v = 0.0;
+      if (gn < N && gk < k1) {
+        bool zero = (d.triB == 1 && gk < gn) || (d.triB == 2 && gk > gn);
+        if (!zero) v = d.tb ? B[gn + (int64_t)gk * ldb] : B[gk + (int64_t)gn * ldb];
+      }
+      sB[kk][nn] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; kk++) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; i++) a[i] = sA[kk][tm + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; j++) b[j] = sB[kk][tn + 8 * j];
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  const double alpha = d.alpha * bases.alpha_scale, beta = d.beta;
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    int gm = m0 + tm + 16 * i;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      int gn = n0 + tn + 8 * j;
+      if (gn >= N) continue;
+      if (d.lowC && gm < gn) continue;
+      double* cp = C + gm + (int64_t)gn * ldc;
+      double v = alpha * acc[i][j];
+      if (beta != 0.0) v = fma(beta, *cp, v);
+      *cp = v;
+    }
+  }
+}
+
+void GemmBatch::build(const std::vector<GemmDesc>& d, cudaStream_t s) {
+  nprob = (int)d.size();
+  std::vector<int> pre(nprob + 1, 0);
+  maxM = 0;
+  anyLaunchM = false;
+  for (int i = 0; i < nprob; i++) {
+    pre[i + 1] = pre[i] + std::max(0, cdiv(d[i].N, BN));
+    if (d[i].M < 0) anyLaunchM = true; else maxM = std::max(maxM, d[i].M);
+  }
+  ntilesN = pre[nprob];
+  upload(desc, d, s);
+  upload(prefix, pre, s);
+}
+
+void GemmBatch::run(const GemmBases& b, cudaStream_t s) const {
+  if (nprob == 0 || ntilesN == 0) return;
+  int M = maxM;
+  if (anyLaunchM) M = std::max(M, b.M);
+  if (M <= 0) return;
+  dim3 grid(ntilesN, cdiv(M, BM));
+  RSF_CHECK(grid.y <= 65535, RSF_EINVAL, "gemm: M too large");
+  LAUNCH(gemm_kernel, grid, GT, 0, s, desc.as<GemmDesc>(), prefix.as<int>(), nprob, b);
+}
+
+// ============================================================ pivoted QR
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long pivot_key(double norm2, int col) {
+  // Non-negative doubles order like their bit patterns; the low 16 bits carry
+  // the complement of the column so that ties go to the lowest column.
+  unsigned long long b = (unsigned long long)__double_as_longlong(norm2);
+  return (b & ~0xFFFFull) | (unsigned long long)(0xFFFF - col);
+}
+
+// Initial column norms: one warp per (problem, eligible column).
+__global__ void qr_init_kernel(const QRProb* __restrict__ probs, QRState* __restrict__ st,
+                               const int* __restrict__ colprefix, int nprob, int64_t ncols,
+                               const double* __restrict__ pool, unsigned char* __restrict__ chosen) {
+  int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (gw >= ncols) return;
+  int p = find_prob(colprefix, nprob, (int)gw);
+  const QRProb q = probs[p];
+  int col = (int)(gw - colprefix[p]);
+  if (lane == 0) chosen[q.col0 + col] = 0;
+  if (col >= q.cpiv) return;
+  const double* a = pool + q.a + (int64_t)col * q.lda;
+  double s = 0.0;
+  for (int i = lane; i < q.m; i += 32) s = fma(a[i], a[i], s);
+  s = warp_sum(s);
+  if (lane == 0) atomicMax(&st[p].key[0], pivot_key(s, col));
+}
+
+__global__ void qr_reset_kernel(QRState* st, int nprob) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nprob) return;
+  st[p].done = 0; st[p].k = 0; st[p].r11 = 0.0; st[p].tau = 0.0;
+  st[p].key[0] = 0ull; st[p].key[1] = 0ull;
+}
+
+// Step j, one CTA per problem: choose the pivot, build the Householder
+// reflector H = I - tau v v^T with H x = beta e_j, store v and tau.
+__global__ void __launch_bounds__(256) qr_pivot_kernel(const QRProb* __restrict__ probs,
+                                                       QRState* __restrict__ st, int j,
+                                                       double* __restrict__ pool,
+                                                       int* __restrict__ piv,
+                                                       unsigned char* __restrict__ chosen,
+                                                       double* __restrict__ vbuf,
+                                                       int* __restrict__ ndone,
+                                                       DevStatus* dst, int level) {
+  const int p = blockIdx.x;
+  __shared__ double red[8];
+  __shared__ int s_p, s_stop;
+  QRState* S = st + p;
+  if (S->done) return;
+  const QRProb q = probs[p];
+  const int t = threadIdx.x;
+  if (t == 0) {
+    unsigned long long key = S->key[j & 1];
+    int stop = 0;
+    if (j >= q.maxk || j >= q.m || j >= q.cpiv || key == 0ull) stop = 1;
+    s_p = stop ? -1 : 0xFFFF - (int)(key & 0xFFFFull);
+    s_stop = stop;
+  }
+  __syncthreads();
+  if (s_stop) {
+    if (t == 0) { S->done = 1; S->k = j; atomicAdd(ndone, 1); }
+    return;
+  }
+  const int pc = s_p;
+  double* a = pool + q.a + (int64_t)pc * q.lda;
+  double s = 0.0;
+  for (int i = j + t; i < q.m; i += 256) s = fma(a[i], a[i], s);
+  s = warp_sum(s);
+  if ((t & 31) == 0) red[t >> 5] = s;
+  __syncthreads();
+  if (t == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < 8; w++) tot += red[w];
+    double nrm = sqrt(tot);
+    if (!(nrm == nrm) || nrm > DBL_MAX) report(dst, RSF_ENUMERIC, level, p, j);
+    if (j == 0) S->r11 = nrm;
+    int stop = (nrm == 0.0) || (q.tol > 0.0 && nrm <= q.tol * S->r11) || !(nrm == nrm);
+    if (stop) {
+      S->done = 1; S->k = j; atomicAdd(ndone, 1);
+      s_stop = 1;
+    } else {
+      double x0 = a[j];
+      double beta = x0 >= 0.0 ? -nrm : nrm;
+      double v0 = x0 - beta;
+      S->tau = (beta - x0) / beta;
+      red[0] = 1.0 / v0;
+      a[j] = beta;
+      piv[q.col0 + j] = pc;
+      chosen[q.col0 + pc] = 1;
+      S->key[(j + 1) & 1] = 0ull;
+      s_stop = 0;
+    }
+  }
+  __syncthreads();
+  if (s_stop) return;
+  const double inv_v0 = red[0];
+  double* v = vbuf + q.row0;
+  if (t == 0) v[j] = 1.0;
+  for (int i = j + 1 + t; i < q.m; i += 256) {
+    v[i] = a[i] * inv_v0;
+    a[i] = 0.0;
+  }
+}
+
+// Step j: apply H to every unchosen column, recompute its norm below row j
+// and offer it as the next pivot.  One warp per (problem, column).
+__global__ void qr_update_kernel(const QRProb* __restrict__ probs, QRState* __restrict__ st,
+                                 const int* __restrict__ colprefix, int nprob, int64_t ncols,
+                                 int j, double* __restrict__ pool,
+                                 const unsigned char* __restrict__ chosen,
+                                 const double* __restrict__ vbuf) {
+  int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (gw >= ncols) return;
+  int p = find_prob(colprefix, nprob, (int)gw);
+  if (st[p].done) return;
+  const QRProb q = probs[p];
+  int col = (int)(gw - colprefix[p]);
+  if (chosen[q.col0 + col]) return;
+  double* a = pool + q.a + (int64_t)col * q.lda;
+  const double* v = vbuf + q.row0;
+  double s = 0.0;
+  for (int i = j + lane; i < q.m; i += 32) s = fma(v[i], a[i], s);
+  s = warp_sum(s) * st[p].tau;
+  double n2 = 0.0;
+  for (int i = j + lane; i < q.m; i += 32) {
+    double x = fma(-s, v[i], a[i]);
+    a[i] = x;
+    if (i > j) n2 = fma(x, x, n2);
+  }
+  n2 = warp_sum(n2);
+  if (lane == 0 && col < q.cpiv) atomicMax(&st[p].key[(j + 1) & 1], pivot_key(n2, col));
+}
+
+void QRBatch::build(const std::vector<QRProb>& p, cudaStream_t s) {
+  nprob = (int)p.size();
+  std::vector<QRProb> pp = p;
+  colprefix_h.assign(nprob + 1, 0);
+  ncols = 0; nrows = 0; maxsteps = 0;
+  for (int i = 0; i < nprob; i++) {
+    RSF_CHECK(pp[i].cpiv <= 0xFFFF, RSF_EINVAL, "qr: too many pivot columns");
+    pp[i].col0 = ncols;
+    pp[i].row0 = nrows;
+    ncols += pp[i].c;
+    nrows += pp[i].m;
+    colprefix_h[i + 1] = (int)ncols;
+    maxsteps = std::max(maxsteps, std::min(pp[i].maxk, std::min(pp[i].m, pp[i].cpiv)));
+  }
+  RSF_CHECK(ncols < (int64_t)1 << 31, RSF_EINVAL, "qr: too many columns");
+  upload(prob, pp, s);
+  upload(colprefix, colprefix_h, s);
+  state.alloc(sizeof(QRState) * std::max(1, nprob), s);
+  piv.alloc(sizeof(int) * std::max<int64_t>(1, ncols), s);
+  chosen.alloc(std::max<int64_t>(1, ncols), s);
+  vbuf.alloc(sizeof(double) * std::max<int64_t>(1, nrows), s);
+  ndone.alloc(sizeof(int), s);
+}
+
+void QRBatch::run(double* pool, DevStatus* st, int level, cudaStream_t s) {
+  if (nprob == 0) return;
+  LAUNCH(qr_reset_kernel, cdiv(nprob, 128), 128, 0, s, state.as<QRState>(), nprob);
+  ndone.zero();
+  int blocksU = cdiv(ncols * 32, 256);
+  LAUNCH(qr_init_kernel, blocksU, 256, 0, s, prob.as<QRProb>(), state.as<QRState>(),
+         colprefix.as<int>(), nprob, ncols, pool, chosen.as<unsigned char>());
+  int hdone = 0;
+  for (int j = 0; j <= maxsteps; j++) {
+    LAUNCH(qr_pivot_kernel, nprob, 256, 0, s, prob.as<QRProb>(), state.as<QRState>(), j, pool,
+           piv.as<int>(), chosen.as<unsigned char>(), vbuf.as<double>(), ndone.as<int>(), st, level);
+    if (j == maxsteps) break;
+    LAUNCH(qr_update_kernel, blocksU, 256, 0, s, prob.as<QRProb>(), state.as<QRState>(),
+           colprefix.as<int>(), nprob, ncols, j, pool, chosen.as<unsigned char>(), vbuf.as<double>());
+    if ((j & 31) == 31) {
+      d2h(&hdone, ndone.as<int>(), 1, s);
+      sync(s);
+      if (hdone >= nprob) break;
+    }
+  }
+}
+
+// [S, R] split: S in pivot order, R = remaining eligible columns ascending.
+__global__ void qr_split_kernel(const QRProb* __restrict__ probs, const QRState* __restrict__ st,
+                                const int* __restrict__ piv, const unsigned char* __restrict__ chosen,
+                                const int64_t* __restrict__ out0, int* __restrict__ perm,
+                                int* __restrict__ kout) {
+  const int p = blockIdx.x;
+  const QRProb q = probs[p];
+  const int k = st[p].k;
+  int* o = perm + out0[p];
+  if (threadIdx.x == 0) kout[p] = k;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) o[i] = piv[q.col0 + i];
+  // ordered compaction of the unchosen eligible columns (single warp scan)
+  if (threadIdx.x < 32) {
+    int lane = threadIdx.x, base = k;
+    for (int c0 = 0; c0 < q.cpiv; c0 += 32) {
+      int c = c0 + lane;
+      int flag = (c < q.cpiv) && !chosen[q.col0 + c];
+      unsigned m = __ballot_sync(0xffffffffu, flag);
+      if (flag) o[base + __popc(m & ((1u << lane) - 1u))] = c;
+      base += __popc(m);
+    }
+  }
+}
+
+void qr_split(const QRBatch& qb, const int64_t* d_out0, int* d_perm, int* d_kout, cudaStream_t s) {
+  if (qb.nprob == 0) return;
+  LAUNCH(qr_split_kernel, qb.nprob, 128, 0, s, qb.d_prob(), qb.d_state(), qb.d_piv(),
+         qb.chosen.as<unsigned char>(), d_out0, d_perm, d_kout);
+}
+
+// Back-substitution, one warp per (problem, rhs): column-oriented, in place in
+// the output column.  Uses R11[i][jj] = A[i, piv[jj]].
+struct TrsmDev {
+  int nrhs;
+  int64_t rhs0, out0;
+};
+
+__global__ void qr_trsm_kernel(const QRProb* __restrict__ probs, const QRState* __restrict__ st,
+                               const int* __restrict__ piv, const TrsmDev* __restrict__ tp,
+                               const int* __restrict__ prefix, int nprob, int total,
+                               const int* __restrict__ rhs, const double* __restrict__ pool,
+                               double* __restrict__ outpool, DevStatus* dst, int level) {
+  int gw = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  int lane = threadIdx.x & 31;
+  if (gw >= total) return;
+  int p = find_prob(prefix, nprob, gw);
+  int s = gw - prefix[p];
+  const QRProb q = probs[p];
+  const TrsmDev d = tp[p];
+  const int k = st[p].k;
+  const int* pv = piv + q.col0;
+  double* x = outpool + d.out0 + (int64_t)s * k;
+  if (d.rhs0 >= 0) {
+    int col = rhs[d.rhs0 + s];
+    const double* a = pool + q.a + (int64_t)col * q.lda;
+    for (int i = lane; i < k; i += 32) x[i] = a[i];
+  } else {
+    for (int i = lane; i < k; i += 32) x[i] = (i == s) ? 1.0 : 0.0;
+  }
+  __syncwarp();
+  int iend = (d.rhs0 >= 0) ? k - 1 : min(s, k - 1);
+  for (int i = k - 1; i > iend; i--) {
+    if (lane == 0) x[i] = 0.0;  // identity mode: rows below s are zero
+  }
+  __syncwarp();
+  for (int i = iend; i >= 0; i--) {
+    const double* ri = pool + q.a + (int64_t)pv[i] * q.lda;  // column i of R11
+    double xi = x[i] / ri[i];
+    __syncwarp();
+    if (lane == 0) x[i] = xi;
+    for (int r = lane; r < i; r += 32) x[r] = fma(-xi, ri[r], x[r]);
+    __syncwarp();
+  }
+}
+
+void qr_trsm(const QRBatch& qb, const std::vector<TrsmProb>& tp, const int* d_rhs,
+             double* pool, double* outpool, DevStatus* st, int level, cudaStream_t s) {
+  if (qb.nprob == 0) return;
+  std::vector<TrsmDev> td(qb.nprob);
+  std::vector<int> pre(qb.nprob + 1, 0);
+  for (int i = 0; i < qb.nprob; i++) {
+    td[i].nrhs = tp[i].nrhs;
+    td[i].rhs0 = tp[i].rhs0;
+    td[i].out0 = tp[i].out0;
+    pre[i + 1] = pre[i] + tp[i].nrhs;
+  }
+  if (pre[qb.nprob] == 0) return;
+  DBuf dtd, dpre;
+  upload(dtd, td, s);
+  upload(dpre, pre, s);
+  LAUNCH(qr_trsm_kernel, cdiv((int64_t)pre[qb.nprob] * 32, 256), 256, 0, s, qb.d_prob(),
+         qb.d_state(), qb.d_piv(), dtd.as<TrsmDev>(), dpre.as<int>(), qb.nprob, pre[qb.nprob],
+         d_rhs, pool, outpool, st, level);
+}
+
+// ============================================================== Cholesky
+constexpr int NB = 32;
+
+// Panel p0: factor the diagonal block in shared memory, then solve the
+// rows below against it.  One CTA (256 threads) per problem.
+__global__ void __launch_bounds__(256) chol_panel_kernel(const CholProb* __restrict__ probs,
+                                                         int p0, double* __restrict__ pool,
+                                                         DevStatus* dst, int level) {
+  const CholProb q = probs[blockIdx.x];
+  if (p0 >= q.n) return;
+  const int nb = min(NB, q.n - p0);
+  double* A = pool + q.a;
+  const int ld = q.ld;
+  __shared__ double D[NB][NB + 1];
+  const int t = threadIdx.x;
+  for (int idx = t; idx < nb * nb; idx += 256) {
+    int i = idx % nb, j = idx / nb;
+    D[i][j] = (i >= j) ? A[(p0 + i) + (int64_t)(p0 + j) * ld] : 0.0;
+  }
+  __syncthreads();
+  for (int j = 0; j < nb; j++) {
+    if (t == 0) {
+      double d = D[j][j];
+      if (!(d > 0.0)) {
+        report(dst, RSF_ENOTPD, level, q.box, p0 + j);
+        d = 1.0;
+      }
+      D[j][j] = sqrt(d);
+    }
+    __syncthreads();
+    double djj = D[j][j];
+    for (int i = j + 1 + t; i < nb; i += 256) D[i][j] /= djj;
+    __syncthreads();
+    for (int idx = t; idx < nb * nb; idx += 256) {
+      int i = idx % nb, c = idx / nb;
+      if (c > j && i >= c) D[i][c] = fma(-D[i][j], D[c][j], D[i][c]);
+    }
+    __syncthreads();
+  }
+  for (int idx = t; idx < nb * nb; idx += 256) {
+    int i = idx % nb, j = idx / nb;
+    if (i >= j) A[(p0 + i) + (int64_t)(p0 + j) * ld] = D[i][j];
+  }
+  // rows below: L21 = A21 D^-T (forward substitution per row)
+  for (int i = p0 + nb + t; i < q.n; i += 256) {
+    double x[NB];
+#pragma unroll
+    for (int j = 0; j < NB; j++) x[j] = (j < nb) ? A[i + (int64_t)(p0 + j) * ld] : 0.0;
+#pragma unroll
+    for (int j = 0; j < NB; j++) {
+      if (j < nb) {
+        double v = x[j];
+#pragma unroll
+        for (int c = 0; c < NB; c++)
+          if (c < j) v = fma(-x[c], D[j][c], v);
+        x[j] = v / D[j][j];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NB; j++)
+      if (j < nb) A[i + (int64_t)(p0 + j) * ld] = x[j];
+  }
+}
+
+void cholesky_batched(const std::vector<CholProb>& p, double* pool, DevStatus* st, int level,
+                      cudaStream_t s) {
+  if (p.empty()) return;
+  DBuf dp;
+  upload(dp, p, s);
+  int nmax = 0;
+  for (auto& q : p) nmax = std::max(nmax, q.n);
+  for (int p0 = 0; p0 < nmax; p0 += NB) {
+    LAUNCH(chol_panel_kernel, (int)p.size(), 256, 0, s, dp.as<CholProb>(), p0, pool, st, level);
+    int p1 = p0 + NB;
+    if (p1 >= nmax) break;
+    std::vector<GemmDesc> gd;
+    for (auto& q : p) {
+      if (q.n <= p1) continue;
+      GemmDesc g{};
+      g.M = g.N = q.n - p1;
+      g.K = NB;
+      g.lda = g.ldb = g.ldc = q.ld;
+      g.a = q.a + p1 + (int64_t)p0 * q.ld;       // L21
+      g.b = g.a;                                  // L21^T
+      g.c = q.a + p1 + (int64_t)p1 * q.ld;
+      g.abase = g.bbase = g.cbase = 0;
+      g.ta = 0; g.tb = 1; g.triB = 0; g.lowC = 1;
+      g.alpha = -1.0; g.beta = 1.0;
+      gd.push_back(g);
+    }
+    if (gd.empty()) continue;
+    GemmBatch gb;
+    gb.build(gd, s);
+    GemmBases b{};
+    b.p[0] = pool; b.alpha_scale = 1.0;
+    b.sc[0] = b.sc[1] = b.sc[2] = b.sc[3] = 1;
+    gb.run(b, s);
+  }
+}
+
+// ====================================================== triangular inverse
+__global__ void lower_inverse_kernel(const TriInvProb* __restrict__ probs, const int* __restrict__ prefix,
+                                     int nprob, int total, const double* __restrict__ in,
+                                     double* __restrict__ out) {
+  int gw = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  int lane = threadIdx.x & 31;
+  if (gw >= total) return;
+  int p = find_prob(prefix, nprob, gw);
+  const TriInvProb q = probs[p];
+  int j = gw - prefix[p];
+  const double* C = in + q.a;
+  double* y = out + q.out + (int64_t)j * q.n;
+  for (int i = lane; i < q.n; i += 32) y[i] = (i == j) ? 1.0 : 0.0;
+  __syncwarp();
+  for (int i = j; i < q.n; i++) {
+    double yi = y[i] / C[i + (int64_t)i * q.ld];
+    __syncwarp();
+    if (lane == 0) y[i] = yi;
+    for (int r = i + 1 + lane; r < q.n; r += 32) y[r] = fma(-yi, C[r + (int64_t)i * q.ld], y[r]);
+    __syncwarp();
+  }
+}
+
+void lower_inverse_batched(const std::vector<TriInvProb>& p, const double* in, double* out,
+                           cudaStream_t s) {
+  if (p.empty()) return;
+  std::vector<int> pre(p.size() + 1, 0);
+  for (size_t i = 0; i < p.size(); i++) pre[i + 1] = pre[i] + p[i].n;
+  if (pre.back() == 0) return;
+  DBuf dp, dpre;
+  upload(dp, p, s);
+  upload(dpre, pre, s);
+  LAUNCH(lower_inverse_kernel, cdiv((int64_t)pre.back() * 32, 256), 256, 0, s, dp.as<TriInvProb>(),
+         dpre.as<int>(), (int)p.size(), pre.back(), in, out);
+}
+
+// ============================================================ small helpers
+__global__ void symmetrize_kernel(const SqProb* __restrict__ probs, const int64_t* __restrict__ prefix,
+                                  int nprob, int64_t total, double* __restrict__ pool) {
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= total) return;
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= g) lo = mid; else hi = mid - 1;
+  }
+  const SqProb q = probs[lo];
+  int64_t e = g - prefix[lo];
+  int i = (int)(e % q.n), j = (int)(e / q.n);
+  if (i <= j) return;
+  double* A = pool + q.a;
+  double a = A[i + (int64_t)j * q.ld], b = A[j + (int64_t)i * q.ld];
+  double m = 0.5 * (a + b);
+  A[i + (int64_t)j * q.ld] = m;
+  A[j + (int64_t)i * q.ld] = m;
+}
+
+void symmetrize_batched(const std::vector<SqProb>& p, double* pool, cudaStream_t s) {
+  if (p.empty()) return;
+  std::vector<int64_t> pre(p.size() + 1, 0);
+  for (size_t i = 0; i < p.size(); i++) pre[i + 1] = pre[i] + (int64_t)p[i].n * p[i].n;
+  if (pre.back() == 0) return;
+  DBuf dp, dpre;
+  upload(dp, p, s);
+  upload(dpre, pre, s);
+  LAUNCH(symmetrize_kernel, cdiv(pre.back(), 256), 256, 0, s, dp.as<SqProb>(), dpre.as<int64_t>(),
+         (int)p.size(), pre.back(), pool);
+}
+
+__global__ void copy_kernel(const CopyProb* __restrict__ probs, const int64_t* __restrict__ prefix,
+                            int nprob, int64_t total, const double* __restrict__ src,
+                            double* __restrict__ dst) {
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= total) return;
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= g) lo = mid; else hi = mid - 1;
+  }
+  const CopyProb q = probs[lo];
+  int64_t e = g - prefix[lo];
+  int i = (int)(e % q.m), j = (int)(e / q.m);
+  double v = q.trans ? src[q.src + j + (int64_t)i * q.lds] : src[q.src + i + (int64_t)j * q.lds];
+  dst[q.dst + i + (int64_t)j * q.ldd] = v;
+}
+
+void copy_batched(const std::vector<CopyProb>& p, const double* src, double* dst, cudaStream_t s) {
+  if (p.empty()) return;
+  std::vector<int64_t> pre(p.size() + 1, 0);
+  for (size_t i = 0; i < p.size(); i++) pre[i + 1] = pre[i] + (int64_t)p[i].m * p[i].n;
+  if (pre.back() == 0) return;
+  DBuf dp, dpre;
+  upload(dp, p, s);
+  upload(dpre, pre, s);
+  LAUNCH(copy_kernel, cdiv(pre.back(), 256), 256, 0, s, dp.as<CopyProb>(), dpre.as<int64_t>(),
+         (int)p.size(), pre.back(), src, dst);
+}
+
+}  // namespace rsf

@@ -1,0 +1,132 @@
+// Batched ragged fp64 dense linear algebra used by every level of the
+// factorization, the solves and the peeling: GEMM, column-pivoted Householder
+// QR (one launch pair per elimination step over all problems), triangular
+// solves and a blocked Cholesky.
+#pragma once
+
+#include "common.cuh"
+
+namespace rsf {
+
+// C = alpha op(A) op(B) + beta C, column-major.  Pointers are offsets into
+// one of four base arrays passed at launch, so descriptor arrays built once
+// can be reused with fresh buffers (M < 0 / ld < 0 take the launch's values).
+struct GemmDesc {
+  int M, N, K;
+  int lda, ldb, ldc;
+  int64_t a, b, c;
+  int8_t abase, bbase, cbase;
+  int8_t ta, tb;
+  int8_t triB;   // 0: none, 1: op(B) lower triangular, 2: op(B) upper triangular
+  int8_t lowC;   // 1: skip output tiles strictly above the diagonal
+  int8_t pad;
+  double alpha, beta;
+};
+
+struct GemmBases {
+  double* p[4];
+  int64_t sc[4];  // offset multiplier per base (row-major buffers: the row length)
+  int M;       // used where desc.M < 0
+  int ld;      // used where desc.lda/ldc < 0
+  double alpha_scale;  // multiplies every desc.alpha
+};
+
+// Device-resident batch of GEMM problems with its tile prefix.
+struct GemmBatch {
+  DBuf desc, prefix;
+  int nprob = 0;
+  int ntilesN = 0;   // sum over problems of ceil(N / BN)
+  int maxM = 0;      // max M over problems with M >= 0
+  bool anyLaunchM = false;
+  void build(const std::vector<GemmDesc>& d, cudaStream_t s);
+  void run(const GemmBases& b, cudaStream_t s) const;
+};
+
+// ----------------------------------------------------------- pivoted QR
+// One problem: A (m x c, column-major, leading dimension lda) at offset a of
+// the QR pool.  Only the first cpiv columns may be pivots; the others are
+// carried along (they receive Q^T).  Stops after maxk steps or when the next
+// pivot's column norm is <= tol * (first pivot norm) (tol > 0).
+struct QRProb {
+  int m, c, cpiv, maxk, lda;
+  int64_t a;        // offset of A in the pool
+  int64_t col0;     // offset of this problem's per-column arrays (size c)
+  int64_t row0;     // offset of this problem's Householder vector (size m)
+  double tol;
+};
+struct QRState {
+  int done, k, pad0, pad1;
+  double r11, tau;
+  unsigned long long key[2];
+};
+
+struct QRBatch {
+  int nprob = 0;
+  int64_t ncols = 0, nrows = 0;
+  int maxsteps = 0;
+  std::vector<int> colprefix_h;   // host copy of the column prefix (for launch sizing)
+  DBuf prob, state, piv, chosen, vbuf, colprefix, ndone;
+  // m (rows) may be finalised on the device (near-field counts) before run().
+  void build(const std::vector<QRProb>& p, cudaStream_t s);
+  // Runs all steps; pool is the matrix storage; st is the status word.
+  void run(double* pool, DevStatus* st, int level, cudaStream_t s);
+  int* d_piv() const { return piv.as<int>(); }
+  QRState* d_state() const { return state.as<QRState>(); }
+  QRProb* d_prob() const { return prob.as<QRProb>(); }
+};
+
+// After a QR with truncation: per problem, the [S, R] permutation (S = pivot
+// order, R = remaining eligible columns in increasing order) written to
+// perm[out0 .. out0 + cpiv) and k to kout.
+void qr_split(const QRBatch& qb, const int64_t* d_out0, int* d_perm, int* d_kout, cudaStream_t s);
+
+// Back-substitution with the QR's upper triangle R11 (k x k, pivot order):
+// for each problem and each right-hand side column listed by rhs (physical
+// column indices of A, count nrhs per problem), solve R11 t = A[0:k, col]
+// into out (k x nrhs column-major at out0, ld k).  Identity mode (rhs null):
+// right-hand sides are the unit vectors e_0..e_{k-1} (gives R11^-1).
+struct TrsmProb {
+  int nrhs;
+  int64_t rhs0;   // offset into the rhs column-index array (or -1: identity)
+  int64_t out0;   // offset of the output in outpool
+};
+void qr_trsm(const QRBatch& qb, const std::vector<TrsmProb>& tp, const int* d_rhs,
+             double* pool, double* outpool, DevStatus* st, int level, cudaStream_t s);
+
+// ----------------------------------------------------------- Cholesky
+// In place lower Cholesky of n x n blocks (column-major, ld) at offsets a in
+// pool; upper triangles are left untouched (garbage).  Blocked: one panel
+// kernel per 32 columns plus a lower-triangle GEMM for the trailing matrix.
+struct CholProb {
+  int n, ld;
+  int64_t a;
+  int box;       // reported on failure
+};
+void cholesky_batched(const std::vector<CholProb>& p, double* pool, DevStatus* st,
+                      int level, cudaStream_t s);
+
+// Inverse of lower-triangular blocks: out (n x n, ld n, zero upper) at outoff
+// from in (n x n at a, ld) -- one warp per column.
+struct TriInvProb {
+  int n, ld;
+  int64_t a, out;
+};
+void lower_inverse_batched(const std::vector<TriInvProb>& p, const double* in,
+                           double* out, cudaStream_t s);
+
+// Symmetrise square blocks: A <- (A + A^T) / 2.
+struct SqProb {
+  int n, ld;
+  int64_t a;
+};
+void symmetrize_batched(const std::vector<SqProb>& p, double* pool, cudaStream_t s);
+
+// Copy sub-blocks: dst[i + j*ldd] = src[i + j*lds] (or transposed source).
+struct CopyProb {
+  int m, n, lds, ldd;
+  int64_t src, dst;
+  int trans;  // 1: dst[i + j*ldd] = src[j + i*lds]
+};
+void copy_batched(const std::vector<CopyProb>& p, const double* src, double* dst, cudaStream_t s);
+
+}  // namespace rsf

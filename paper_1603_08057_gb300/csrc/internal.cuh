@@ -1,0 +1,158 @@
+// Internal structures of the RSF library (tree, factorization levels) and
+// the device kernel-function evaluation shared by the assembly kernels.
+#pragma once
+
+#include <array>
+#include <memory>
+
+#include "dense.cuh"
+
+struct rsf_tree_s;
+struct rsf_handle_s;
+
+namespace rsf {
+
+constexpr int DEPTH_BITS = 24;
+
+struct KernelParams {
+  int family;
+  double alpha;
+  double l, s2, nug;
+  int which;  // 0 Sigma, 1 d/dl, 2 d/ds2, 3 d/dnug
+};
+
+// Off-diagonal entry of Sigma (which 0) or dSigma/dtheta (which 1, 2, 3) at
+// distance r (Sec. 1 Eqs. (matern), (rationalquadratic); Sec. 5.5).
+__device__ __forceinline__ double kernel_offdiag(const KernelParams& kp, double r) {
+  if (kp.which == 3) return 0.0;
+  const double l = kp.l;
+  double k, dk;  // correlation and its l-derivative
+  switch (kp.family) {
+    case RSF_MATERN12: {
+      double e = exp(-r / l);
+      k = e;
+      dk = (r / (l * l)) * e;
+      break;
+    }
+    case RSF_MATERN32: {
+      double a = 1.7320508075688772 * r / l;
+      double e = exp(-a);
+      k = (1.0 + a) * e;
+      dk = a * a * e / l;
+      break;
+    }
+    case RSF_MATERN52: {
+      double a = 2.23606797749979 * r / l;
+      double e = exp(-a);
+      k = (1.0 + a + a * a / 3.0) * e;
+      dk = (a * a / 3.0) * (1.0 + a) * e / l;
+      break;
+    }
+    default: {  // RSF_RQ
+      double u = 1.0 + r * r / (2.0 * kp.alpha * l * l);
+      double p = pow(u, -kp.alpha);
+      k = p;
+      dk = p / u * r * r / (l * l * l);
+      break;
+    }
+  }
+  if (kp.which == 0) return kp.s2 * k;
+  if (kp.which == 1) return kp.s2 * dk;
+  return k;
+}
+
+__device__ __forceinline__ double kernel_diag(const KernelParams& kp) {
+  if (kp.which == 0) return kp.s2 + kp.nug;
+  if (kp.which == 1) return 0.0;
+  return 1.0;
+}
+
+__device__ __forceinline__ double dist2(double ax, double ay, double bx, double by) {
+  double dx = __dsub_rn(ax, bx), dy = __dsub_rn(ay, by);
+  return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+}
+
+// Host view of the quadtree (Sec. 2.1, Remark (tree)); device copies of the
+// tree-order coordinates and permutation.
+struct TreeData {
+  int64_t n = 0;
+  double lo[2] = {0, 0}, side = 1.0;
+  int n_occ = 64;
+  int L = 0;
+  // boxes (root first, levels contiguous)
+  std::vector<int> level, start, count, parent, slot, ix, iy;
+  std::vector<std::array<int, 4>> children;
+  std::vector<char> is_leaf;
+  std::vector<double> cx, cy, w;
+  std::vector<std::vector<int>> by_level;
+  std::vector<int> leafpos;      // host: per tree position, index in its leaf (built lazily)
+  int max_leaf = 0;
+  cudaStream_t stream = nullptr;
+  DBuf xt;     // n x 2 tree-order coordinates
+  DBuf perm;   // tree position -> original index (int)
+  DBuf iperm;  // original index -> tree position (int)
+};
+
+// One level of the factorization (boxes processed together).
+struct LevelData {
+  int lev = 0;
+  int nb = 0;
+  std::vector<int> box;                 // tree box ids
+  std::vector<int> c, k, r;             // |I|, |S|, |R|
+  std::vector<int64_t> row0;            // row offset of the box in the level's row space
+  int64_t nrows = 0;                    // sum of c
+  std::vector<int64_t> toff, eoff, doff, dioff;  // factor pool offsets: T, E, D, Dinv
+  std::vector<char> leafbox;
+  DBuf fpool;    // this level's factor storage (T, E, D, Dinv)
+  DBuf rr;       // per box R-row range (first row, count) for the middle copies
+  int nrr = 0;
+  DBuf Isr;      // DOF ids (tree positions) in [S, R] order, nrows ints
+  DBuf src;      // gather map: >= 0 row of level lev+1, < 0: -(1 + tree position)
+  // solve descriptors (offset based; bases: 0 = X in, 1 = X out/tmp, 2 = factor pool)
+  GemmBatch gRS_T;   // X_R += a * (op T) X_S   (C = R rows, A = S rows, B = T)
+  GemmBatch gSR_Et;  // X_S += a * E X_R
+  GemmBatch gRS_E;   // X_R += a * E^T X_S
+  GemmBatch gSR_Tt;  // X_S += a * T X_R
+  // middle (block diagonal) products on R rows: out = in * op(B)
+  GemmBatch gMid[5];  // 0: Dinv^T, 1: Dinv, 2: D, 3: D^T, 4: D (full, indefinite)
+};
+
+}  // namespace rsf
+
+// Opaque handle types of the C ABI.
+struct rsf_tree_s {
+  rsf::TreeData t;
+  rsf_opts opts;
+};
+
+struct rsf_handle_s {
+  std::shared_ptr<rsf_tree_s> tree;   // shared with other handles built on it
+  rsf_tree_s* tree_raw = nullptr;
+  rsf::KernelParams kp;
+  rsf_opts opts;
+  double tol = 0;
+  bool spd = true;
+  cudaStream_t stream = nullptr;
+  std::vector<rsf::LevelData> levels;  // index = tree level (0 = root)
+  rsf::DBuf status;                    // DevStatus
+  rsf::DBuf logdet_parts;              // per box partial log-determinants
+  int64_t nboxes_total = 0;
+  // bookkeeping
+  int max_rank = 0, max_active = 0;
+  double flops = 0, kevals = 0;
+  int64_t factor_entries = 0;
+};
+
+namespace rsf {
+std::shared_ptr<rsf_tree_s> build_tree(const double* points, int64_t n, const rsf_opts& o,
+                                       cudaStream_t s);
+void factorize(rsf_handle_s* h);
+void check_status(rsf_handle_s* h);
+// Internal solve on tree-order, row-major (n x q) buffers: out = op(F) in.
+void solve_rows(rsf_handle_s* h, int op, const double* in, double* out, int q);
+double peel_trace(rsf_handle_s* F, rsf_handle_s* Fk, double tol, const rsf_opts& o, double* d_out);
+// device reductions
+double dot_device(const double* a, const double* b, int64_t n, cudaStream_t s);
+// a . b into a device scalar (stream ordered, no synchronisation)
+void dot_into(const double* a, const double* b, int64_t n, double* d_out, cudaStream_t s);
+}  // namespace rsf

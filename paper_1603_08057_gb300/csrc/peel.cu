@@ -1,0 +1,711 @@
+// Trace of a symmetric black-box operator by weak-admissibility peeling
+// (Sec. 3), G = F^-1 or G = (F^-1 F_k + F_k F^-1)/2 (Algorithm 1).
+//
+// Level l = 1..L, top down:
+//   * test matrices W_k (k = slot 0..3) with i.i.d. N(0,1) entries on the rows
+//     of the level-l boxes in child slot k, zero elsewhere (Sec. 3.2); drawn
+//     from Philox4x32-10 with counter (row, col/4, level, 0), Box-Muller;
+//   * Y_k = G W_k - sum_{m<l} G^(m) W_k (all four slots in one multi-RHS
+//     application);
+//   * every ordered sibling pair (a, b): Y_ab = Y_{slot(b)}(I_a, :) ~ G_ab W_b;
+//     column-pivoted QR with relative cut-off tol gives the rank r_ab and the
+//     basis U_ab = Y_ab(:, piv) R11^-1;
+//   * Eq. (lowrankapprox): M_ab = (W_a^T U_ab)^+ Z (U_ba^T W_b)^+ with the
+//     symmetrised core Z = (W_a^T Y_ab + (W_b^T Y_ba)^T)/2 and M_ba = M_ab^T;
+//   * adaptivity: if a rank exceeds q - c, another q columns are appended.
+// Finally H = (G - sum_m G^(m)) E with E the stacked leaf identities and
+// Tr(G) ~ sum_leaves Tr H(I_i, [n_i]) (Sec. 3.2.4).
+#include <algorithm>
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace rsf {
+
+// --------------------------------------------------------------- Philox
+__device__ __forceinline__ void philox4x32_10(unsigned c[4], unsigned k0, unsigned k1) {
+#pragma unroll
+  for (int r = 0; r < 10; r++) {
+    if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+    unsigned long long p0 = (unsigned long long)0xD2511F53u * c[0];
+    unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c[2];
+    unsigned hi0 = (unsigned)(p0 >> 32), lo0 = (unsigned)p0;
+    unsigned hi1 = (unsigned)(p1 >> 32), lo1 = (unsigned)p1;
+    unsigned n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+  }
+}
+
+__device__ __forceinline__ double philox_normal(unsigned row, unsigned col, unsigned level, unsigned stream,
+                                                unsigned long long seed) {
+  unsigned c[4] = {row, col >> 2, level, stream};
+  philox4x32_10(c, (unsigned)(seed & 0xFFFFFFFFull), (unsigned)(seed >> 32));
+  const double two32 = 4294967296.0;
+  int w = col & 3;
+  double ua = ((double)c[w < 2 ? 0 : 2] + 0.5) / two32;
+  double ub = ((double)c[w < 2 ? 1 : 3] + 0.5) / two32;
+  double rad = sqrt(-2.0 * log(ua));
+  double s, co;
+  sincospi(2.0 * ub, &s, &co);
+  return (w & 1) ? rad * s : rad * co;
+}
+
+// W chunk: n x (4 qc) row-major; row p of a level box in slot s gets the
+// normals of columns col0 .. col0+qc-1 in column block s.
+__global__ void gen_w_kernel(const int* __restrict__ slotrow, int64_t n, int qc, int col0, int level,
+                             unsigned long long seed, double* __restrict__ W) {
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t tot = n * 4 * qc;
+  if (g >= tot) return;
+  int64_t p = g / (4 * qc);
+  int c = (int)(g % (4 * qc));
+  int s = slotrow[p];
+  double v = 0.0;
+  if (s >= 0 && c / qc == s) v = philox_normal((unsigned)p, (unsigned)(col0 + c % qc), (unsigned)level, 0u, seed);
+  W[g] = v;
+}
+
+// Column block extraction from row-major chunks into column-major matrices:
+// out[i + (col0 + j) * ldo] = in[(r0 + i) * ldi + cb + j], i < rows, j < qc.
+struct ExtractProb {
+  int64_t r0, out0;
+  int rows, cb;
+};
+__global__ void extract_kernel(const ExtractProb* __restrict__ ep, const int64_t* __restrict__ prefix, int nprob,
+                               int64_t total, int qc, int ldi, int col0, const double* __restrict__ in,
+                               double* __restrict__ out) {
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= total) return;
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= g) lo = mid; else hi = mid - 1;
+  }
+  const ExtractProb e = ep[lo];
+  int64_t x = g - prefix[lo];
+  int i = (int)(x % e.rows), j = (int)(x / e.rows);
+  out[e.out0 + i + (int64_t)(col0 + j) * e.rows] = in[(e.r0 + i) * ldi + e.cb + j];
+}
+
+// Gather pivot columns: out[:, t] = Y[:, piv[t]] for t < k.
+struct PivGather {
+  int64_t y0, out0, col0;
+  int rows;
+};
+__global__ void pivgather_kernel(const PivGather* __restrict__ pg, const int64_t* __restrict__ prefix, int nprob,
+                                 int64_t total, const int* __restrict__ piv, const QRState* __restrict__ st,
+                                 const double* __restrict__ Y, double* __restrict__ out) {
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= total) return;
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= g) lo = mid; else hi = mid - 1;
+  }
+  const PivGather e = pg[lo];
+  int64_t x = g - prefix[lo];
+  int i = (int)(x % e.rows), t = (int)(x / e.rows);
+  if (t >= st[lo].k) return;
+  int c = piv[e.col0 + t];
+  out[e.out0 + i + (int64_t)t * e.rows] = Y[e.y0 + i + (int64_t)c * e.rows];
+}
+
+// Least-squares scatter: out[o0 + piv[i]*ri + s*rs] = t[t0 + i + s*kq].
+struct PermScatter {
+  int64_t t0, o0, col0;
+  int nrow, ncol, ri, rs;
+};
+__global__ void permscatter_kernel(const PermScatter* __restrict__ ps, const int64_t* __restrict__ prefix,
+                                   int nprob, int64_t total, const int* __restrict__ piv,
+                                   const QRState* __restrict__ st, const double* __restrict__ t,
+                                   double* __restrict__ out) {
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= total) return;
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= g) lo = mid; else hi = mid - 1;
+  }
+  const PermScatter e = ps[lo];
+  int64_t x = g - prefix[lo];
+  int i = (int)(x % e.nrow), s = (int)(x / e.nrow);
+  int kq = st[lo].k;
+  if (i >= kq) return;
+  out[e.o0 + (int64_t)piv[e.col0 + i] * e.ri + (int64_t)s * e.rs] = t[e.t0 + i + (int64_t)s * kq];
+}
+
+// core = (Z_ab + Z_ba^T) / 2 (q x q), written into the QR work matrix.
+struct CoreProb {
+  int64_t zab, zba, out;
+  int q;
+};
+__global__ void core_kernel(const CoreProb* __restrict__ cp, int nprob, const double* __restrict__ Z,
+                            double* __restrict__ out) {
+  int p = blockIdx.y;
+  if (p >= nprob) return;
+  const CoreProb c = cp[p];
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= (int64_t)c.q * c.q) return;
+  int i = (int)(g % c.q), j = (int)(g / c.q);
+  out[c.out + g] = 0.5 * (Z[c.zab + i + (int64_t)j * c.q] + Z[c.zba + j + (int64_t)i * c.q]);
+}
+
+// trace of the leaf diagonal blocks: sum_p H[p, leafpos[p]]
+__global__ void diag_trace_kernel(const double* __restrict__ H, const int* __restrict__ leafpos, int64_t n,
+                                  int nl, double* __restrict__ part) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int64_t p = (int64_t)blockIdx.x * 256 + threadIdx.x; p < n; p += (int64_t)gridDim.x * 256)
+    s += H[p * nl + leafpos[p]];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+__global__ void sum_parts_kernel(const double* __restrict__ part, int n, double* __restrict__ out) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) s += part[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+__global__ void unit_cols_kernel(const int* __restrict__ leafpos, int64_t n, int nl, double* __restrict__ E) {
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n * nl) return;
+  int64_t p = g / nl;
+  int c = (int)(g % nl);
+  E[g] = (c == leafpos[p]) ? 1.0 : 0.0;
+}
+__global__ void axpby_kernel(double* __restrict__ y, const double* __restrict__ x, double a, double b, int64_t n) {
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < n) y[g] = a * y[g] + b * x[g];
+}
+
+// ----------------------------------------------------------------- host
+namespace {
+
+struct PBox {
+  int box, start, cnt, slot;
+  int nsib;             // number of siblings
+  int sib[3];           // indices (into the level's PBox list) of the siblings
+  int r[3];             // r_ab for each sibling (U_ab columns)
+  int ucol[3];          // column offset of U_ab within Ucat_a
+  int Ra;
+  int64_t ucat;         // offset of Ucat_a in the pool
+  int64_t pcol;         // column offset of this box's block in the P / Q temps
+};
+struct PPair {
+  int a, b;             // a < b (indices into the level's PBox list)
+  int sa, sb;           // position of b among a's siblings, a among b's
+  int64_t m;            // offset of M_ab (r_ab x r_ba, ld r_ab)
+};
+struct PLevel {
+  int lev = 0;
+  std::vector<PBox> bx;
+  std::vector<PPair> pr;
+  DBuf pool;            // Ucat blocks then M blocks
+  int64_t sumRa = 0;
+  GemmBatch gP, gQ, gY; // application of G^(lev)
+  bool active = false;
+};
+
+GemmDesc mk(int M, int N, int K, int8_t abase, int64_t a, int lda, int8_t ta, int8_t bbase, int64_t b, int ldb,
+            int8_t tb, int8_t cbase, int64_t c, int ldc, double alpha, double beta, int8_t triB = 0) {
+  GemmDesc g{};
+  g.M = M; g.N = N; g.K = K;
+  g.abase = abase; g.a = a; g.lda = lda; g.ta = ta;
+  g.bbase = bbase; g.b = b; g.ldb = ldb; g.tb = tb;
+  g.cbase = cbase; g.c = c; g.ldc = ldc;
+  g.alpha = alpha; g.beta = beta; g.triB = triB;
+  return g;
+}
+
+void run_gemm(const std::vector<GemmDesc>& d, double* p0, double* p1, double* p2, double* p3, cudaStream_t s,
+              int64_t sc0 = 1, int64_t sc1 = 1, int64_t sc2 = 1, int64_t sc3 = 1) {
+  if (d.empty()) return;
+  GemmBatch gb;
+  gb.build(d, s);
+  GemmBases b{};
+  b.p[0] = p0; b.p[1] = p1; b.p[2] = p2; b.p[3] = p3;
+  b.sc[0] = sc0; b.sc[1] = sc1; b.sc[2] = sc2; b.sc[3] = sc3;
+  b.alpha_scale = 1.0;
+  gb.run(b, s);
+}
+
+template <class T>
+void upload_prefix(DBuf& d, DBuf& pre, const std::vector<T>& v, const std::vector<int64_t>& prefix,
+                   cudaStream_t s) {
+  upload(d, v, s);
+  upload(pre, prefix, s);
+}
+
+// Y -= G^(lev) X for row-major (n x nc) X, Y.
+void apply_level(const PLevel& P, const double* X, double* Y, int nc, DBuf& tmp, cudaStream_t s) {
+  if (!P.active) return;
+  int64_t need = (int64_t)nc * 2 * std::max<int64_t>(1, P.sumRa);
+  if ((int64_t)tmp.bytes < need * (int64_t)sizeof(double)) tmp.alloc(need * sizeof(double), s);
+  GemmBases b{};
+  b.p[0] = const_cast<double*>(X); b.p[1] = Y; b.p[2] = P.pool.as<double>(); b.p[3] = tmp.as<double>();
+  b.sc[0] = nc; b.sc[1] = nc; b.sc[2] = 1; b.sc[3] = nc;
+  b.M = nc; b.ld = nc; b.alpha_scale = 1.0;
+  P.gP.run(b, s);
+  P.gQ.run(b, s);
+  P.gY.run(b, s);
+}
+
+}  // namespace
+
+double peel_trace(rsf_handle_s* F, rsf_handle_s* Fk, double tol, const rsf_opts& o, double* d_out) {
+  cudaStream_t s = F->stream;
+  TreeData& T = F->tree_raw->t;
+  const int64_t n = T.n;
+  const int L = T.L;
+  const int c_over = std::max(0, o.oversample);
+  DevStatus* dst = F->status.as<DevStatus>();
+  int64_t n64 = n;
+
+  // G application on row-major tree-order blocks
+  DBuf ga, gb2;
+  auto applyG = [&](const double* in, double* out, int q) {
+    if (!Fk) {
+      solve_rows(F, RSF_OP_INV, in, out, q);
+      return;
+    }
+    int64_t bytes = sizeof(double) * n64 * q;
+    if ((int64_t)ga.bytes < bytes) ga.alloc(bytes, s);
+    if ((int64_t)gb2.bytes < bytes) gb2.alloc(bytes, s);
+    solve_rows(Fk, RSF_OP_APPLY, in, ga.as<double>(), q);
+    solve_rows(F, RSF_OP_INV, ga.as<double>(), gb2.as<double>(), q);   // F^-1 F_k W
+    solve_rows(F, RSF_OP_INV, in, ga.as<double>(), q);
+    solve_rows(Fk, RSF_OP_APPLY, ga.as<double>(), out, q);             // F_k F^-1 W
+    LAUNCH(axpby_kernel, cdiv(n64 * q, 256), 256, 0, s, out, gb2.as<double>(), 0.5, 0.5, n64 * q);
+  };
+
+  std::vector<PLevel> levels(L + 1);
+  DBuf tmpP;  // P/Q temps for apply_level
+  std::vector<int> slotrow(n);
+  DBuf dslot;
+  int r_prev = 0;
+  int max_rank_seen = 0;
+
+  for (int lev = 1; lev <= L; lev++) {
+    PLevel& PL = levels[lev];
+    PL.lev = lev;
+    // boxes at this level with at least one sibling
+    std::vector<int> idx_of(T.level.size(), -1);
+    for (int b : T.by_level[lev]) {
+      int par = T.parent[b];
+      int nsib = 0;
+      for (int sl = 0; sl < 4; sl++) nsib += T.children[par][sl] >= 0;
+      if (nsib < 2) continue;
+      PBox pb{};
+      pb.box = b; pb.start = T.start[b]; pb.cnt = T.count[b]; pb.slot = T.slot[b];
+      idx_of[b] = (int)PL.bx.size();
+      PL.bx.push_back(pb);
+    }
+    if (PL.bx.empty()) continue;
+    PL.active = true;
+    for (auto& pb : PL.bx) {
+      int par = T.parent[pb.box];
+      pb.nsib = 0;
+      for (int sl = 0; sl < 4; sl++) {
+        int c = T.children[par][sl];
+        if (c >= 0 && c != pb.box) pb.sib[pb.nsib++] = idx_of[c];
+      }
+    }
+    for (int a = 0; a < (int)PL.bx.size(); a++)
+      for (int t = 0; t < PL.bx[a].nsib; t++) {
+        int b = PL.bx[a].sib[t];
+        if (a < b) {
+          PPair pp{};
+          pp.a = a; pp.b = b; pp.sa = t;
+          for (int u = 0; u < PL.bx[b].nsib; u++)
+            if (PL.bx[b].sib[u] == a) pp.sb = u;
+          PL.pr.push_back(pp);
+        }
+      }
+    const int nbx = (int)PL.bx.size();
+    // slot of every row at this level (-1 outside the level's boxes)
+    std::fill(slotrow.begin(), slotrow.end(), -1);
+    for (auto& pb : PL.bx)
+      for (int i = 0; i < pb.cnt; i++) slotrow[pb.start + i] = pb.slot;
+    upload(dslot, slotrow, s);
+
+    // ordered pairs list: (a, t) for each box a and sibling position t
+    struct OPair { int a, t; };
+    std::vector<OPair> op;
+    for (int a = 0; a < nbx; a++)
+      for (int t = 0; t < PL.bx[a].nsib; t++) op.push_back({a, t});
+    const int nop = (int)op.size();
+
+    int q = std::max(lev == 1 ? std::max(o.q0, 1) : 8, r_prev) + c_over;
+    std::vector<int> chunk_q, chunk_col0;
+    std::vector<DBuf> Wch, Ych;
+    std::vector<int> rank(nop, 0);
+    QRBatch qb;
+    DBuf Yorig, Yqr, Wbox;
+    std::vector<int64_t> yoff(nop + 1, 0), woff(nbx + 1, 0);
+    int qtot = 0;
+    while (true) {
+      int qc = q - qtot;
+      // new chunk
+      DBuf W, Y;
+      W.alloc(sizeof(double) * n64 * 4 * qc, s);
+      Y.alloc(sizeof(double) * n64 * 4 * qc, s);
+      LAUNCH(gen_w_kernel, cdiv(n64 * 4 * qc, 256), 256, 0, s, dslot.as<int>(), n64, qc, qtot, lev,
+             (unsigned long long)o.seed, W.as<double>());
+      applyG(W.as<double>(), Y.as<double>(), 4 * qc);
+      for (int m = 1; m < lev; m++) apply_level(levels[m], W.as<double>(), Y.as<double>(), 4 * qc, tmpP, s);
+      chunk_q.push_back(qc);
+      chunk_col0.push_back(qtot);
+      Wch.push_back(std::move(W));
+      Ych.push_back(std::move(Y));
+      qtot = q;
+      // gather Y_ab (column-major |I_a| x q) and W_a (|I_a| x q)
+      for (int i = 0; i < nop; i++) yoff[i + 1] = yoff[i] + (int64_t)PL.bx[op[i].a].cnt * q;
+      for (int a = 0; a < nbx; a++) woff[a + 1] = woff[a] + (int64_t)PL.bx[a].cnt * q;
+      Yorig.alloc(sizeof(double) * std::max<int64_t>(1, yoff[nop]), s);
+      Wbox.alloc(sizeof(double) * std::max<int64_t>(1, woff[nbx]), s);
+      for (size_t ch = 0; ch < Ych.size(); ch++) {
+        int qq = chunk_q[ch];
+        std::vector<ExtractProb> ey, ew;
+        std::vector<int64_t> py(1, 0), pw(1, 0);
+        for (int i = 0; i < nop; i++) {
+          const PBox& A = PL.bx[op[i].a];
+          const PBox& B = PL.bx[A.sib[op[i].t]];
+          ey.push_back({(int64_t)A.start, yoff[i], A.cnt, B.slot * qq});
+          py.push_back(py.back() + (int64_t)A.cnt * qq);
+        }
+        for (int a = 0; a < nbx; a++) {
+          const PBox& A = PL.bx[a];
+          ew.push_back({(int64_t)A.start, woff[a], A.cnt, A.slot * qq});
+          pw.push_back(pw.back() + (int64_t)A.cnt * qq);
+        }
+        DBuf d1, d2, d3, d4;
+        upload_prefix(d1, d2, ey, py, s);
+        LAUNCH(extract_kernel, cdiv(py.back(), 256), 256, 0, s, d1.as<ExtractProb>(), d2.as<int64_t>(), nop,
+               py.back(), qq, 4 * qq, chunk_col0[ch], Ych[ch].as<double>(), Yorig.as<double>());
+        upload_prefix(d3, d4, ew, pw, s);
+        LAUNCH(extract_kernel, cdiv(pw.back(), 256), 256, 0, s, d3.as<ExtractProb>(), d4.as<int64_t>(), nbx,
+               pw.back(), qq, 4 * qq, chunk_col0[ch], Wch[ch].as<double>(), Wbox.as<double>());
+      }
+      // rank-revealing QR of every Y_ab
+      Yqr.alloc(sizeof(double) * std::max<int64_t>(1, yoff[nop]), s);
+      RSF_CUDA(cudaMemcpyAsync(Yqr.p, Yorig.p, sizeof(double) * yoff[nop], cudaMemcpyDeviceToDevice, s));
+      std::vector<QRProb> qp(nop);
+      for (int i = 0; i < nop; i++) {
+        int rows = PL.bx[op[i].a].cnt;
+        qp[i] = QRProb{};
+        qp[i].m = rows; qp[i].c = q; qp[i].cpiv = q; qp[i].maxk = std::min(rows, q);
+        qp[i].lda = rows; qp[i].a = yoff[i]; qp[i].tol = tol;
+      }
+      qb = QRBatch();
+      qb.build(qp, s);
+      qb.run(Yqr.as<double>(), dst, lev, s);
+      std::vector<QRState> hst(nop);
+      d2h(hst.data(), qb.d_state(), nop, s);
+      sync(s);
+      int rmax = 0;
+      for (int i = 0; i < nop; i++) {
+        rank[i] = hst[i].k;
+        rmax = std::max(rmax, rank[i]);
+      }
+      if (rmax <= q - c_over || q >= (int)std::min<int64_t>(n64, 1 << 15)) break;
+      q = q + q;
+    }
+    Wch.clear();
+    Ych.clear();
+    // ordered-pair index of (a, t) and one-sided zero ranks: a block whose
+    // row or column space is empty is dropped in both directions
+    std::vector<int> opbase(nbx + 1, 0);
+    for (int a = 0; a < nbx; a++) opbase[a + 1] = opbase[a] + PL.bx[a].nsib;
+    auto opidx = [&](int a, int t) { return opbase[a] + t; };
+    for (const PPair& pp : PL.pr) {
+      int iab = opidx(pp.a, pp.sa), iba = opidx(pp.b, pp.sb);
+      if (rank[iab] == 0 || rank[iba] == 0) rank[iab] = rank[iba] = 0;
+    }
+    r_prev = 0;
+    for (int i = 0; i < nop; i++) r_prev = std::max(r_prev, rank[i]);
+    max_rank_seen = std::max(max_rank_seen, r_prev);
+
+    // ---- bases U_ab = Y_ab(:, piv[:r]) R11^-1, stored in Ucat_a
+    int64_t pool = 0;
+    PL.sumRa = 0;
+    for (int a = 0; a < nbx; a++) {
+      PBox& A = PL.bx[a];
+      A.Ra = 0;
+      A.ucat = pool;
+      A.pcol = PL.sumRa;
+      for (int t = 0; t < A.nsib; t++) { A.r[t] = 0; A.ucol[t] = 0; }
+    }
+    for (int i = 0; i < nop; i++) {
+      PBox& A = PL.bx[op[i].a];
+      A.r[op[i].t] = rank[i];
+    }
+    for (int a = 0; a < nbx; a++) {
+      PBox& A = PL.bx[a];
+      A.Ra = 0;
+      for (int t = 0; t < A.nsib; t++) { A.ucol[t] = A.Ra; A.Ra += A.r[t]; }
+      A.ucat = pool;
+      pool += (int64_t)A.cnt * A.Ra;
+      A.pcol = PL.sumRa;
+      PL.sumRa += A.Ra;
+    }
+    for (auto& pp : PL.pr) {
+      pp.m = pool;
+      pool += (int64_t)PL.bx[pp.a].r[pp.sa] * PL.bx[pp.b].r[pp.sb];
+    }
+    PL.pool.alloc(sizeof(double) * std::max<int64_t>(1, pool), s);
+    PL.pool.zero();
+    double* UP = PL.pool.as<double>();
+    {
+      // R11^-1 for each ordered pair (identity-mode back-substitution)
+      std::vector<TrsmProb> tp(nop);
+      std::vector<int64_t> roff(nop + 1, 0);
+      for (int i = 0; i < nop; i++) {
+        tp[i].nrhs = rank[i];
+        tp[i].rhs0 = -1;
+        tp[i].out0 = roff[i];
+        roff[i + 1] = roff[i] + (int64_t)rank[i] * rank[i];
+      }
+      DBuf Rinv, Ypiv;
+      Rinv.alloc(sizeof(double) * std::max<int64_t>(1, roff[nop]), s);
+      qr_trsm(qb, tp, nullptr, Yqr.as<double>(), Rinv.as<double>(), dst, lev, s);
+      std::vector<int64_t> poff(nop + 1, 0);
+      std::vector<PivGather> pg(nop);
+      for (int i = 0; i < nop; i++) {
+        int rows = PL.bx[op[i].a].cnt;
+        pg[i] = {yoff[i], poff[i], qb.colprefix_h[i], rows};
+        poff[i + 1] = poff[i] + (int64_t)rows * rank[i];
+      }
+      Ypiv.alloc(sizeof(double) * std::max<int64_t>(1, poff[nop]), s);
+      // pivgather iterates over rows x k (k <= q); prefix in units of rows * q
+      std::vector<int64_t> gpre(nop + 1, 0);
+      for (int i = 0; i < nop; i++) gpre[i + 1] = gpre[i] + (int64_t)pg[i].rows * rank[i];
+      if (gpre[nop] > 0) {
+        DBuf d1, d2;
+        upload_prefix(d1, d2, pg, gpre, s);
+        LAUNCH(pivgather_kernel, cdiv(gpre[nop], 256), 256, 0, s, d1.as<PivGather>(), d2.as<int64_t>(), nop,
+               gpre[nop], qb.d_piv(), qb.d_state(), Yorig.as<double>(), Ypiv.as<double>());
+      }
+      std::vector<GemmDesc> g;
+      for (int i = 0; i < nop; i++) {
+        const PBox& A = PL.bx[op[i].a];
+        int r = rank[i];
+        if (r == 0) continue;
+        // U = Ypiv (rows x r) * Rinv (r x r, upper)
+        g.push_back(mk(A.cnt, r, r, 0, poff[i], A.cnt, 0, 1, roff[i], r, 0, 2,
+                       A.ucat + (int64_t)A.ucol[op[i].t] * A.cnt, A.cnt, 1.0, 0.0, 2));
+      }
+      run_gemm(g, Ypiv.as<double>(), Rinv.as<double>(), UP, nullptr, s);
+    }
+    // ---- cores M_ab (Eq. (lowrankapprox))
+    {
+      // B_ab = W_a^T U_ab (q x r_ab) and Z_ab = W_a^T Y_ab (q x q)
+      std::vector<int64_t> boff(nop + 1, 0), zoff(nop + 1, 0);
+      for (int i = 0; i < nop; i++) {
+        boff[i + 1] = boff[i] + (int64_t)q * rank[i];
+        zoff[i + 1] = zoff[i] + (int64_t)q * q;
+      }
+      DBuf Bm, Zm;
+      Bm.alloc(sizeof(double) * std::max<int64_t>(1, boff[nop]), s);
+      Zm.alloc(sizeof(double) * std::max<int64_t>(1, zoff[nop]), s);
+      std::vector<GemmDesc> g1, g2;
+      for (int i = 0; i < nop; i++) {
+        const PBox& A = PL.bx[op[i].a];
+        int a = op[i].a;
+        if (rank[i] > 0)
+          g1.push_back(mk(q, rank[i], A.cnt, 0, woff[a], A.cnt, 1, 1, A.ucat + (int64_t)A.ucol[op[i].t] * A.cnt,
+                          A.cnt, 0, 2, boff[i], q, 1.0, 0.0));
+        g2.push_back(mk(q, q, A.cnt, 0, woff[a], A.cnt, 1, 3, yoff[i], A.cnt, 0, 2, zoff[i], q, 1.0, 0.0));
+      }
+      // bases: 0 = Wbox, 1 = U pool, 2 = out (B or Z), 3 = Yorig
+      run_gemm(g1, Wbox.as<double>(), UP, Bm.as<double>(), Yorig.as<double>(), s);
+      run_gemm(g2, Wbox.as<double>(), UP, Zm.as<double>(), Yorig.as<double>(), s);
+      // X1 = (B_ab)^+ core  via QR of [B_ab | core]  (q x (r_ab + q))
+      const int npr = (int)PL.pr.size();
+      std::vector<QRProb> q1;
+      std::vector<CopyProb> cp1;
+      std::vector<CoreProb> cores;
+      std::vector<int> live;
+      int64_t qpool = 0;
+      for (int p = 0; p < npr; p++) {
+        const PPair& pp = PL.pr[p];
+        int iab = opidx(pp.a, pp.sa), iba = opidx(pp.b, pp.sb);
+        int rab = rank[iab], rba = rank[iba];
+        if (rab == 0 || rba == 0) continue;
+        live.push_back(p);
+        QRProb x{};
+        x.m = q; x.c = rab + q; x.cpiv = rab; x.maxk = rab; x.lda = q; x.a = qpool; x.tol = 0.0;
+        cp1.push_back({q, rab, q, q, boff[iab], qpool, 0});
+        cores.push_back({zoff[iab], zoff[iba], qpool + (int64_t)q * rab, q});
+        qpool += (int64_t)q * (rab + q);
+        q1.push_back(x);
+      }
+      if (!live.empty()) {
+        DBuf W1;
+        W1.alloc(sizeof(double) * qpool, s);
+        copy_batched(cp1, Bm.as<double>(), W1.as<double>(), s);
+        {
+          DBuf dc;
+          upload(dc, cores, s);
+          dim3 grid(cdiv((int64_t)q * q, 256), (unsigned)cores.size());
+          LAUNCH(core_kernel, grid, 256, 0, s, dc.as<CoreProb>(), (int)cores.size(), Zm.as<double>(), W1.as<double>());
+        }
+        QRBatch qx;
+        qx.build(q1, s);
+        qx.run(W1.as<double>(), dst, lev, s);
+        std::vector<int> rhs;
+        std::vector<TrsmProb> tp(live.size());
+        std::vector<int64_t> toff(live.size() + 1, 0);
+        std::vector<PermScatter> ps(live.size());
+        std::vector<int64_t> xoff(live.size() + 1, 0), spre(live.size() + 1, 0);
+        for (size_t j = 0; j < live.size(); j++) {
+          const PPair& pp = PL.pr[live[j]];
+          int rab = rank[opidx(pp.a, pp.sa)];
+          tp[j].nrhs = q;
+          tp[j].rhs0 = (int64_t)rhs.size();
+          tp[j].out0 = toff[j];
+          for (int t = 0; t < q; t++) rhs.push_back(rab + t);
+          toff[j + 1] = toff[j] + (int64_t)rab * q;
+          // X1 (r_ab x q, ld r_ab): X1[piv[i], s] = t[i, s]
+          ps[j] = {toff[j], xoff[j], qx.colprefix_h[j], rab, q, 1, rab};
+          xoff[j + 1] = xoff[j] + (int64_t)rab * q;
+          spre[j + 1] = spre[j] + (int64_t)rab * q;
+        }
+        DBuf drhs, tout, X1;
+        upload(drhs, rhs, s);
+        tout.alloc(sizeof(double) * std::max<int64_t>(1, toff.back()), s);
+        X1.alloc(sizeof(double) * std::max<int64_t>(1, xoff.back()), s);
+        X1.zero();
+        qr_trsm(qx, tp, drhs.as<int>(), W1.as<double>(), tout.as<double>(), dst, lev, s);
+        {
+          DBuf d1, d2;
+          upload_prefix(d1, d2, ps, spre, s);
+          LAUNCH(permscatter_kernel, cdiv(spre.back(), 256), 256, 0, s, d1.as<PermScatter>(), d2.as<int64_t>(),
+                 (int)ps.size(), spre.back(), qx.d_piv(), qx.d_state(), tout.as<double>(), X1.as<double>());
+        }
+        // M_ab^T = (B_ba)^+ X1^T via QR of [B_ba | X1^T]  (q x (r_ba + r_ab))
+        std::vector<QRProb> q2;
+        std::vector<CopyProb> cp2;
+        int64_t qpool2 = 0;
+        for (size_t j = 0; j < live.size(); j++) {
+          const PPair& pp = PL.pr[live[j]];
+          int iab = opidx(pp.a, pp.sa), iba = opidx(pp.b, pp.sb);
+          int rab = rank[iab], rba = rank[iba];
+          QRProb x{};
+          x.m = q; x.c = rba + rab; x.cpiv = rba; x.maxk = rba; x.lda = q; x.a = qpool2; x.tol = 0.0;
+          cp2.push_back({q, rba, q, q, boff[iba], qpool2, 0});
+          qpool2 += (int64_t)q * (rba + rab);
+          q2.push_back(x);
+        }
+        DBuf W2;
+        W2.alloc(sizeof(double) * qpool2, s);
+        copy_batched(cp2, Bm.as<double>(), W2.as<double>(), s);
+        {
+          std::vector<CopyProb> cpx;
+          int64_t off2 = 0;
+          for (size_t j = 0; j < live.size(); j++) {
+            const PPair& pp = PL.pr[live[j]];
+            int rab = rank[opidx(pp.a, pp.sa)], rba = rank[opidx(pp.b, pp.sb)];
+            // X1^T (q x r_ab) into columns r_ba.. of the work matrix
+            cpx.push_back({q, rab, rab, q, xoff[j], off2 + (int64_t)q * rba, 1});
+            off2 += (int64_t)q * (rba + rab);
+          }
+          copy_batched(cpx, X1.as<double>(), W2.as<double>(), s);
+        }
+        QRBatch qy;
+        qy.build(q2, s);
+        qy.run(W2.as<double>(), dst, lev, s);
+        std::vector<int> rhs2;
+        std::vector<TrsmProb> tp2(live.size());
+        std::vector<int64_t> toff2(live.size() + 1, 0), spre2(live.size() + 1, 0);
+        std::vector<PermScatter> ps2(live.size());
+        for (size_t j = 0; j < live.size(); j++) {
+          const PPair& pp = PL.pr[live[j]];
+          int rab = rank[opidx(pp.a, pp.sa)], rba = rank[opidx(pp.b, pp.sb)];
+          tp2[j].nrhs = rab;
+          tp2[j].rhs0 = (int64_t)rhs2.size();
+          tp2[j].out0 = toff2[j];
+          for (int t = 0; t < rab; t++) rhs2.push_back(rba + t);
+          toff2[j + 1] = toff2[j] + (int64_t)rba * rab;
+          // M^T[piv[i], s] = t[i, s]  ->  M (r_ab x r_ba, ld r_ab): M[s, piv[i]]
+          ps2[j] = {toff2[j], pp.m, qy.colprefix_h[j], rba, rab, rab, 1};
+          spre2[j + 1] = spre2[j] + (int64_t)rba * rab;
+        }
+        DBuf drhs2, tout2;
+        upload(drhs2, rhs2, s);
+        tout2.alloc(sizeof(double) * std::max<int64_t>(1, toff2.back()), s);
+        qr_trsm(qy, tp2, drhs2.as<int>(), W2.as<double>(), tout2.as<double>(), dst, lev, s);
+        {
+          DBuf d1, d2;
+          upload_prefix(d1, d2, ps2, spre2, s);
+          LAUNCH(permscatter_kernel, cdiv(spre2.back(), 256), 256, 0, s, d1.as<PermScatter>(), d2.as<int64_t>(),
+                 (int)ps2.size(), spre2.back(), qy.d_piv(), qy.d_state(), tout2.as<double>(), UP);
+        }
+      }
+    }
+    // ---- application descriptors of G^(lev) (bases 0 X, 1 Y, 2 pool, 3 temp)
+    {
+      std::vector<GemmDesc> gP, gQ, gY;
+      for (int a = 0; a < nbx; a++) {
+        const PBox& A = PL.bx[a];
+        if (A.Ra == 0) continue;
+        // P_a^T (nc x Ra) = X(I_a)^T Ucat_a
+        gP.push_back(mk(-1, A.Ra, A.cnt, 0, A.start, -1, 0, 2, A.ucat, A.cnt, 0, 3, A.pcol, -1, 1.0, 0.0));
+        // Y(I_a)^T -= Q_a^T Ucat_a^T, Q stored after all P blocks
+        gY.push_back(mk(-1, A.cnt, A.Ra, 3, PL.sumRa + A.pcol, -1, 0, 2, A.ucat, A.cnt, 1, 1, A.start, -1, -1.0,
+                        1.0));
+      }
+      for (const PPair& pp : PL.pr) {
+        const PBox& A = PL.bx[pp.a];
+        const PBox& B = PL.bx[pp.b];
+        int rab = A.r[pp.sa], rba = B.r[pp.sb];
+        if (rab == 0 || rba == 0) continue;
+        // Q_ab^T (nc x r_ab) = P_(b->a)^T (nc x r_ba) M_ab^T
+        gQ.push_back(mk(-1, rab, rba, 3, B.pcol + B.ucol[pp.sb], -1, 0, 2, pp.m, rab, 1, 3,
+                        PL.sumRa + A.pcol + A.ucol[pp.sa], -1, 1.0, 0.0));
+        // Q_ba^T (nc x r_ba) = P_(a->b)^T (nc x r_ab) M_ab
+        gQ.push_back(mk(-1, rba, rab, 3, A.pcol + A.ucol[pp.sa], -1, 0, 2, pp.m, rab, 0, 3,
+                        PL.sumRa + B.pcol + B.ucol[pp.sb], -1, 1.0, 0.0));
+      }
+      PL.gP.build(gP, s);
+      PL.gQ.build(gQ, s);
+      PL.gY.build(gY, s);
+    }
+    sync(s);
+  }
+
+  // ---- extraction: H = (G - sum_m G^(m)) E, trace of the leaf blocks
+  const int nl = std::max(1, T.max_leaf);
+  DBuf dlp;
+  upload(dlp, T.leafpos, s);
+  DBuf E, H;
+  E.alloc(sizeof(double) * n64 * nl, s);
+  H.alloc(sizeof(double) * n64 * nl, s);
+  LAUNCH(unit_cols_kernel, cdiv(n64 * nl, 256), 256, 0, s, dlp.as<int>(), n64, nl, E.as<double>());
+  applyG(E.as<double>(), H.as<double>(), nl);
+  for (int m = 1; m <= L; m++) apply_level(levels[m], E.as<double>(), H.as<double>(), nl, tmpP, s);
+  int nb = (int)std::min<int64_t>(1024, std::max<int64_t>(1, cdiv(n64, 256)));
+  DBuf part, res;
+  part.alloc(sizeof(double) * nb, s);
+  res.alloc(sizeof(double), s);
+  LAUNCH(diag_trace_kernel, nb, 256, 0, s, H.as<double>(), dlp.as<int>(), n64, nl, part.as<double>());
+  double* outp = d_out ? d_out : res.as<double>();
+  LAUNCH(sum_parts_kernel, 1, 256, 0, s, part.as<double>(), nb, outp);
+  double tr = 0;
+  d2h(&tr, outp, 1, s);
+  sync(s);
+  (void)max_rank_seen;
+  return tr;
+}
+
+}  // namespace rsf

@@ -1,0 +1,209 @@
+// Multi-right-hand-side application of the factorization (Sec. 2.3.2):
+// F = Q D Q^T with Q = prod_l prod_I L_I U_I (leaf level leftmost) and D the
+// block-diagonal of the X_RR blocks and the root block.
+//
+//   Q^-1 (leaves first):   x_R -= T^T x_S ;  x_S -= E x_R
+//   Q^-T (root side first): x_R -= E^T x_S ;  x_S -= T x_R
+//   Q^T  (leaves first):   x_S += T x_R   ;  x_R += E^T x_S
+//   Q    (root side first): x_S += E x_R   ;  x_R += T^T x_S
+//   F^-1 = Q^-T D^-1 Q^-1, F = Q D Q^T, F^1/2 = Q C, F^-1/2 = C^-1 Q^-1.
+//
+// Work buffers: one row-major (rows x q) block per level holding the active
+// DOFs of that level in [S, R] order per box; the skeleton rows move between
+// levels through the gather map built with the factorization.  Every box
+// operation of a level is one batched GEMM launch.
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace rsf {
+
+// X_lev[row] = src >= 0 ? X_up[src] : in[-(1 + src)]   (row length q)
+__global__ void gather_rows_kernel(const int* __restrict__ src, int64_t nrows, int q,
+                                   const double* __restrict__ child, const double* __restrict__ in,
+                                   double* __restrict__ out) {
+  int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  int lane = threadIdx.x & 31;
+  if (row >= nrows) return;
+  int s = src[row];
+  const double* from = s >= 0 ? child + (int64_t)s * q : in + (int64_t)(-(1 + s)) * q;
+  double* to = out + row * q;
+  for (int c = lane; c < q; c += 32) to[c] = from[c];
+}
+
+// Inverse of the gather: rows with src >= 0 go back to the level below, leaf
+// rows to the output.
+__global__ void scatter_rows_kernel(const int* __restrict__ src, int64_t nrows, int q,
+                                    const double* __restrict__ lev, double* __restrict__ child,
+                                    double* __restrict__ out) {
+  int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  int lane = threadIdx.x & 31;
+  if (row >= nrows) return;
+  int s = src[row];
+  double* to = s >= 0 ? child + (int64_t)s * q : out + (int64_t)(-(1 + s)) * q;
+  const double* from = lev + row * q;
+  for (int c = lane; c < q; c += 32) to[c] = from[c];
+}
+
+// Copy the R rows (ranges) of a level between two buffers.
+__global__ void copy_ranges_kernel(const int64_t* __restrict__ rr, int nrr, int q,
+                                   const double* __restrict__ from, double* __restrict__ to) {
+  int i = blockIdx.x;
+  if (i >= nrr) return;
+  int64_t r0 = rr[2 * i], nr = rr[2 * i + 1];
+  const double* f = from + r0 * q;
+  double* t = to + r0 * q;
+  for (int64_t e = threadIdx.x; e < nr * q; e += blockDim.x) t[e] = f[e];
+}
+
+static void run_level_gemm(const GemmBatch& g, double* X, double* tmp, double* pool, int q, double alpha,
+                           cudaStream_t s) {
+  GemmBases b{};
+  b.p[0] = X; b.p[1] = tmp; b.p[2] = pool; b.p[3] = nullptr;
+  b.sc[0] = q; b.sc[1] = q; b.sc[2] = 1; b.sc[3] = 1;
+  b.M = q; b.ld = q; b.alpha_scale = alpha;
+  g.run(b, s);
+}
+
+void solve_rows(rsf_handle_s* h, int op, const double* in, double* out, int q) {
+  cudaStream_t s = h->stream;
+  const int L = (int)h->levels.size() - 1;
+  RSF_CHECK(q >= 1, RSF_EINVAL, "nrhs must be >= 1");
+  if (!h->spd) RSF_CHECK(op == RSF_OP_APPLY, RSF_EINVAL, "only APPLY is defined for a derivative factorization");
+  // buffers
+  std::vector<int64_t> off(L + 2, 0);
+  int64_t maxrows = 0;
+  for (int l = 0; l <= L; l++) {
+    off[l + 1] = off[l] + h->levels[l].nrows;
+    maxrows = std::max(maxrows, h->levels[l].nrows);
+  }
+  DBuf X, tmp;
+  X.alloc(sizeof(double) * std::max<int64_t>(1, off[L + 1]) * q, s);
+  tmp.alloc(sizeof(double) * std::max<int64_t>(1, maxrows) * q, s);
+  auto Xl = [&](int l) { return X.as<double>() + off[l] * q; };
+
+  int up = 0, down = 0, mid = 0;  // up/down: 0 none, 1 inverse, 2 forward
+  switch (op) {
+    case RSF_OP_INV: up = 1; down = 1; mid = 0; break;
+    case RSF_OP_APPLY: up = 2; down = 2; mid = 1; break;
+    case RSF_OP_SQRT: up = 0; down = 2; mid = 2; break;
+    case RSF_OP_SQRT_T: up = 2; down = 0; mid = 3; break;
+    case RSF_OP_INV_SQRT: up = 1; down = 0; mid = 4; break;
+    case RSF_OP_INV_SQRT_T: up = 0; down = 1; mid = 5; break;
+    default: fail(RSF_EINVAL, "unknown op");
+  }
+  // upward sweep
+  for (int l = L; l >= 0; l--) {
+    LevelData& Lv = h->levels[l];
+    if (Lv.nrows == 0) continue;
+    const double* child = (l < L) ? Xl(l + 1) : nullptr;
+    LAUNCH(gather_rows_kernel, cdiv(Lv.nrows, 8), 256, 0, s, Lv.src.as<int>(), Lv.nrows, q, child, in, Xl(l));
+    if (l == 0) break;
+    double* F = Lv.fpool.as<double>();
+    if (up == 1) {
+      run_level_gemm(Lv.gRS_T, Xl(l), tmp.as<double>(), F, q, -1.0, s);
+      run_level_gemm(Lv.gSR_Et, Xl(l), tmp.as<double>(), F, q, -1.0, s);
+    } else if (up == 2) {
+      run_level_gemm(Lv.gSR_Tt, Xl(l), tmp.as<double>(), F, q, 1.0, s);
+      run_level_gemm(Lv.gRS_E, Xl(l), tmp.as<double>(), F, q, 1.0, s);
+    }
+  }
+  // block-diagonal middle factor on the R rows of every level
+  for (int l = 0; l <= L; l++) {
+    LevelData& Lv = h->levels[l];
+    if (Lv.nrr == 0) continue;
+    double* F = Lv.fpool.as<double>();
+    double* x = Xl(l);
+    double* t = tmp.as<double>();
+    auto prod = [&](int v, bool from_tmp) {
+      // out = in * op(B): descriptors read base 0 and write base 1
+      GemmBases b{};
+      b.p[0] = from_tmp ? t : x; b.p[1] = from_tmp ? x : t; b.p[2] = F; b.p[3] = nullptr;
+      b.sc[0] = q; b.sc[1] = q; b.sc[2] = 1; b.sc[3] = 1;
+      b.M = q; b.ld = q; b.alpha_scale = 1.0;
+      Lv.gMid[v].run(b, s);
+    };
+    auto copy_to_tmp = [&]() {
+      LAUNCH(copy_ranges_kernel, Lv.nrr, 256, 0, s, Lv.rr.as<int64_t>(), Lv.nrr, q, x, t);
+    };
+    switch (mid) {
+      case 0: prod(0, false); prod(1, true); break;             // D^-1 = Cinv^T Cinv
+      case 1:
+        if (h->spd) { prod(2, false); prod(3, true); }           // D = C C^T
+        else { copy_to_tmp(); prod(4, true); }                   // D = X_RR
+        break;
+      case 2: copy_to_tmp(); prod(3, true); break;               // C
+      case 3: copy_to_tmp(); prod(2, true); break;               // C^T
+      case 4: copy_to_tmp(); prod(0, true); break;               // C^-1
+      case 5: copy_to_tmp(); prod(1, true); break;               // C^-T
+    }
+  }
+  // downward sweep
+  for (int l = 0; l <= L; l++) {
+    LevelData& Lv = h->levels[l];
+    if (Lv.nrows == 0) continue;
+    double* F = Lv.fpool.as<double>();
+    if (l > 0) {
+      if (down == 1) {
+        run_level_gemm(Lv.gRS_E, Xl(l), tmp.as<double>(), F, q, -1.0, s);
+        run_level_gemm(Lv.gSR_Tt, Xl(l), tmp.as<double>(), F, q, -1.0, s);
+      } else if (down == 2) {
+        run_level_gemm(Lv.gSR_Et, Xl(l), tmp.as<double>(), F, q, 1.0, s);
+        run_level_gemm(Lv.gRS_T, Xl(l), tmp.as<double>(), F, q, 1.0, s);
+      }
+    }
+    double* child = (l < L) ? Xl(l + 1) : nullptr;
+    LAUNCH(scatter_rows_kernel, cdiv(Lv.nrows, 8), 256, 0, s, Lv.src.as<int>(), Lv.nrows, q, Xl(l), child, out);
+  }
+}
+
+// ------------------------------------------------------------- reductions
+__global__ void dot_partial_kernel(const double* __restrict__ a, const double* __restrict__ b, int64_t n,
+                                   double* __restrict__ part) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256)
+    s = fma(a[i], b[i], s);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+__global__ void sum_kernel(const double* __restrict__ part, int n, double* __restrict__ out) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) s += part[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+void dot_into(const double* a, const double* b, int64_t n, double* d_out, cudaStream_t s) {
+  int nb = (int)std::min<int64_t>(1024, std::max<int64_t>(1, cdiv(n, 256)));
+  DBuf part;
+  part.alloc(sizeof(double) * nb, s);
+  LAUNCH(dot_partial_kernel, nb, 256, 0, s, a, b, n, part.as<double>());
+  LAUNCH(sum_kernel, 1, 256, 0, s, part.as<double>(), nb, d_out);
+}
+
+double dot_device(const double* a, const double* b, int64_t n, cudaStream_t s) {
+  int nb = (int)std::min<int64_t>(1024, std::max<int64_t>(1, cdiv(n, 256)));
+  DBuf part, res;
+  part.alloc(sizeof(double) * nb, s);
+  res.alloc(sizeof(double), s);
+  LAUNCH(dot_partial_kernel, nb, 256, 0, s, a, b, n, part.as<double>());
+  LAUNCH(sum_kernel, 1, 256, 0, s, part.as<double>(), nb, res.as<double>());
+  double h = 0;
+  d2h(&h, res.as<double>(), 1, s);
+  sync(s);
+  return h;
+}
+
+}  // namespace rsf
