@@ -178,6 +178,16 @@ rsf_status rsf_get_info(rsf_handle h, rsf_info_t* info);
  * (host-side count of launches issued). */
 int64_t rsf_launch_count(int reset);
 
+/* Kernel timing for reporting: while enabled, the library records CUDA events
+ * on the launching stream around its batched GEMM (category 0), pivoted-QR
+ * update (1) and pivot (2) launches, with each launch's algorithmic fp64
+ * flops and bytes.  rsf_profile_read returns the totals of a category since
+ * the last reset (launches, summed event time in ms, flops, bytes; any output
+ * may be NULL) and synchronises the recorded events. */
+void rsf_profile_enable(int on);
+rsf_status rsf_profile_read(int category, int reset, int64_t* launches, double* ms,
+                            double* flops, double* bytes);
+
 /* Frees a handle and all its device memory.  Safe on NULL. */
 void rsf_destroy(rsf_handle h);
 

@@ -25,7 +25,7 @@ STATUS = {0: "RSF_OK", 1: "RSF_EINVAL", 2: "RSF_ENOMEM", 3: "RSF_ENOTPD",
 EXPORTS = ["rsf_opts_default", "rsf_last_error", "rsf_tree_build", "rsf_tree_destroy",
            "rsf_build", "rsf_build_on_tree", "rsf_logdet", "rsf_solve", "rsf_peel_trace",
            "gp_loglik", "gp_score", "gp_loglik_and_score", "rsf_get_info",
-           "rsf_launch_count", "rsf_destroy"]
+           "rsf_launch_count", "rsf_profile_enable", "rsf_profile_read", "rsf_destroy"]
 
 
 class RsfKernel(C.Structure):
@@ -80,13 +80,16 @@ def lib():
         L.gp_loglik_and_score.argtypes = [vp, vp, i64, C.POINTER(RsfKernel), dp, C.c_double,
                                           C.c_double, C.POINTER(RsfOpts), vp, dp, dp, dp]
         L.rsf_get_info.argtypes = [vp, C.POINTER(RsfInfo)]
+        L.rsf_profile_enable.argtypes = [ip]
+        L.rsf_profile_enable.restype = None
+        L.rsf_profile_read.argtypes = [ip, ip, C.POINTER(C.c_int64), dp, dp, dp]
         L.rsf_launch_count.argtypes = [ip]
         L.rsf_launch_count.restype = C.c_int64
         L.rsf_destroy.argtypes = [vp]
         L.rsf_destroy.restype = None
         for name in EXPORTS:
             if name not in ("rsf_opts_default", "rsf_last_error", "rsf_tree_destroy",
-                            "rsf_launch_count", "rsf_destroy"):
+                            "rsf_launch_count", "rsf_profile_enable", "rsf_destroy"):
                 getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -125,6 +128,23 @@ def _theta(theta):
 
 def launch_count(reset=False) -> int:
     return int(lib().rsf_launch_count(1 if reset else 0))
+
+
+PROF_GEMM, PROF_QR_UPDATE, PROF_QR_PIVOT = 0, 1, 2
+
+
+def profile(enable: bool) -> None:
+    """Turns the library's per-kernel event timing on or off."""
+    lib().rsf_profile_enable(1 if enable else 0)
+
+
+def profile_read(category: int, reset: bool = False) -> dict:
+    """Totals of one kernel category: launches, ms (summed CUDA-event time on
+    the launching stream), algorithmic flops and bytes."""
+    n = C.c_int64()
+    ms, fl, by = C.c_double(), C.c_double(), C.c_double()
+    _check(lib().rsf_profile_read(category, 1 if reset else 0, C.byref(n), C.byref(ms), C.byref(fl), C.byref(by)))
+    return dict(launches=n.value, ms=ms.value, flops=fl.value, bytes=by.value)
 
 
 class Tree:

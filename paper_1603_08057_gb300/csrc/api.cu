@@ -23,6 +23,80 @@ struct Exception {
 
 void set_error(const std::string& msg) { g_err = msg; }
 
+// ------------------------------------------------------ kernel timing
+namespace {
+struct ProfRec {
+  cudaEvent_t a, b;
+  int cat;
+  double flops, bytes;
+};
+bool g_prof_on = false;
+int g_prof_next = 0;
+std::map<int, ProfRec> g_prof_open;   // begun, not yet ended (token -> record)
+std::vector<ProfRec> g_prof_done;     // ended, not yet read
+std::vector<cudaEvent_t> g_event_pool;
+struct ProfAcc {
+  int64_t launches = 0;
+  double ms = 0, flops = 0, bytes = 0;
+} g_prof_acc[PROF_NCAT];
+
+cudaEvent_t get_event() {
+  if (!g_event_pool.empty()) {
+    cudaEvent_t e = g_event_pool.back();
+    g_event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  RSF_CUDA(cudaEventCreate(&e));
+  return e;
+}
+void prof_drain() {
+  for (auto& r : g_prof_done) {
+    float ms = 0;
+    if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      ProfAcc& acc = g_prof_acc[r.cat];
+      acc.launches++;
+      acc.ms += ms;
+      acc.flops += r.flops;
+      acc.bytes += r.bytes;
+    }
+    g_event_pool.push_back(r.a);
+    g_event_pool.push_back(r.b);
+  }
+  g_prof_done.clear();
+}
+}  // namespace
+
+bool prof_enabled() { return g_prof_on; }
+
+bool verbose() {
+  static const bool v = std::getenv("RSF_VERBOSE") != nullptr;
+  return v;
+}
+
+int prof_begin(cudaStream_t s) {
+  if (!g_prof_on) return -1;
+  if (g_prof_done.size() > 20000) prof_drain();
+  ProfRec r{get_event(), get_event(), -1, 0, 0};
+  RSF_CUDA(cudaEventRecord(r.a, s));
+  int tok = g_prof_next++ & 0x3fffffff;
+  g_prof_open[tok] = r;
+  return tok;
+}
+
+void prof_end(int token, cudaStream_t s, int cat, double flops, double bytes) {
+  if (token < 0) return;
+  auto it = g_prof_open.find(token);
+  if (it == g_prof_open.end()) return;
+  ProfRec r = it->second;
+  g_prof_open.erase(it);
+  RSF_CUDA(cudaEventRecord(r.b, s));
+  r.cat = cat;
+  r.flops = flops;
+  r.bytes = bytes;
+  g_prof_done.push_back(r);
+}
+
 void fail(rsf_status code, const std::string& msg) { throw Exception{code, msg}; }
 
 // Trees handed out through the C ABI; handles share ownership.
@@ -86,6 +160,20 @@ __global__ void sum_logdet_kernel(const double* __restrict__ parts, int n, doubl
   if (threadIdx.x == 0) *out = red[0];
 }
 
+// Two trees are interchangeable when their box tables and point orders agree
+// (e.g. built twice from the same points).
+static bool same_tree(rsf_tree_s* a, rsf_tree_s* b) {
+  if (a == b) return true;
+  const TreeData &A = a->t, &B = b->t;
+  if (A.n != B.n || A.start != B.start || A.count != B.count || A.level != B.level) return false;
+  std::vector<int> pa(A.n), pb(B.n);
+  d2h(pa.data(), A.perm.as<int>(), A.n, A.stream);
+  d2h(pb.data(), B.perm.as<int>(), B.n, B.stream);
+  sync(A.stream);
+  sync(B.stream);
+  return pa == pb;
+}
+
 static rsf_opts resolve_opts(const rsf_opts* o) {
   rsf_opts r;
   rsf_opts_default(&r);
@@ -120,7 +208,9 @@ static rsf_handle_s* make_handle(std::shared_ptr<rsf_tree_s> tree, const rsf_ker
   h->kp.s2 = theta[1];
   h->kp.nug = theta[2];
   h->kp.which = which;
+  int tk = prof_begin(h->stream);
   factorize(h.get());
+  prof_end(tk, h->stream, PROF_FACTOR, h->flops, 0);
   check_status(h.get());
   return h.release();
 }
@@ -244,7 +334,7 @@ rsf_status rsf_peel_trace(rsf_handle F, rsf_handle Fk, double tol_peel, const rs
   API_BEGIN
   RSF_CHECK(F && trace, RSF_EINVAL, "F and trace must not be NULL");
   RSF_CHECK(F->spd, RSF_EINVAL, "F must factor Sigma");
-  RSF_CHECK(!Fk || Fk->tree_raw == F->tree_raw, RSF_EINVAL, "F and Fk must share a tree");
+  RSF_CHECK(!Fk || same_tree(Fk->tree_raw, F->tree_raw), RSF_EINVAL, "F and Fk must be built on the same tree");
   RSF_CHECK(tol_peel > 0.0 && tol_peel < 1.0, RSF_EINVAL, "tol_peel must be in (0, 1)");
   rsf_opts o = resolve_opts(opts);
   double t = peel_trace(F, Fk, tol_peel, o, nullptr);
@@ -359,6 +449,24 @@ rsf_status rsf_get_info(rsf_handle h, rsf_info_t* info) {
   info->factor_entries = h->factor_entries;
   info->flops = h->flops;
   info->kernel_evals = h->kevals;
+  API_END
+}
+
+void rsf_profile_enable(int on) {
+  if (!on) prof_drain();
+  g_prof_on = on != 0;
+}
+
+rsf_status rsf_profile_read(int category, int reset, int64_t* launches, double* ms, double* flops, double* bytes) {
+  API_BEGIN
+  RSF_CHECK(category >= 0 && category < PROF_NCAT, RSF_EINVAL, "unknown profile category");
+  prof_drain();
+  ProfAcc& a = g_prof_acc[category];
+  if (launches) *launches = a.launches;
+  if (ms) *ms = a.ms;
+  if (flops) *flops = a.flops;
+  if (bytes) *bytes = a.bytes;
+  if (reset) a = ProfAcc{};
   API_END
 }
 

@@ -47,6 +47,21 @@ extern int64_t g_launches;
     }                                                                         \
   } while (0)
 
+// Optional per-category kernel timing: CUDA events recorded on the launching
+// stream around instrumented launches, with the launch's algorithmic flops.
+enum ProfCat {
+  PROF_GEMM = 0, PROF_QR_UPDATE = 1, PROF_QR_PIVOT = 2,
+  // phases (spans of many launches)
+  PROF_PEEL_APPLY = 3, PROF_PEEL_SUB = 4, PROF_PEEL_QR = 5, PROF_PEEL_REST = 6, PROF_FACTOR = 7,
+  PROF_NCAT = 8
+};
+// Diagnostics to stderr when the environment variable RSF_VERBOSE is set.
+bool verbose();
+bool prof_enabled();
+// Returns a token for prof_end (or -1 when profiling is off).
+int prof_begin(cudaStream_t s);
+void prof_end(int token, cudaStream_t s, int cat, double flops, double bytes);
+
 // Device status word written by kernels on numerical failure:
 // [0] code (rsf_status), [1] level, [2] box, [3] detail.
 struct DevStatus {

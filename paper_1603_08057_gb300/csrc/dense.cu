@@ -115,9 +115,30 @@ void GemmBatch::build(const std::vector<GemmDesc>& d, cudaStream_t s) {
   std::vector<int> pre(nprob + 1, 0);
   maxM = 0;
   anyLaunchM = false;
+  fixedMNK = launchNK = fixedBytes = launchBytesPerM = launchBytes0 = 0;
   for (int i = 0; i < nprob; i++) {
     pre[i + 1] = pre[i] + std::max(0, cdiv(d[i].N, BN));
     if (d[i].M < 0) anyLaunchM = true; else maxM = std::max(maxM, d[i].M);
+    // nonzero (k, n) pairs of op(B) and the computed part of C
+    double N = d[i].N, K = d[i].K, nk;
+    if (d[i].triB == 1) {          // op(B)[k, n] != 0 for k >= n
+      double m = std::min(N, K);
+      nk = m * K - m * (m - 1) / 2;
+    } else if (d[i].triB == 2) {   // op(B)[k, n] != 0 for k <= n
+      double m = std::min(N, K);
+      nk = m * (m + 1) / 2 + (N - m) * K;
+    } else {
+      nk = N * K;
+    }
+    double cfrac = d[i].lowC ? 0.5 * (1.0 + 1.0 / std::max(1.0, N)) : 1.0;
+    if (d[i].M < 0) {
+      launchNK += nk * cfrac;
+      launchBytesPerM += 8.0 * (K + 2.0 * N * cfrac);
+      launchBytes0 += 8.0 * nk;
+    } else {
+      fixedMNK += (double)d[i].M * nk * cfrac;
+      fixedBytes += 8.0 * ((double)d[i].M * K + nk + 2.0 * d[i].M * N * cfrac);
+    }
   }
   ntilesN = pre[nprob];
   upload(desc, d, s);
@@ -131,7 +152,13 @@ void GemmBatch::run(const GemmBases& b, cudaStream_t s) const {
   if (M <= 0) return;
   dim3 grid(ntilesN, cdiv(M, BM));
   RSF_CHECK(grid.y <= 65535, RSF_EINVAL, "gemm: M too large");
+  int tok = prof_begin(s);
   LAUNCH(gemm_kernel, grid, GT, 0, s, desc.as<GemmDesc>(), prefix.as<int>(), nprob, b);
+  if (tok >= 0) {
+    double Ml = anyLaunchM ? (double)b.M : 0.0;
+    prof_end(tok, s, PROF_GEMM, 2.0 * (fixedMNK + Ml * launchNK),
+             fixedBytes + (anyLaunchM ? launchBytes0 + Ml * launchBytesPerM : 0.0));
+  }
 }
 
 // ============================================================ pivoted QR
@@ -307,11 +334,15 @@ void QRBatch::run(double* pool, DevStatus* st, int level, cudaStream_t s) {
          colprefix.as<int>(), nprob, ncols, pool, chosen.as<unsigned char>());
   int hdone = 0;
   for (int j = 0; j <= maxsteps; j++) {
+    int tp = prof_begin(s);
     LAUNCH(qr_pivot_kernel, nprob, 256, 0, s, prob.as<QRProb>(), state.as<QRState>(), j, pool,
            piv.as<int>(), chosen.as<unsigned char>(), vbuf.as<double>(), ndone.as<int>(), st, level);
+    prof_end(tp, s, PROF_QR_PIVOT, 0.0, 0.0);
     if (j == maxsteps) break;
+    int tu = prof_begin(s);
     LAUNCH(qr_update_kernel, blocksU, 256, 0, s, prob.as<QRProb>(), state.as<QRState>(),
            colprefix.as<int>(), nprob, ncols, j, pool, chosen.as<unsigned char>(), vbuf.as<double>());
+    prof_end(tu, s, PROF_QR_UPDATE, 0.0, 0.0);
     if ((j & 31) == 31) {
       d2h(&hdone, ndone.as<int>(), 1, s);
       sync(s);

@@ -38,6 +38,8 @@ struct GemmBatch {
   int ntilesN = 0;   // sum over problems of ceil(N / BN)
   int maxM = 0;      // max M over problems with M >= 0
   bool anyLaunchM = false;
+  // algorithmic work: flops = 2 (fixedMNK + launchM * launchNK), same for bytes
+  double fixedMNK = 0, launchNK = 0, fixedBytes = 0, launchBytesPerM = 0, launchBytes0 = 0;
   void build(const std::vector<GemmDesc>& d, cudaStream_t s);
   void run(const GemmBases& b, cudaStream_t s) const;
 };

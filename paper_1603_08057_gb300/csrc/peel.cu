@@ -362,8 +362,12 @@ double peel_trace(rsf_handle_s* F, rsf_handle_s* Fk, double tol, const rsf_opts&
       Y.alloc(sizeof(double) * n64 * 4 * qc, s);
       LAUNCH(gen_w_kernel, cdiv(n64 * 4 * qc, 256), 256, 0, s, dslot.as<int>(), n64, qc, qtot, lev,
              (unsigned long long)o.seed, W.as<double>());
+      int tk = prof_begin(s);
       applyG(W.as<double>(), Y.as<double>(), 4 * qc);
+      prof_end(tk, s, PROF_PEEL_APPLY, 0, 0);
+      tk = prof_begin(s);
       for (int m = 1; m < lev; m++) apply_level(levels[m], W.as<double>(), Y.as<double>(), 4 * qc, tmpP, s);
+      prof_end(tk, s, PROF_PEEL_SUB, 0, 0);
       chunk_q.push_back(qc);
       chunk_col0.push_back(qtot);
       Wch.push_back(std::move(W));
@@ -409,7 +413,9 @@ double peel_trace(rsf_handle_s* F, rsf_handle_s* Fk, double tol, const rsf_opts&
       }
       qb = QRBatch();
       qb.build(qp, s);
+      int tq = prof_begin(s);
       qb.run(Yqr.as<double>(), dst, lev, s);
+      prof_end(tq, s, PROF_PEEL_QR, 0, 0);
       std::vector<QRState> hst(nop);
       d2h(hst.data(), qb.d_state(), nop, s);
       sync(s);
@@ -418,6 +424,8 @@ double peel_trace(rsf_handle_s* F, rsf_handle_s* Fk, double tol, const rsf_opts&
         rank[i] = hst[i].k;
         rmax = std::max(rmax, rank[i]);
       }
+      if (verbose())
+        fprintf(stderr, "[rsf] peel level %d: q %d, max rank %d, pairs %d, boxes %d\n", lev, q, rmax, nop, nbx);
       if (rmax <= q - c_over || q >= (int)std::min<int64_t>(n64, 1 << 15)) break;
       q = q + q;
     }
@@ -437,6 +445,7 @@ double peel_trace(rsf_handle_s* F, rsf_handle_s* Fk, double tol, const rsf_opts&
     max_rank_seen = std::max(max_rank_seen, r_prev);
 
     // ---- bases U_ab = Y_ab(:, piv[:r]) R11^-1, stored in Ucat_a
+    int trest = prof_begin(s);
     int64_t pool = 0;
     PL.sumRa = 0;
     for (int a = 0; a < nbx; a++) {
@@ -681,6 +690,7 @@ double peel_trace(rsf_handle_s* F, rsf_handle_s* Fk, double tol, const rsf_opts&
       PL.gQ.build(gQ, s);
       PL.gY.build(gY, s);
     }
+    prof_end(trest, s, PROF_PEEL_REST, 0, 0);
     sync(s);
   }
 
@@ -692,8 +702,12 @@ double peel_trace(rsf_handle_s* F, rsf_handle_s* Fk, double tol, const rsf_opts&
   E.alloc(sizeof(double) * n64 * nl, s);
   H.alloc(sizeof(double) * n64 * nl, s);
   LAUNCH(unit_cols_kernel, cdiv(n64 * nl, 256), 256, 0, s, dlp.as<int>(), n64, nl, E.as<double>());
+  int tk = prof_begin(s);
   applyG(E.as<double>(), H.as<double>(), nl);
+  prof_end(tk, s, PROF_PEEL_APPLY, 0, 0);
+  tk = prof_begin(s);
   for (int m = 1; m <= L; m++) apply_level(levels[m], E.as<double>(), H.as<double>(), nl, tmpP, s);
+  prof_end(tk, s, PROF_PEEL_SUB, 0, 0);
   int nb = (int)std::min<int64_t>(1024, std::max<int64_t>(1, cdiv(n64, 256)));
   DBuf part, res;
   part.alloc(sizeof(double) * nb, s);

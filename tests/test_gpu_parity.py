@@ -1,0 +1,230 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances (derived from the arithmetic):
+* exact identities of the computed factors (F^-1 F = I, F^1/2 F^1/2^T = F):
+  rounding only, kappa(F) u with kappa <~ 1e4 here -> 1e-10 relative;
+* F vs Sigma: the ID tolerance eps_fact = 1e-9 with modest growth -> 1e-8;
+* log|F| vs log|Sigma|, log-likelihood vs dense: the acceptance bar 1e-6
+  relative at eps_fact = 1e-9;
+* score vs the dense exact score: the acceptance bar 1e-3 relative, and
+  1e-5 of the term scale (|quad_k| + |trace_k|)/2 since the peeled traces
+  carry eps_peel = 1e-6 relative error;
+* GPU vs oracle RSF (same algorithm, different pivots by rounding): the
+  same bars as against the exact values.
+"""
+import numpy as np
+import pytest
+
+from oracle import dense
+from oracle import kernels as K
+from oracle import rsf as orsf
+from paper_1603_08057_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1603_08057_gb300 import build
+    build.build()
+    from paper_1603_08057_gb300 import binding
+    return binding
+
+
+def T(a):
+    return torch.tensor(np.asarray(a), dtype=torch.float64, device="cuda")
+
+
+TH1 = (0.1, 1.0, 1e-2)
+
+
+@pytest.fixture(scope="module")
+def uni(B):
+    n = 3000
+    x = W.uniform(n, 101)
+    F = B.Factorization(T(x), B.MATERN32, TH1, B.SIGMA, 1e-9)
+    S = dense.cov_matrix(x, K.MATERN32, TH1)
+    return x, F, S
+
+
+def test_apply_matches_sigma_elementwise(B, uni):
+    x, F, S = uni
+    V = W.standard_normal(x.shape[0], 7, 5)
+    FV = F.solve(T(V), B.OP_APPLY).cpu().numpy()
+    ref = S @ V
+    assert np.max(np.abs(FV - ref)) <= 1e-8 * np.max(np.abs(ref))
+
+
+def test_apply_matches_oracle_rsf(B, uni):
+    x, F, S = uni
+    Fo = orsf.Factorization(x, K.MATERN32, TH1, K.SIGMA, 1e-9)
+    v = W.standard_normal(x.shape[0], 8)
+    ref = np.empty_like(v)
+    ref[Fo.tree.perm] = Fo.apply(v[Fo.tree.perm])
+    got = F.solve(T(v), B.OP_APPLY).cpu().numpy()
+    assert np.max(np.abs(got - ref)) <= 1e-8 * np.max(np.abs(ref))
+
+
+def test_solve_inverts_apply(B, uni):
+    x, F, S = uni
+    V = W.standard_normal(x.shape[0], 9, 3)
+    Y = F.solve(F.solve(T(V), B.OP_APPLY), B.OP_INV).cpu().numpy()
+    assert np.max(np.abs(Y - V)) <= 1e-10 * np.max(np.abs(V))
+
+
+def test_square_root_identities(B, uni):
+    x, F, S = uni
+    n = x.shape[0]
+    E = np.eye(n)[:, ::97]
+    FE = F.solve(T(E), B.OP_APPLY)
+    SS = F.solve(F.solve(T(E), B.OP_SQRT_T), B.OP_SQRT)
+    assert torch.max(torch.abs(SS - FE)).item() <= 1e-12 * torch.max(torch.abs(FE)).item()
+    I1 = F.solve(F.solve(T(E), B.OP_INV_SQRT), B.OP_SQRT).cpu().numpy()
+    I2 = F.solve(F.solve(T(E), B.OP_SQRT_T), B.OP_INV_SQRT_T).cpu().numpy()
+    assert np.max(np.abs(I1 - E)) <= 1e-10 and np.max(np.abs(I2 - E)) <= 1e-10
+
+
+def test_logdet_matches_dense(B, uni):
+    x, F, S = uni
+    ref = np.linalg.slogdet(S)[1]
+    assert abs(F.logdet() - ref) <= 1e-9 * abs(ref)
+
+
+@pytest.mark.parametrize("which", [1, 2])
+def test_derivative_factorizations_apply(B, which):
+    x = W.mixture(2500, 111)
+    th = (0.05, 2.0, 1e-2)
+    Fk = B.Factorization(T(x), B.MATERN32, th, which, 1e-9)
+    Sk = dense.cov_matrix(x, K.MATERN32, th, which)
+    V = W.standard_normal(2500, 112, 4)
+    got = Fk.solve(T(V), B.OP_APPLY).cpu().numpy()
+    ref = Sk @ V
+    assert np.max(np.abs(got - ref)) <= 1e-7 * np.max(np.abs(ref))
+
+
+def _check_loglik_score(B, x, z, fam, th, alpha=0.0):
+    d = dense.score_dense(x, z, fam, th, alpha)
+    ll, g, terms = B.loglik_and_score(T(x), T(z), fam, th, 1e-9, 1e-6, alpha)
+    assert abs(ll - d["ell"]) <= 1e-6 * abs(d["ell"])
+    g = g.numpy()
+    assert np.all(np.abs(g - d["g"]) <= 1e-3 * np.abs(d["g"]))
+    scale = 0.5 * np.abs(d["quadk"]) + 0.5 * np.abs(d["trace"])
+    assert np.all(np.abs(g - d["g"]) <= 1e-5 * scale)
+    t = terms.numpy()
+    np.testing.assert_allclose(t[:3], d["quadk"], rtol=1e-6)
+    np.testing.assert_allclose(t[3:], d["trace"], rtol=1e-5)
+    return ll, g
+
+
+def test_loglik_and_score_matern32_uniform_n4096(B):
+    # Matern 3/2, n = 4096 uniform points, l = 0.1, s2 = 1, nugget 1e-2,
+    # z from the dense Cholesky factor, eps_fact 1e-9, eps_peel 1e-6
+    wl = W.WORKLOADS["matern32_uniform_n4096"]
+    x = W.uniform(wl["n"], wl["seed_points"])
+    z = dense.sample_z_dense(x, K.MATERN32, wl["theta"], W.standard_normal(wl["n"], wl["seed_z"]))
+    _check_loglik_score(B, x, z, K.MATERN32, wl["theta"])
+
+
+def test_loglik_and_score_rq_mixture(B):
+    x = W.mixture(3000, 121)
+    th = (0.05, 1.0, 1e-3)
+    z = dense.sample_z_dense(x, K.RQ, th, W.standard_normal(3000, 122), 1.0)
+    _check_loglik_score(B, x, z, K.RQ, th, 1.0)
+
+
+@pytest.mark.parametrize("fam", [K.MATERN12, K.MATERN52])
+def test_loglik_other_matern(B, fam):
+    x = W.uniform(1500, 131)
+    th = (0.08, 1.5, 5e-3)
+    z = dense.sample_z_dense(x, fam, th, W.standard_normal(1500, 132))
+    _check_loglik_score(B, x, z, fam, th)
+
+
+def test_peeled_traces_match_oracle_peeling(B):
+    from oracle import peel
+    x = W.mixture(2000, 141)
+    th = (0.05, 2.0, 1e-2)
+    F = B.Factorization(T(x), B.MATERN32, th, B.SIGMA, 1e-9)
+    Fo = orsf.Factorization(x, K.MATERN32, th, K.SIGMA, 1e-9)
+    t_gpu = B.peel_trace(F, None, 1e-6)
+    t_or, _ = peel.peel_trace(Fo.solve, Fo.tree, 1e-6)
+    exact = np.trace(np.linalg.inv(dense.cov_matrix(x, K.MATERN32, th)))
+    assert abs(t_gpu - exact) <= 1e-6 * abs(exact)
+    assert abs(t_gpu - t_or) <= 1e-6 * abs(exact)
+
+
+def test_variance_nugget_trace_identity(B):
+    # Sigma = s2 Sigma_s2 + nug I  =>  s2 Tr(S^-1 S_s2) + nug Tr(S^-1) = n
+    x = W.mixture(3000, 151)
+    th = (0.05, 2.0, 1e-2)
+    F = B.Factorization(T(x), B.MATERN32, th, B.SIGMA, 1e-9)
+    Fs = B.Factorization(T(x), B.MATERN32, th, B.D_S2, 1e-9)
+    tn = B.peel_trace(F, None, 1e-6)
+    ts = B.peel_trace(F, Fs, 1e-6)
+    assert th[1] * ts + th[2] * tn == pytest.approx(3000, rel=1e-6)
+
+
+@pytest.mark.parametrize("n", [1, 2, 64, 65, 200])
+def test_small_and_ragged_sizes(B, n):
+    x = W.uniform(n, 161)
+    th = (0.2, 1.0, 1e-1)
+    z = dense.sample_z_dense(x, K.MATERN32, th, W.standard_normal(n, 162))
+    d = dense.score_dense(x, z, K.MATERN32, th)
+    ll, g, _ = B.loglik_and_score(T(x), T(z), B.MATERN32, th)
+    assert abs(ll - d["ell"]) <= 1e-8 * max(1.0, abs(d["ell"]))
+    scale = 0.5 * np.abs(d["quadk"]) + 0.5 * np.abs(d["trace"])
+    assert np.all(np.abs(g.numpy() - d["g"]) <= 1e-6 * scale + 1e-12)
+
+
+def test_coincident_and_collinear_points(B):
+    x = W.uniform(700, 171)
+    x[350:400] = x[0]            # 51 copies of one location (nugget keeps them apart)
+    x[400:600, 1] = 0.5          # a line of points
+    th = (0.1, 1.0, 5e-2)
+    z = dense.sample_z_dense(x, K.MATERN32, th, W.standard_normal(700, 172))
+    _check_loglik_score(B, x, z, K.MATERN32, th)
+
+
+def test_autograd_backward_is_the_score(B):
+    x = W.uniform(1200, 181)
+    th = (0.1, 1.0, 1e-2)
+    z = dense.sample_z_dense(x, K.MATERN32, th, W.standard_normal(1200, 182))
+    d = dense.score_dense(x, z, K.MATERN32, th)
+    theta = torch.tensor(th, dtype=torch.float64, requires_grad=True)
+    ll = B.gp_loglik(theta, T(x), T(z), B.MATERN32)
+    ll.backward()
+    assert ll.item() == pytest.approx(d["ell"], rel=1e-6)
+    np.testing.assert_allclose(theta.grad.numpy(), d["g"], rtol=1e-3)
+
+
+def test_deterministic(B):
+    x = W.mixture(2000, 191)
+    z = W.standard_normal(2000, 192)
+    th = (0.05, 2.0, 1e-2)
+    a = B.loglik_and_score(T(x), T(z), B.MATERN32, th)
+    b = B.loglik_and_score(T(x), T(z), B.MATERN32, th)
+    assert a[0] == b[0] and torch.equal(a[1], b[1])
+
+
+def test_invalid_arguments_raise(B):
+    x = T(W.uniform(100, 1))
+    with pytest.raises(B.RsfError) as e:
+        B.Factorization(x, B.MATERN32, (0.1, 1.0, 1e-2), B.SIGMA, 0.0)
+    assert e.value.code == 1
+    with pytest.raises(B.RsfError):
+        B.Factorization(x, 17, (0.1, 1.0, 1e-2))
+    with pytest.raises(B.RsfError):
+        B.Factorization(x, B.MATERN32, (-0.1, 1.0, 1e-2))
+    bad = W.uniform(100, 1)
+    bad[3, 0] = np.nan
+    with pytest.raises(B.RsfError):
+        B.Factorization(T(bad), B.MATERN32, (0.1, 1.0, 1e-2))
+    Fl = B.Factorization(x, B.MATERN32, (0.1, 1.0, 1e-2), B.D_L)
+    with pytest.raises(B.RsfError):
+        Fl.logdet()
+    with pytest.raises(B.RsfError):
+        Fl.solve(T(np.ones(100)), B.OP_INV)
