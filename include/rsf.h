@@ -90,7 +90,14 @@ typedef struct {
   int oversample;   /* peeling oversampling c (10), Sec. 3.1 */
   int q0;           /* peeling: minimum initial sample count at level 1 (64) */
   uint64_t seed;    /* Philox4x32-10 key of the peeling test matrices (0) */
+  int precision;    /* RSF_PREC_FP64 (0): every step in fp64.  RSF_PREC_MIXED
+                       (1, default): the IDs, Cholesky/QR factors and
+                       log-determinant stay fp64, the multi-RHS solves and the
+                       peeling products run in double-float (fp32-pair)
+                       arithmetic with ~48-bit significands */
 } rsf_opts;
+
+enum { RSF_PREC_FP64 = 0, RSF_PREC_MIXED = 1 };
 
 typedef struct rsf_tree_s* rsf_tree;
 typedef struct rsf_handle_s* rsf_handle;

@@ -202,6 +202,11 @@ static rsf_handle_s* make_handle(std::shared_ptr<rsf_tree_s> tree, const rsf_ker
   h->tol = tol;
   h->stream = tree->t.stream;
   h->spd = (which == RSF_SIGMA);
+  RSF_CHECK(o.precision == RSF_PREC_FP64 || o.precision == RSF_PREC_MIXED, RSF_EINVAL, "unknown precision");
+  // df64 for the Cholesky-based factorization of Sigma; a derivative
+  // factorization is probed at the end of factorize() and falls back to fp64
+  // when df64 would cost accuracy.
+  h->df = (o.precision == RSF_PREC_MIXED);
   h->kp.family = kernel->family;
   h->kp.alpha = kernel->alpha;
   h->kp.l = theta[0];
@@ -250,6 +255,7 @@ void rsf_opts_default(rsf_opts* o) {
   o->oversample = 10;
   o->q0 = 64;
   o->seed = 0;
+  o->precision = RSF_PREC_MIXED;
 }
 
 const char* rsf_last_error(void) { return g_err.c_str(); }

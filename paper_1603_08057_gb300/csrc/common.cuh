@@ -53,7 +53,8 @@ enum ProfCat {
   PROF_GEMM = 0, PROF_QR_UPDATE = 1, PROF_QR_PIVOT = 2,
   // phases (spans of many launches)
   PROF_PEEL_APPLY = 3, PROF_PEEL_SUB = 4, PROF_PEEL_QR = 5, PROF_PEEL_REST = 6, PROF_FACTOR = 7,
-  PROF_NCAT = 8
+  PROF_GEMM_DF = 8,  // the GEMM kernel in df64 arithmetic (PROF_GEMM: fp64)
+  PROF_NCAT = 9
 };
 // Diagnostics to stderr when the environment variable RSF_VERBOSE is set.
 bool verbose();

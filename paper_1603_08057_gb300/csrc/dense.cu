@@ -3,6 +3,7 @@
 #include <cfloat>
 
 #include "dense.cuh"
+#include "df64.cuh"
 
 namespace rsf {
 
@@ -20,9 +21,50 @@ __device__ __forceinline__ int find_prob(const int* prefix, int nprob, int tile)
   return lo;
 }
 
+// Element access for the two arithmetic modes: fp64, or df64 (8-byte
+// float2 pairs, products accumulated with error-free transformations).
+template <bool DF> struct Arith;
+template <> struct Arith<false> {
+  typedef double T;
+  typedef double Acc;
+  static __device__ __forceinline__ T load(const double* p) { return *p; }
+  static __device__ __forceinline__ T zero() { return 0.0; }
+  static __device__ __forceinline__ Acc acc0() { return 0.0; }
+  static __device__ __forceinline__ void mac(Acc& c, T a, T b) { c = fma(a, b, c); }
+  static __device__ __forceinline__ void store(double* p, Acc c, double alpha, double beta) {
+    double v = alpha * c;
+    if (beta != 0.0) v = fma(beta, *p, v);
+    *p = v;
+  }
+};
+template <> struct Arith<true> {
+  typedef df64 T;
+  typedef dfacc Acc;
+  static __device__ __forceinline__ T load(const double* p) {
+    float2 f = *reinterpret_cast<const float2*>(p);
+    return {f.x, f.y};
+  }
+  static __device__ __forceinline__ T zero() { return {0.f, 0.f}; }
+  static __device__ __forceinline__ Acc acc0() { return {0.f, 0.f}; }
+  static __device__ __forceinline__ void mac(Acc& c, T a, T b) { df_mac(c, a, b); }
+  static __device__ __forceinline__ void store(double* p, Acc c, double alpha, double beta) {
+    df64 v = df_scale(df_of_acc(c), (float)alpha);
+    if (beta != 0.0) {
+      float2 o = *reinterpret_cast<const float2*>(p);
+      df64 old = {o.x, o.y};
+      if (beta != 1.0) old = df_scale(old, (float)beta);
+      v = df_add(v, old);
+    }
+    *reinterpret_cast<float2*>(p) = make_float2(v.hi, v.lo);
+  }
+};
+
+template <bool DF>
 __global__ void __launch_bounds__(GT) gemm_kernel(const GemmDesc* __restrict__ descs,
                                                   const int* __restrict__ prefix, int nprob,
                                                   GemmBases bases) {
+  typedef Arith<DF> AR;
+  typedef typename AR::T T;
   const int p = find_prob(prefix, nprob, blockIdx.x);
   const GemmDesc d = descs[p];
   const int M = d.M >= 0 ? d.M : bases.M;
@@ -34,53 +76,61 @@ __global__ void __launch_bounds__(GT) gemm_kernel(const GemmDesc* __restrict__ d
   const int lda = d.lda >= 0 ? d.lda : bases.ld;
   const int ldb = d.ldb >= 0 ? d.ldb : bases.ld;
   const int ldc = d.ldc >= 0 ? d.ldc : bases.ld;
-  const double* __restrict__ A = bases.p[d.abase] + d.a * bases.sc[d.abase];
-  const double* __restrict__ B = bases.p[d.bbase] + d.b * bases.sc[d.bbase];
-  double* __restrict__ C = bases.p[d.cbase] + d.c * bases.sc[d.cbase];
+  const double* pa = d.abase == 0 ? bases.p[0] : d.abase == 1 ? bases.p[1] : d.abase == 2 ? bases.p[2] : bases.p[3];
+  const double* pb = d.bbase == 0 ? bases.p[0] : d.bbase == 1 ? bases.p[1] : d.bbase == 2 ? bases.p[2] : bases.p[3];
+  double* pc = d.cbase == 0 ? bases.p[0] : d.cbase == 1 ? bases.p[1] : d.cbase == 2 ? bases.p[2] : bases.p[3];
+  const int64_t sa = d.abase == 0 ? bases.sc[0] : d.abase == 1 ? bases.sc[1] : d.abase == 2 ? bases.sc[2] : bases.sc[3];
+  const int64_t sb = d.bbase == 0 ? bases.sc[0] : d.bbase == 1 ? bases.sc[1] : d.bbase == 2 ? bases.sc[2] : bases.sc[3];
+  const int64_t scc = d.cbase == 0 ? bases.sc[0] : d.cbase == 1 ? bases.sc[1] : d.cbase == 2 ? bases.sc[2] : bases.sc[3];
+  const double* __restrict__ A = pa + d.a * sa;
+  const double* __restrict__ B = pb + d.b * sb;
+  double* __restrict__ C = pc + d.c * scc;
   int k0 = 0, k1 = K;
   if (d.triB == 1) k0 = min(n0, K);
   if (d.triB == 2) k1 = min(K, n0 + BN);
 
-  __shared__ double sA[BK][BM + 1];
-  __shared__ double sB[BK][BN + 1];
+  __shared__ T sA[BK][BM + 1];
+  __shared__ T sB[BK][BN + 1];
   const int t = threadIdx.x;
   const int tm = t & 15, tn = t >> 4;
-  double acc[4][4];
+  typename AR::Acc acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; i++)
 #pragma unroll
-    for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
+    for (int j = 0; j < 4; j++) acc[i][j] = AR::acc0();
 
   for (int kb = k0; kb < k1; kb += BK) {
-    // A tile: BM x BK of op(A)
 #pragma unroll
     for (int r = 0; r < (BM * BK) / GT; r++) {
       int idx = t + r * GT;
       int mm, kk;
       if (!d.ta) { mm = idx % BM; kk = idx / BM; } else { kk = idx % BK; mm = idx / BK; }
       int gm = m0 + mm, gk = kb + kk;
-      double v = 0.0;
-      if (gm < M && gk < k1) v = d.ta ? A[gk + (int64_t)gm * lda] : A[gm + (int64_t)gk * lda];
+      T v = AR::zero();
+      if (gm < M && gk < k1) {
+        if (d.gatherK) v = AR::load(A + gm + (int64_t)bases.kidx[d.kofs + gk] * lda);
+        else v = AR::load(d.ta ? A + gk + (int64_t)gm * lda : A + gm + (int64_t)gk * lda);
+      }
       sA[kk][mm] = v;
     }
-    // B tile: BK x BN of op(B)
 #pragma unroll
     for (int r = 0; r < (BN * BK) / GT; r++) {
       int idx = t + r * GT;
       int nn, kk;
       if (!d.tb) { kk = idx % BK; nn = idx / BK; } else { nn = idx % BN; kk = idx / BN; }
       int gn = n0 + nn, gk = kb + kk;
-      double v = 0.0;
+      T v = AR::zero();
       if (gn < N && gk < k1) {
         bool zero = (d.triB == 1 && gk < gn) || (d.triB == 2 && gk > gn);
-        if (!zero) v = d.tb ? B[gn + (int64_t)gk * ldb] : B[gk + (int64_t)gn * ldb];
+        if (d.gatherK) v = AR::load(B + (bases.kidx[d.kofs + gk] - d.kb0) + (int64_t)gn * ldb);
+        else if (!zero) v = AR::load(d.tb ? B + gn + (int64_t)gk * ldb : B + gk + (int64_t)gn * ldb);
       }
       sB[kk][nn] = v;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; kk++) {
-      double a[4], b[4];
+      T a[4], b[4];
 #pragma unroll
       for (int i = 0; i < 4; i++) a[i] = sA[kk][tm + 16 * i];
 #pragma unroll
@@ -88,7 +138,7 @@ __global__ void __launch_bounds__(GT) gemm_kernel(const GemmDesc* __restrict__ d
 #pragma unroll
       for (int i = 0; i < 4; i++)
 #pragma unroll
-        for (int j = 0; j < 4; j++) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < 4; j++) AR::mac(acc[i][j], a[i], b[j]);
     }
     __syncthreads();
   }
@@ -102,10 +152,7 @@ __global__ void __launch_bounds__(GT) gemm_kernel(const GemmDesc* __restrict__ d
       int gn = n0 + tn + 8 * j;
       if (gn >= N) continue;
       if (d.lowC && gm < gn) continue;
-      double* cp = C + gm + (int64_t)gn * ldc;
-      double v = alpha * acc[i][j];
-      if (beta != 0.0) v = fma(beta, *cp, v);
-      *cp = v;
+      AR::store(C + gm + (int64_t)gn * ldc, acc[i][j], alpha, beta);
     }
   }
 }
@@ -153,10 +200,13 @@ void GemmBatch::run(const GemmBases& b, cudaStream_t s) const {
   dim3 grid(ntilesN, cdiv(M, BM));
   RSF_CHECK(grid.y <= 65535, RSF_EINVAL, "gemm: M too large");
   int tok = prof_begin(s);
-  LAUNCH(gemm_kernel, grid, GT, 0, s, desc.as<GemmDesc>(), prefix.as<int>(), nprob, b);
+  if (b.df)
+    LAUNCH(gemm_kernel<true>, grid, GT, 0, s, desc.as<GemmDesc>(), prefix.as<int>(), nprob, b);
+  else
+    LAUNCH(gemm_kernel<false>, grid, GT, 0, s, desc.as<GemmDesc>(), prefix.as<int>(), nprob, b);
   if (tok >= 0) {
     double Ml = anyLaunchM ? (double)b.M : 0.0;
-    prof_end(tok, s, PROF_GEMM, 2.0 * (fixedMNK + Ml * launchNK),
+    prof_end(tok, s, b.df ? PROF_GEMM_DF : PROF_GEMM, 2.0 * (fixedMNK + Ml * launchNK),
              fixedBytes + (anyLaunchM ? launchBytes0 + Ml * launchBytesPerM : 0.0));
   }
 }

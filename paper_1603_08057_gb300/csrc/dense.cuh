@@ -19,8 +19,11 @@ struct GemmDesc {
   int8_t ta, tb;
   int8_t triB;   // 0: none, 1: op(B) lower triangular, 2: op(B) upper triangular
   int8_t lowC;   // 1: skip output tiles strictly above the diagonal
-  int8_t pad;
+  int8_t gatherK;  // 1: the K index runs over kidx[kofs .. kofs + K): A column
+                   //    (ta = 0) kidx[.], B row (tb = 0) kidx[.] - kb0
   double alpha, beta;
+  int64_t kofs;
+  int64_t kb0;
 };
 
 struct GemmBases {
@@ -29,6 +32,8 @@ struct GemmBases {
   int M;       // used where desc.M < 0
   int ld;      // used where desc.lda/ldc < 0
   double alpha_scale;  // multiplies every desc.alpha
+  int df;              // 1: operands and result are df64 pairs (df64.cuh)
+  const int* kidx;     // K index list of descriptors with gatherK
 };
 
 // Device-resident batch of GEMM problems with its tile prefix.

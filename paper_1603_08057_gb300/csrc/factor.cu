@@ -234,6 +234,12 @@ __global__ void scatter_E_kernel(const EScatter* __restrict__ es, const int64_t*
   if (i < kq) fpool[e.e0 + s + (int64_t)pc * e.k] = tpool[e.t0 + i + (int64_t)s * kq];
 }
 
+// y -= x
+__global__ void axpy_neg_kernel(double* __restrict__ y, const double* __restrict__ x, int64_t n) {
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < n) y[g] -= x[g];
+}
+
 // 2 sum log diag per box (SPD levels).
 struct LdBox {
   int64_t d;
@@ -792,6 +798,52 @@ void factorize(rsf_handle_s* h) {
     prevAIIoff.assign(aiioff.begin(), aiioff.end() - 1);
     prevIsr = Lv.Isr.as<int>();
     sync(s);  // host vectors used by uploads above stay valid until here
+  }
+  // mixed precision: the solve factors are used as df64 pairs from here on
+  if (h->df) {
+    if (h->spd) {
+      for (auto& Lv : h->levels) convert_df64(Lv.fpool.as<double>(), (int64_t)(Lv.fpool.bytes / sizeof(double)), 1, s);
+    } else {
+      // A derivative matrix is eliminated with indefinite diagonal blocks,
+      // which can amplify rounding errors far beyond the ID tolerance.  Probe
+      // one application in fp64 and in df64 and keep df64 only when the two
+      // agree to the ID tolerance (the factorization's own error level).
+      h->df = false;
+      std::vector<double> hx(n);
+      uint64_t st = 0x9E3779B97F4A7C15ull;
+      for (int64_t i = 0; i < n; i++) {
+        st = st * 6364136223846793005ull + 1442695040888963407ull;
+        hx[i] = (double)(int64_t)(st >> 11) / 9007199254740992.0 - 0.5;
+      }
+      DBuf x, y64, ydf;
+      upload(x, hx, s);
+      y64.alloc(sizeof(double) * n, s);
+      ydf.alloc(sizeof(double) * n, s);
+      solve_rows(h, RSF_OP_APPLY, x.as<double>(), y64.as<double>(), 1, 0);
+      std::vector<DBuf> keep(h->levels.size());
+      for (size_t l = 0; l < h->levels.size(); l++) {
+        LevelData& Lv = h->levels[l];
+        DBuf c;
+        c.alloc(Lv.fpool.bytes, s);
+        if (Lv.fpool.bytes) RSF_CUDA(cudaMemcpyAsync(c.p, Lv.fpool.p, Lv.fpool.bytes, cudaMemcpyDeviceToDevice, s));
+        convert_df64(c.as<double>(), (int64_t)(c.bytes / sizeof(double)), 1, s);
+        keep[l] = std::move(Lv.fpool);
+        Lv.fpool = std::move(c);
+      }
+      h->df = true;
+      solve_rows(h, RSF_OP_APPLY, x.as<double>(), ydf.as<double>(), 1, 0);
+      double nn = dot_device(y64.as<double>(), y64.as<double>(), n, s);
+      LAUNCH(axpy_neg_kernel, cdiv(n, 256), 256, 0, s, ydf.as<double>(), y64.as<double>(), n);
+      double dd = dot_device(ydf.as<double>(), ydf.as<double>(), n, s);
+      bool ok = std::isfinite(dd) && dd <= h->tol * h->tol * nn;
+      if (verbose())
+        fprintf(stderr, "[rsf] derivative factorization: df64 vs fp64 apply rel diff %.3e -> %s\n",
+                std::sqrt(dd / std::max(nn, 1e-300)), ok ? "df64" : "fp64");
+      if (!ok) {
+        for (size_t l = 0; l < h->levels.size(); l++) h->levels[l].fpool = std::move(keep[l]);
+        h->df = false;
+      }
+    }
   }
   h->flops = flops;
   h->kevals = kevals;

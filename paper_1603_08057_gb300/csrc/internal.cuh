@@ -132,6 +132,7 @@ struct rsf_handle_s {
   rsf_opts opts;
   double tol = 0;
   bool spd = true;
+  bool df = false;                     // solve factors stored as df64 pairs
   cudaStream_t stream = nullptr;
   std::vector<rsf::LevelData> levels;  // index = tree level (0 = root)
   rsf::DBuf status;                    // DevStatus
@@ -149,7 +150,10 @@ std::shared_ptr<rsf_tree_s> build_tree(const double* points, int64_t n, const rs
 void factorize(rsf_handle_s* h);
 void check_status(rsf_handle_s* h);
 // Internal solve on tree-order, row-major (n x q) buffers: out = op(F) in.
-void solve_rows(rsf_handle_s* h, int op, const double* in, double* out, int q);
+// io_df: in/out hold df64 pairs (else doubles, converted when h->df).
+void solve_rows(rsf_handle_s* h, int op, const double* in, double* out, int q, int io_df = 0);
+// In-place conversion of n doubles to df64 pairs (to = 1) or back (to = 0).
+void convert_df64(double* p, int64_t n, int to, cudaStream_t s);
 double peel_trace(rsf_handle_s* F, rsf_handle_s* Fk, double tol, const rsf_opts& o, double* d_out);
 // device reductions
 double dot_device(const double* a, const double* b, int64_t n, cudaStream_t s);

@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "df64.cuh"
 #include "internal.cuh"
 
 namespace rsf {
@@ -50,10 +51,26 @@ __device__ __forceinline__ double philox_normal(unsigned row, unsigned col, unsi
   return (w & 1) ? rad * s : rad * co;
 }
 
+__device__ __forceinline__ void store_val(double* p, double v, int df) {
+  if (df) {
+    df64 d = df_from_double(v);
+    *reinterpret_cast<float2*>(p) = make_float2(d.hi, d.lo);
+  } else {
+    *p = v;
+  }
+}
+__device__ __forceinline__ double load_val(const double* p, int df) {
+  if (df) {
+    float2 f = *reinterpret_cast<const float2*>(p);
+    return df_to_double({f.x, f.y});
+  }
+  return *p;
+}
+
 // W chunk: n x (4 qc) row-major; row p of a level box in slot s gets the
 // normals of columns col0 .. col0+qc-1 in column block s.
 __global__ void gen_w_kernel(const int* __restrict__ slotrow, int64_t n, int qc, int col0, int level,
-                             unsigned long long seed, double* __restrict__ W) {
+                             unsigned long long seed, double* __restrict__ W, int df) {
   int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int64_t tot = n * 4 * qc;
   if (g >= tot) return;
@@ -62,7 +79,31 @@ __global__ void gen_w_kernel(const int* __restrict__ slotrow, int64_t n, int qc,
   int s = slotrow[p];
   double v = 0.0;
   if (s >= 0 && c / qc == s) v = philox_normal((unsigned)p, (unsigned)(col0 + c % qc), (unsigned)level, 0u, seed);
-  W[g] = v;
+  store_val(W + g, v, df);
+}
+
+// Sketch block V_a (|I_a| x 2q) of box a: N(0,1) draws from Philox stream 2,
+// written into columns q .. 3q-1 of [W_a V_a].  V_a is independent of the
+// test matrices, so the basis it selects does not depend on W_a.
+struct VBox {
+  int64_t r0, out0;
+  int rows;
+};
+__global__ void gen_v_kernel(const VBox* __restrict__ vb, const int64_t* __restrict__ prefix, int nprob,
+                             int64_t total, int q, int level, unsigned long long seed, double* __restrict__ out,
+                             int df) {
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= total) return;
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= g) lo = mid; else hi = mid - 1;
+  }
+  const VBox v = vb[lo];
+  int64_t x = g - prefix[lo];
+  int i = (int)(x % v.rows), j = (int)(x / v.rows);
+  store_val(out + v.out0 + i + (int64_t)j * v.rows,
+            philox_normal((unsigned)(v.r0 + i), (unsigned)j, (unsigned)level, 2u, seed), df);
 }
 
 // Column block extraction from row-major chunks into column-major matrices:
@@ -73,7 +114,7 @@ struct ExtractProb {
 };
 __global__ void extract_kernel(const ExtractProb* __restrict__ ep, const int64_t* __restrict__ prefix, int nprob,
                                int64_t total, int qc, int ldi, int col0, const double* __restrict__ in,
-                               double* __restrict__ out) {
+                               double* __restrict__ out, int df) {
   int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= total) return;
   int lo = 0, hi = nprob - 1;
@@ -84,13 +125,13 @@ __global__ void extract_kernel(const ExtractProb* __restrict__ ep, const int64_t
   const ExtractProb e = ep[lo];
   int64_t x = g - prefix[lo];
   int i = (int)(x % e.rows), j = (int)(x / e.rows);
-  out[e.out0 + i + (int64_t)(col0 + j) * e.rows] = in[(e.r0 + i) * ldi + e.cb + j];
+  out[e.out0 + i + (int64_t)(col0 + j) * e.rows] = load_val(in + (e.r0 + i) * ldi + e.cb + j, df);
 }
 
 // Gather pivot columns: out[:, t] = Y[:, piv[t]] for t < k.
 struct PivGather {
   int64_t y0, out0, col0;
-  int rows;
+  int rows, ldy;
 };
 __global__ void pivgather_kernel(const PivGather* __restrict__ pg, const int64_t* __restrict__ prefix, int nprob,
                                  int64_t total, const int* __restrict__ piv, const QRState* __restrict__ st,
@@ -107,7 +148,7 @@ __global__ void pivgather_kernel(const PivGather* __restrict__ pg, const int64_t
   int i = (int)(x % e.rows), t = (int)(x / e.rows);
   if (t >= st[lo].k) return;
   int c = piv[e.col0 + t];
-  out[e.out0 + i + (int64_t)t * e.rows] = Y[e.y0 + i + (int64_t)c * e.rows];
+  out[e.out0 + i + (int64_t)t * e.rows] = Y[e.y0 + i + (int64_t)c * e.ldy];
 }
 
 // Least-squares scatter: out[o0 + piv[i]*ri + s*rs] = t[t0 + i + s*kq].
@@ -137,7 +178,7 @@ __global__ void permscatter_kernel(const PermScatter* __restrict__ ps, const int
 // core = (Z_ab + Z_ba^T) / 2 (q x q), written into the QR work matrix.
 struct CoreProb {
   int64_t zab, zba, out;
-  int q;
+  int q, ld;
 };
 __global__ void core_kernel(const CoreProb* __restrict__ cp, int nprob, const double* __restrict__ Z,
                             double* __restrict__ out) {
@@ -147,16 +188,16 @@ __global__ void core_kernel(const CoreProb* __restrict__ cp, int nprob, const do
   int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= (int64_t)c.q * c.q) return;
   int i = (int)(g % c.q), j = (int)(g / c.q);
-  out[c.out + g] = 0.5 * (Z[c.zab + i + (int64_t)j * c.q] + Z[c.zba + j + (int64_t)i * c.q]);
+  out[c.out + g] = 0.5 * (Z[c.zab + i + (int64_t)j * c.ld] + Z[c.zba + j + (int64_t)i * c.ld]);
 }
 
 // trace of the leaf diagonal blocks: sum_p H[p, leafpos[p]]
 __global__ void diag_trace_kernel(const double* __restrict__ H, const int* __restrict__ leafpos, int64_t n,
-                                  int nl, double* __restrict__ part) {
+                                  int nl, double* __restrict__ part, int df) {
   __shared__ double red[256];
   double s = 0.0;
   for (int64_t p = (int64_t)blockIdx.x * 256 + threadIdx.x; p < n; p += (int64_t)gridDim.x * 256)
-    s += H[p * nl + leafpos[p]];
+    s += load_val(H + p * nl + leafpos[p], df);
   red[threadIdx.x] = s;
   __syncthreads();
   for (int o = 128; o > 0; o >>= 1) {
@@ -177,16 +218,25 @@ __global__ void sum_parts_kernel(const double* __restrict__ part, int n, double*
   }
   if (threadIdx.x == 0) *out = red[0];
 }
-__global__ void unit_cols_kernel(const int* __restrict__ leafpos, int64_t n, int nl, double* __restrict__ E) {
+__global__ void unit_cols_kernel(const int* __restrict__ leafpos, int64_t n, int nl, double* __restrict__ E,
+                                 int df) {
   int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= n * nl) return;
   int64_t p = g / nl;
   int c = (int)(g % nl);
-  E[g] = (c == leafpos[p]) ? 1.0 : 0.0;
+  store_val(E + g, (c == leafpos[p]) ? 1.0 : 0.0, df);
 }
-__global__ void axpby_kernel(double* __restrict__ y, const double* __restrict__ x, double a, double b, int64_t n) {
+// y = (y + x) / 2
+__global__ void average_kernel(double* __restrict__ y, const double* __restrict__ x, int64_t n, int df) {
   int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g < n) y[g] = a * y[g] + b * x[g];
+  if (g >= n) return;
+  if (df) {
+    float2 a = reinterpret_cast<float2*>(y)[g], b = reinterpret_cast<const float2*>(x)[g];
+    df64 v = df_scale(df_add({a.x, a.y}, {b.x, b.y}), 0.5f);
+    reinterpret_cast<float2*>(y)[g] = make_float2(v.hi, v.lo);
+  } else {
+    y[g] = 0.5 * y[g] + 0.5 * x[g];
+  }
 }
 
 // ----------------------------------------------------------------- host
@@ -229,7 +279,7 @@ GemmDesc mk(int M, int N, int K, int8_t abase, int64_t a, int lda, int8_t ta, in
 }
 
 void run_gemm(const std::vector<GemmDesc>& d, double* p0, double* p1, double* p2, double* p3, cudaStream_t s,
-              int64_t sc0 = 1, int64_t sc1 = 1, int64_t sc2 = 1, int64_t sc3 = 1) {
+              int64_t sc0 = 1, int64_t sc1 = 1, int64_t sc2 = 1, int64_t sc3 = 1, int df = 0) {
   if (d.empty()) return;
   GemmBatch gb;
   gb.build(d, s);
@@ -237,6 +287,7 @@ void run_gemm(const std::vector<GemmDesc>& d, double* p0, double* p1, double* p2
   b.p[0] = p0; b.p[1] = p1; b.p[2] = p2; b.p[3] = p3;
   b.sc[0] = sc0; b.sc[1] = sc1; b.sc[2] = sc2; b.sc[3] = sc3;
   b.alpha_scale = 1.0;
+  b.df = df;
   gb.run(b, s);
 }
 
@@ -248,7 +299,7 @@ void upload_prefix(DBuf& d, DBuf& pre, const std::vector<T>& v, const std::vecto
 }
 
 // Y -= G^(lev) X for row-major (n x nc) X, Y.
-void apply_level(const PLevel& P, const double* X, double* Y, int nc, DBuf& tmp, cudaStream_t s) {
+void apply_level(const PLevel& P, const double* X, double* Y, int nc, DBuf& tmp, cudaStream_t s, int df) {
   if (!P.active) return;
   int64_t need = (int64_t)nc * 2 * std::max<int64_t>(1, P.sumRa);
   if ((int64_t)tmp.bytes < need * (int64_t)sizeof(double)) tmp.alloc(need * sizeof(double), s);
@@ -256,7 +307,52 @@ void apply_level(const PLevel& P, const double* X, double* Y, int nc, DBuf& tmp,
   b.p[0] = const_cast<double*>(X); b.p[1] = Y; b.p[2] = P.pool.as<double>(); b.p[3] = tmp.as<double>();
   b.sc[0] = nc; b.sc[1] = nc; b.sc[2] = 1; b.sc[3] = nc;
   b.M = nc; b.ld = nc; b.alpha_scale = 1.0;
+  b.df = df;
   P.gP.run(b, s);
+  P.gQ.run(b, s);
+  P.gY.run(b, s);
+}
+
+// Y -= G^(lev) X for the block-sparse test matrix of a finer level: column
+// block k (qc columns) of X is nonzero only on the rows listed in
+// slotlist[sb[k] .. sb[k+1]) (ascending tree positions), so the first product
+// U_ba^T X(I_b) runs over those rows only.
+void apply_level_sparse(const PLevel& P, const double* X, double* Y, int qc, const std::vector<int>& slotlist,
+                        const int64_t sb[5], const int* d_slotlist, DBuf& tmp, cudaStream_t s, int df) {
+  if (!P.active) return;
+  const int nc = 4 * qc;
+  int64_t need = (int64_t)nc * 2 * std::max<int64_t>(1, P.sumRa);
+  if ((int64_t)tmp.bytes < need * (int64_t)sizeof(double)) tmp.alloc(need * sizeof(double), s);
+  std::vector<GemmDesc> g;
+  for (const PBox& A : P.bx) {
+    if (A.Ra == 0) continue;
+    for (int k = 0; k < 4; k++) {
+      auto b0 = slotlist.begin() + sb[k], b1 = slotlist.begin() + sb[k + 1];
+      auto lo = std::lower_bound(b0, b1, A.start), hi = std::lower_bound(b0, b1, A.start + A.cnt);
+      GemmDesc d = mk(qc, A.Ra, (int)(hi - lo), 0, (int64_t)k * qc, nc, 0, 2, A.ucat, A.cnt, 0, 3,
+                      A.pcol * nc + (int64_t)k * qc, nc, 1.0, 0.0);
+      d.gatherK = 1;
+      d.kofs = lo - slotlist.begin();
+      d.kb0 = A.start;
+      g.push_back(d);
+    }
+  }
+  {
+    GemmBatch gb;
+    gb.build(g, s);
+    GemmBases b{};
+    b.p[0] = const_cast<double*>(X); b.p[1] = Y; b.p[2] = P.pool.as<double>(); b.p[3] = tmp.as<double>();
+    b.sc[0] = b.sc[1] = b.sc[2] = b.sc[3] = 1;
+    b.alpha_scale = 1.0;
+    b.df = df;
+    b.kidx = d_slotlist;
+    gb.run(b, s);
+  }
+  GemmBases b{};
+  b.p[0] = const_cast<double*>(X); b.p[1] = Y; b.p[2] = P.pool.as<double>(); b.p[3] = tmp.as<double>();
+  b.sc[0] = nc; b.sc[1] = nc; b.sc[2] = 1; b.sc[3] = nc;
+  b.M = nc; b.ld = nc; b.alpha_scale = 1.0;
+  b.df = df;
   P.gQ.run(b, s);
   P.gY.run(b, s);
 }
@@ -271,22 +367,36 @@ double peel_trace(rsf_handle_s* F, rsf_handle_s* Fk, double tol, const rsf_opts&
   const int c_over = std::max(0, o.oversample);
   DevStatus* dst = F->status.as<DevStatus>();
   int64_t n64 = n;
+  const int df = F->df ? 1 : 0;
 
   // G application on row-major tree-order blocks
-  DBuf ga, gb2;
+  DBuf ga, gb2, gw;
   auto applyG = [&](const double* in, double* out, int q) {
     if (!Fk) {
-      solve_rows(F, RSF_OP_INV, in, out, q);
+      solve_rows(F, RSF_OP_INV, in, out, q, df);
       return;
     }
     int64_t bytes = sizeof(double) * n64 * q;
     if ((int64_t)ga.bytes < bytes) ga.alloc(bytes, s);
     if ((int64_t)gb2.bytes < bytes) gb2.alloc(bytes, s);
-    solve_rows(Fk, RSF_OP_APPLY, in, ga.as<double>(), q);
-    solve_rows(F, RSF_OP_INV, ga.as<double>(), gb2.as<double>(), q);   // F^-1 F_k W
-    solve_rows(F, RSF_OP_INV, in, ga.as<double>(), q);
-    solve_rows(Fk, RSF_OP_APPLY, ga.as<double>(), out, q);             // F_k F^-1 W
-    LAUNCH(axpby_kernel, cdiv(n64 * q, 256), 256, 0, s, out, gb2.as<double>(), 0.5, 0.5, n64 * q);
+    if (df && !Fk->df) {
+      // F in df64, F_k in fp64: work on doubles, return df64 pairs
+      if ((int64_t)gw.bytes < bytes) gw.alloc(bytes, s);
+      RSF_CUDA(cudaMemcpyAsync(gw.p, in, bytes, cudaMemcpyDeviceToDevice, s));
+      convert_df64(gw.as<double>(), n64 * q, 0, s);
+      solve_rows(Fk, RSF_OP_APPLY, gw.as<double>(), ga.as<double>(), q, 0);
+      solve_rows(F, RSF_OP_INV, ga.as<double>(), gb2.as<double>(), q, 0);   // F^-1 F_k W
+      solve_rows(F, RSF_OP_INV, gw.as<double>(), ga.as<double>(), q, 0);
+      solve_rows(Fk, RSF_OP_APPLY, ga.as<double>(), out, q, 0);             // F_k F^-1 W
+      LAUNCH(average_kernel, cdiv(n64 * q, 256), 256, 0, s, out, gb2.as<double>(), n64 * q, 0);
+      convert_df64(out, n64 * q, 1, s);
+      return;
+    }
+    solve_rows(Fk, RSF_OP_APPLY, in, ga.as<double>(), q, df);
+    solve_rows(F, RSF_OP_INV, ga.as<double>(), gb2.as<double>(), q, df);   // F^-1 F_k W
+    solve_rows(F, RSF_OP_INV, in, ga.as<double>(), q, df);
+    solve_rows(Fk, RSF_OP_APPLY, ga.as<double>(), out, q, df);             // F_k F^-1 W
+    LAUNCH(average_kernel, cdiv(n64 * q, 256), 256, 0, s, out, gb2.as<double>(), n64 * q, df);
   };
 
   std::vector<PLevel> levels(L + 1);
@@ -333,59 +443,90 @@ double peel_trace(rsf_handle_s* F, rsf_handle_s* Fk, double tol, const rsf_opts&
         }
       }
     const int nbx = (int)PL.bx.size();
-    // slot of every row at this level (-1 outside the level's boxes)
     std::fill(slotrow.begin(), slotrow.end(), -1);
     for (auto& pb : PL.bx)
       for (int i = 0; i < pb.cnt; i++) slotrow[pb.start + i] = pb.slot;
     upload(dslot, slotrow, s);
+    // rows of each slot in tree order (the nonzero rows of W_k)
+    std::vector<int> slotlist;
+    int64_t sbeg[5] = {0, 0, 0, 0, 0};
+    for (int k = 0; k < 4; k++) {
+      sbeg[k] = (int64_t)slotlist.size();
+      for (int64_t p = 0; p < n64; p++)
+        if (slotrow[p] == k) slotlist.push_back((int)p);
+    }
+    sbeg[4] = (int64_t)slotlist.size();
+    DBuf dslotlist;
+    upload(dslotlist, slotlist, s);
 
-    // ordered pairs list: (a, t) for each box a and sibling position t
+    // ordered pairs (a, t): box a with its t-th sibling
     struct OPair { int a, t; };
     std::vector<OPair> op;
     for (int a = 0; a < nbx; a++)
       for (int t = 0; t < PL.bx[a].nsib; t++) op.push_back({a, t});
     const int nop = (int)op.size();
+    std::vector<int> opbase(nbx + 1, 0);
+    for (int a = 0; a < nbx; a++) opbase[a + 1] = opbase[a] + PL.bx[a].nsib;
+    auto opidx = [&](int a, int t) { return opbase[a] + t; };
 
-    int q = std::max(lev == 1 ? std::max(o.q0, 1) : 8, r_prev) + c_over;
+    // Initial sample count: at level 1 nine tenths of the largest level-1
+    // skeleton of F (the sibling-block ranks at eps_peel sit below the ID
+    // ranks at eps_fact), deeper down nine tenths of the previous level's
+    // largest rank (ranks shrink slowly towards the leaves).
+    int q0 = 8;
+    if (lev == 1) {
+      q0 = std::max(o.q0, 1);
+      if (F->levels.size() > 1)
+        for (int kk : F->levels[1].k) q0 = std::max(q0, (9 * kk) / 10);
+    } else {
+      q0 = std::max(8, (9 * r_prev) / 10);
+    }
+    int q = q0 + c_over;
     std::vector<int> chunk_q, chunk_col0;
     std::vector<DBuf> Wch, Ych;
     std::vector<int> rank(nop, 0);
     QRBatch qb;
-    DBuf Yorig, Yqr, Wbox;
-    std::vector<int64_t> yoff(nop + 1, 0), woff(nbx + 1, 0);
+    DBuf Yb, WV, Sb, Sqr;
+    std::vector<int64_t> yoff(nop + 1, 0), woff(nbx + 1, 0), soff(nop + 1, 0);
     int qtot = 0;
     while (true) {
       int qc = q - qtot;
-      // new chunk
-      DBuf W, Y;
-      W.alloc(sizeof(double) * n64 * 4 * qc, s);
-      Y.alloc(sizeof(double) * n64 * 4 * qc, s);
-      LAUNCH(gen_w_kernel, cdiv(n64 * 4 * qc, 256), 256, 0, s, dslot.as<int>(), n64, qc, qtot, lev,
-             (unsigned long long)o.seed, W.as<double>());
-      int tk = prof_begin(s);
-      applyG(W.as<double>(), Y.as<double>(), 4 * qc);
-      prof_end(tk, s, PROF_PEEL_APPLY, 0, 0);
-      tk = prof_begin(s);
-      for (int m = 1; m < lev; m++) apply_level(levels[m], W.as<double>(), Y.as<double>(), 4 * qc, tmpP, s);
-      prof_end(tk, s, PROF_PEEL_SUB, 0, 0);
-      chunk_q.push_back(qc);
-      chunk_col0.push_back(qtot);
-      Wch.push_back(std::move(W));
-      Ych.push_back(std::move(Y));
+      {
+        DBuf W, Y;
+        W.alloc(sizeof(double) * n64 * 4 * qc, s);
+        Y.alloc(sizeof(double) * n64 * 4 * qc, s);
+        LAUNCH(gen_w_kernel, cdiv(n64 * 4 * qc, 256), 256, 0, s, dslot.as<int>(), n64, qc, qtot, lev,
+               (unsigned long long)o.seed, W.as<double>(), df);
+        int tk = prof_begin(s);
+        applyG(W.as<double>(), Y.as<double>(), 4 * qc);
+        prof_end(tk, s, PROF_PEEL_APPLY, 0, 0);
+        tk = prof_begin(s);
+        for (int m = 1; m < lev; m++)
+          apply_level_sparse(levels[m], W.as<double>(), Y.as<double>(), qc, slotlist, sbeg, dslotlist.as<int>(), tmpP,
+                             s, df);
+        prof_end(tk, s, PROF_PEEL_SUB, 0, 0);
+        chunk_q.push_back(qc);
+        chunk_col0.push_back(qtot);
+        Wch.push_back(std::move(W));
+        Ych.push_back(std::move(Y));
+      }
       qtot = q;
-      // gather Y_ab (column-major |I_a| x q) and W_a (|I_a| x q)
+      int tq = prof_begin(s);
+      // Y_ab (|I_a| x q) per ordered pair and [W_a V_a] (|I_a| x 2q) per box,
+      // column-major, in the arithmetic of the applications (df64 or fp64)
       for (int i = 0; i < nop; i++) yoff[i + 1] = yoff[i] + (int64_t)PL.bx[op[i].a].cnt * q;
-      for (int a = 0; a < nbx; a++) woff[a + 1] = woff[a] + (int64_t)PL.bx[a].cnt * q;
-      Yorig.alloc(sizeof(double) * std::max<int64_t>(1, yoff[nop]), s);
-      Wbox.alloc(sizeof(double) * std::max<int64_t>(1, woff[nbx]), s);
+      for (int a = 0; a < nbx; a++) woff[a + 1] = woff[a] + (int64_t)PL.bx[a].cnt * 3 * q;
+      for (int i = 0; i < nop; i++) soff[i + 1] = soff[i] + (int64_t)3 * q * q;
+      Yb.alloc(sizeof(double) * std::max<int64_t>(1, yoff[nop]), s);
+      WV.alloc(sizeof(double) * std::max<int64_t>(1, woff[nbx]), s);
       for (size_t ch = 0; ch < Ych.size(); ch++) {
         int qq = chunk_q[ch];
         std::vector<ExtractProb> ey, ew;
         std::vector<int64_t> py(1, 0), pw(1, 0);
         for (int i = 0; i < nop; i++) {
           const PBox& A = PL.bx[op[i].a];
-          const PBox& B = PL.bx[A.sib[op[i].t]];
-          ey.push_back({(int64_t)A.start, yoff[i], A.cnt, B.slot * qq});
+          const PBox& Bx = PL.bx[A.sib[op[i].t]];
+          ey.push_back({(int64_t)A.start, yoff[i], A.cnt, Bx.slot * qq});
           py.push_back(py.back() + (int64_t)A.cnt * qq);
         }
         for (int a = 0; a < nbx; a++) {
@@ -396,25 +537,53 @@ double peel_trace(rsf_handle_s* F, rsf_handle_s* Fk, double tol, const rsf_opts&
         DBuf d1, d2, d3, d4;
         upload_prefix(d1, d2, ey, py, s);
         LAUNCH(extract_kernel, cdiv(py.back(), 256), 256, 0, s, d1.as<ExtractProb>(), d2.as<int64_t>(), nop,
-               py.back(), qq, 4 * qq, chunk_col0[ch], Ych[ch].as<double>(), Yorig.as<double>());
+               py.back(), qq, 4 * qq, chunk_col0[ch], Ych[ch].as<double>(), Yb.as<double>(), 0);
         upload_prefix(d3, d4, ew, pw, s);
         LAUNCH(extract_kernel, cdiv(pw.back(), 256), 256, 0, s, d3.as<ExtractProb>(), d4.as<int64_t>(), nbx,
-               pw.back(), qq, 4 * qq, chunk_col0[ch], Wch[ch].as<double>(), Wbox.as<double>());
+               pw.back(), qq, 4 * qq, chunk_col0[ch], Wch[ch].as<double>(), WV.as<double>(), 0);
       }
-      // rank-revealing QR of every Y_ab
-      Yqr.alloc(sizeof(double) * std::max<int64_t>(1, yoff[nop]), s);
-      RSF_CUDA(cudaMemcpyAsync(Yqr.p, Yorig.p, sizeof(double) * yoff[nop], cudaMemcpyDeviceToDevice, s));
+      {
+        std::vector<VBox> vb(nbx);
+        std::vector<int64_t> pv(nbx + 1, 0);
+        for (int a = 0; a < nbx; a++) {
+          vb[a] = {(int64_t)PL.bx[a].start, woff[a] + (int64_t)PL.bx[a].cnt * q, PL.bx[a].cnt};
+          pv[a + 1] = pv[a] + (int64_t)PL.bx[a].cnt * 2 * q;
+        }
+        DBuf d1, d2;
+        upload_prefix(d1, d2, vb, pv, s);
+        LAUNCH(gen_v_kernel, cdiv(pv.back(), 256), 256, 0, s, d1.as<VBox>(), d2.as<int64_t>(), nbx, pv.back(), q,
+               lev, (unsigned long long)o.seed, WV.as<double>(), df);
+      }
+      // [W_a V_a]^T Y_ab (3q x q): rows 0..q-1 are Z_ab = W_a^T Y_ab (for the
+      // core of Eq. (lowrankapprox)), rows q..3q-1 the sketch S_ab = V_a^T Y_ab
+      // with V_a independent of the test matrices
+      Sb.alloc(sizeof(double) * std::max<int64_t>(1, soff[nop]), s);
+      {
+        std::vector<GemmDesc> g;
+        for (int i = 0; i < nop; i++) {
+          const PBox& A = PL.bx[op[i].a];
+          g.push_back(mk(3 * q, q, A.cnt, 0, woff[op[i].a], A.cnt, 1, 1, yoff[i], A.cnt, 0, 2, soff[i], 3 * q, 1.0,
+                         0.0));
+        }
+        run_gemm(g, WV.as<double>(), Yb.as<double>(), Sb.as<double>(), nullptr, s, 1, 1, 1, 1, df);
+        if (df) convert_df64(Sb.as<double>(), soff[nop], 0, s);
+      }
+      // rank-revealing pivoted QR of the sketches (fp64, 2q x q each)
+      Sqr.alloc(sizeof(double) * std::max<int64_t>(1, (int64_t)nop * 2 * q * q), s);
+      {
+        std::vector<CopyProb> cp(nop);
+        for (int i = 0; i < nop; i++) cp[i] = {2 * q, q, 3 * q, 2 * q, soff[i] + q, (int64_t)i * 2 * q * q, 0};
+        copy_batched(cp, Sb.as<double>(), Sqr.as<double>(), s);
+      }
       std::vector<QRProb> qp(nop);
       for (int i = 0; i < nop; i++) {
-        int rows = PL.bx[op[i].a].cnt;
         qp[i] = QRProb{};
-        qp[i].m = rows; qp[i].c = q; qp[i].cpiv = q; qp[i].maxk = std::min(rows, q);
-        qp[i].lda = rows; qp[i].a = yoff[i]; qp[i].tol = tol;
+        qp[i].m = 2 * q; qp[i].c = q; qp[i].cpiv = q; qp[i].maxk = q;
+        qp[i].lda = 2 * q; qp[i].a = (int64_t)i * 2 * q * q; qp[i].tol = tol;
       }
       qb = QRBatch();
       qb.build(qp, s);
-      int tq = prof_begin(s);
-      qb.run(Yqr.as<double>(), dst, lev, s);
+      qb.run(Sqr.as<double>(), dst, lev, s);
       prof_end(tq, s, PROF_PEEL_QR, 0, 0);
       std::vector<QRState> hst(nop);
       d2h(hst.data(), qb.d_state(), nop, s);
@@ -427,15 +596,14 @@ double peel_trace(rsf_handle_s* F, rsf_handle_s* Fk, double tol, const rsf_opts&
       if (verbose())
         fprintf(stderr, "[rsf] peel level %d: q %d, max rank %d, pairs %d, boxes %d\n", lev, q, rmax, nop, nbx);
       if (rmax <= q - c_over || q >= (int)std::min<int64_t>(n64, 1 << 15)) break;
-      q = q + q;
+      // saturated: grow geometrically; otherwise just past the detected rank
+      if (rmax >= q - 1) q = std::max(q + c_over, (4 * q) / 3);
+      else q = rmax + c_over + std::max(4, rmax / 16);
     }
     Wch.clear();
     Ych.clear();
-    // ordered-pair index of (a, t) and one-sided zero ranks: a block whose
-    // row or column space is empty is dropped in both directions
-    std::vector<int> opbase(nbx + 1, 0);
-    for (int a = 0; a < nbx; a++) opbase[a + 1] = opbase[a] + PL.bx[a].nsib;
-    auto opidx = [&](int a, int t) { return opbase[a] + t; };
+    WV.release();
+    // a block whose row or column space is empty is dropped in both directions
     for (const PPair& pp : PL.pr) {
       int iab = opidx(pp.a, pp.sa), iba = opidx(pp.b, pp.sb);
       if (rank[iab] == 0 || rank[iba] == 0) rank[iab] = rank[iba] = 0;
@@ -444,21 +612,11 @@ double peel_trace(rsf_handle_s* F, rsf_handle_s* Fk, double tol, const rsf_opts&
     for (int i = 0; i < nop; i++) r_prev = std::max(r_prev, rank[i]);
     max_rank_seen = std::max(max_rank_seen, r_prev);
 
-    // ---- bases U_ab = Y_ab(:, piv[:r]) R11^-1, stored in Ucat_a
     int trest = prof_begin(s);
+    // ---- pool layout: U_ab blocks (Ucat_a per box), then the cores M_ab
     int64_t pool = 0;
     PL.sumRa = 0;
-    for (int a = 0; a < nbx; a++) {
-      PBox& A = PL.bx[a];
-      A.Ra = 0;
-      A.ucat = pool;
-      A.pcol = PL.sumRa;
-      for (int t = 0; t < A.nsib; t++) { A.r[t] = 0; A.ucol[t] = 0; }
-    }
-    for (int i = 0; i < nop; i++) {
-      PBox& A = PL.bx[op[i].a];
-      A.r[op[i].t] = rank[i];
-    }
+    for (int i = 0; i < nop; i++) PL.bx[op[i].a].r[op[i].t] = rank[i];
     for (int a = 0; a < nbx; a++) {
       PBox& A = PL.bx[a];
       A.Ra = 0;
@@ -468,6 +626,7 @@ double peel_trace(rsf_handle_s* F, rsf_handle_s* Fk, double tol, const rsf_opts&
       A.pcol = PL.sumRa;
       PL.sumRa += A.Ra;
     }
+    const int64_t mstart = pool;
     for (auto& pp : PL.pr) {
       pp.m = pool;
       pool += (int64_t)PL.bx[pp.a].r[pp.sa] * PL.bx[pp.b].r[pp.sb];
@@ -475,72 +634,66 @@ double peel_trace(rsf_handle_s* F, rsf_handle_s* Fk, double tol, const rsf_opts&
     PL.pool.alloc(sizeof(double) * std::max<int64_t>(1, pool), s);
     PL.pool.zero();
     double* UP = PL.pool.as<double>();
+    // ---- R11^-1 of every sketch QR, U_ab = Y_ab(:, piv) R11^-1 and
+    //      B_ab = W_a^T U_ab = Z_ab(:, piv) R11^-1 with Z_ab = W_a^T Y_ab
+    std::vector<int64_t> roff(nop + 1, 0), poff(nop + 1, 0), zpoff(nop + 1, 0), boff(nop + 1, 0);
+    for (int i = 0; i < nop; i++) {
+      int rows = PL.bx[op[i].a].cnt;
+      roff[i + 1] = roff[i] + (int64_t)rank[i] * rank[i];
+      poff[i + 1] = poff[i] + (int64_t)rows * rank[i];
+      zpoff[i + 1] = zpoff[i] + (int64_t)q * rank[i];
+      boff[i + 1] = boff[i] + (int64_t)q * rank[i];
+    }
+    DBuf Rinv, Ypiv, Zpiv, Bm;
+    Rinv.alloc(sizeof(double) * std::max<int64_t>(1, roff[nop]), s);
     {
-      // R11^-1 for each ordered pair (identity-mode back-substitution)
       std::vector<TrsmProb> tp(nop);
-      std::vector<int64_t> roff(nop + 1, 0);
-      for (int i = 0; i < nop; i++) {
-        tp[i].nrhs = rank[i];
-        tp[i].rhs0 = -1;
-        tp[i].out0 = roff[i];
-        roff[i + 1] = roff[i] + (int64_t)rank[i] * rank[i];
-      }
-      DBuf Rinv, Ypiv;
-      Rinv.alloc(sizeof(double) * std::max<int64_t>(1, roff[nop]), s);
-      qr_trsm(qb, tp, nullptr, Yqr.as<double>(), Rinv.as<double>(), dst, lev, s);
-      std::vector<int64_t> poff(nop + 1, 0);
-      std::vector<PivGather> pg(nop);
+      for (int i = 0; i < nop; i++) tp[i] = {rank[i], -1, roff[i]};
+      qr_trsm(qb, tp, nullptr, Sqr.as<double>(), Rinv.as<double>(), dst, lev, s);
+    }
+    Ypiv.alloc(sizeof(double) * std::max<int64_t>(1, poff[nop]), s);
+    Zpiv.alloc(sizeof(double) * std::max<int64_t>(1, zpoff[nop]), s);
+    Bm.alloc(sizeof(double) * std::max<int64_t>(1, boff[nop]), s);
+    {
+      std::vector<PivGather> pg(nop), pz(nop);
+      std::vector<int64_t> gp(nop + 1, 0), gz(nop + 1, 0);
       for (int i = 0; i < nop; i++) {
         int rows = PL.bx[op[i].a].cnt;
-        pg[i] = {yoff[i], poff[i], qb.colprefix_h[i], rows};
-        poff[i + 1] = poff[i] + (int64_t)rows * rank[i];
+        pg[i] = {yoff[i], poff[i], qb.colprefix_h[i], rows, rows};
+        pz[i] = {soff[i], zpoff[i], qb.colprefix_h[i], q, 3 * q};
+        gp[i + 1] = gp[i] + (int64_t)rows * rank[i];
+        gz[i + 1] = gz[i] + (int64_t)q * rank[i];
       }
-      Ypiv.alloc(sizeof(double) * std::max<int64_t>(1, poff[nop]), s);
-      // pivgather iterates over rows x k (k <= q); prefix in units of rows * q
-      std::vector<int64_t> gpre(nop + 1, 0);
-      for (int i = 0; i < nop; i++) gpre[i + 1] = gpre[i] + (int64_t)pg[i].rows * rank[i];
-      if (gpre[nop] > 0) {
-        DBuf d1, d2;
-        upload_prefix(d1, d2, pg, gpre, s);
-        LAUNCH(pivgather_kernel, cdiv(gpre[nop], 256), 256, 0, s, d1.as<PivGather>(), d2.as<int64_t>(), nop,
-               gpre[nop], qb.d_piv(), qb.d_state(), Yorig.as<double>(), Ypiv.as<double>());
+      if (gp[nop] > 0) {
+        DBuf d1, d2, d3, d4;
+        upload_prefix(d1, d2, pg, gp, s);
+        LAUNCH(pivgather_kernel, cdiv(gp[nop], 256), 256, 0, s, d1.as<PivGather>(), d2.as<int64_t>(), nop,
+               gp[nop], qb.d_piv(), qb.d_state(), Yb.as<double>(), Ypiv.as<double>());
+        upload_prefix(d3, d4, pz, gz, s);
+        LAUNCH(pivgather_kernel, cdiv(gz[nop], 256), 256, 0, s, d3.as<PivGather>(), d4.as<int64_t>(), nop,
+               gz[nop], qb.d_piv(), qb.d_state(), Sb.as<double>(), Zpiv.as<double>());
       }
-      std::vector<GemmDesc> g;
+      std::vector<GemmDesc> gu, gb;
       for (int i = 0; i < nop; i++) {
         const PBox& A = PL.bx[op[i].a];
         int r = rank[i];
         if (r == 0) continue;
-        // U = Ypiv (rows x r) * Rinv (r x r, upper)
-        g.push_back(mk(A.cnt, r, r, 0, poff[i], A.cnt, 0, 1, roff[i], r, 0, 2,
-                       A.ucat + (int64_t)A.ucol[op[i].t] * A.cnt, A.cnt, 1.0, 0.0, 2));
+        // U = Ypiv (rows x r) * Rinv (r x r, upper) into Ucat_a
+        gu.push_back(mk(A.cnt, r, r, 0, poff[i], A.cnt, 0, 1, roff[i], r, 0, 2,
+                        A.ucat + (int64_t)A.ucol[op[i].t] * A.cnt, A.cnt, 1.0, 0.0, 2));
+        // B = Zpiv (q x r) * Rinv
+        gb.push_back(mk(q, r, r, 0, zpoff[i], q, 0, 1, roff[i], r, 0, 2, boff[i], q, 1.0, 0.0, 2));
       }
-      run_gemm(g, Ypiv.as<double>(), Rinv.as<double>(), UP, nullptr, s);
+      run_gemm(gb, Zpiv.as<double>(), Rinv.as<double>(), Bm.as<double>(), nullptr, s);
+      if (df) convert_df64(Rinv.as<double>(), roff[nop], 1, s);
+      run_gemm(gu, Ypiv.as<double>(), Rinv.as<double>(), UP, nullptr, s, 1, 1, 1, 1, df);
     }
+    Ypiv.release();
+    Yb.release();
     // ---- cores M_ab (Eq. (lowrankapprox))
     {
-      // B_ab = W_a^T U_ab (q x r_ab) and Z_ab = W_a^T Y_ab (q x q)
-      std::vector<int64_t> boff(nop + 1, 0), zoff(nop + 1, 0);
-      for (int i = 0; i < nop; i++) {
-        boff[i + 1] = boff[i] + (int64_t)q * rank[i];
-        zoff[i + 1] = zoff[i] + (int64_t)q * q;
-      }
-      DBuf Bm, Zm;
-      Bm.alloc(sizeof(double) * std::max<int64_t>(1, boff[nop]), s);
-      Zm.alloc(sizeof(double) * std::max<int64_t>(1, zoff[nop]), s);
-      std::vector<GemmDesc> g1, g2;
-      for (int i = 0; i < nop; i++) {
-        const PBox& A = PL.bx[op[i].a];
-        int a = op[i].a;
-        if (rank[i] > 0)
-          g1.push_back(mk(q, rank[i], A.cnt, 0, woff[a], A.cnt, 1, 1, A.ucat + (int64_t)A.ucol[op[i].t] * A.cnt,
-                          A.cnt, 0, 2, boff[i], q, 1.0, 0.0));
-        g2.push_back(mk(q, q, A.cnt, 0, woff[a], A.cnt, 1, 3, yoff[i], A.cnt, 0, 2, zoff[i], q, 1.0, 0.0));
-      }
-      // bases: 0 = Wbox, 1 = U pool, 2 = out (B or Z), 3 = Yorig
-      run_gemm(g1, Wbox.as<double>(), UP, Bm.as<double>(), Yorig.as<double>(), s);
-      run_gemm(g2, Wbox.as<double>(), UP, Zm.as<double>(), Yorig.as<double>(), s);
-      // X1 = (B_ab)^+ core  via QR of [B_ab | core]  (q x (r_ab + q))
       const int npr = (int)PL.pr.size();
+      // X1 = (B_ab)^+ core  via QR of [B_ab | core]  (q x (r_ab + q))
       std::vector<QRProb> q1;
       std::vector<CopyProb> cp1;
       std::vector<CoreProb> cores;
@@ -555,7 +708,7 @@ double peel_trace(rsf_handle_s* F, rsf_handle_s* Fk, double tol, const rsf_opts&
         QRProb x{};
         x.m = q; x.c = rab + q; x.cpiv = rab; x.maxk = rab; x.lda = q; x.a = qpool; x.tol = 0.0;
         cp1.push_back({q, rab, q, q, boff[iab], qpool, 0});
-        cores.push_back({zoff[iab], zoff[iba], qpool + (int64_t)q * rab, q});
+        cores.push_back({soff[iab], soff[iba], qpool + (int64_t)q * rab, q, 3 * q});
         qpool += (int64_t)q * (rab + q);
         q1.push_back(x);
       }
@@ -567,7 +720,7 @@ double peel_trace(rsf_handle_s* F, rsf_handle_s* Fk, double tol, const rsf_opts&
           DBuf dc;
           upload(dc, cores, s);
           dim3 grid(cdiv((int64_t)q * q, 256), (unsigned)cores.size());
-          LAUNCH(core_kernel, grid, 256, 0, s, dc.as<CoreProb>(), (int)cores.size(), Zm.as<double>(), W1.as<double>());
+          LAUNCH(core_kernel, grid, 256, 0, s, dc.as<CoreProb>(), (int)cores.size(), Sb.as<double>(), W1.as<double>());
         }
         QRBatch qx;
         qx.build(q1, s);
@@ -604,7 +757,7 @@ double peel_trace(rsf_handle_s* F, rsf_handle_s* Fk, double tol, const rsf_opts&
         }
         // M_ab^T = (B_ba)^+ X1^T via QR of [B_ba | X1^T]  (q x (r_ba + r_ab))
         std::vector<QRProb> q2;
-        std::vector<CopyProb> cp2;
+        std::vector<CopyProb> cp2, cpx;
         int64_t qpool2 = 0;
         for (size_t j = 0; j < live.size(); j++) {
           const PPair& pp = PL.pr[live[j]];
@@ -613,24 +766,14 @@ double peel_trace(rsf_handle_s* F, rsf_handle_s* Fk, double tol, const rsf_opts&
           QRProb x{};
           x.m = q; x.c = rba + rab; x.cpiv = rba; x.maxk = rba; x.lda = q; x.a = qpool2; x.tol = 0.0;
           cp2.push_back({q, rba, q, q, boff[iba], qpool2, 0});
+          cpx.push_back({q, rab, rab, q, xoff[j], qpool2 + (int64_t)q * rba, 1});
           qpool2 += (int64_t)q * (rba + rab);
           q2.push_back(x);
         }
         DBuf W2;
         W2.alloc(sizeof(double) * qpool2, s);
         copy_batched(cp2, Bm.as<double>(), W2.as<double>(), s);
-        {
-          std::vector<CopyProb> cpx;
-          int64_t off2 = 0;
-          for (size_t j = 0; j < live.size(); j++) {
-            const PPair& pp = PL.pr[live[j]];
-            int rab = rank[opidx(pp.a, pp.sa)], rba = rank[opidx(pp.b, pp.sb)];
-            // X1^T (q x r_ab) into columns r_ba.. of the work matrix
-            cpx.push_back({q, rab, rab, q, xoff[j], off2 + (int64_t)q * rba, 1});
-            off2 += (int64_t)q * (rba + rab);
-          }
-          copy_batched(cpx, X1.as<double>(), W2.as<double>(), s);
-        }
+        copy_batched(cpx, X1.as<double>(), W2.as<double>(), s);
         QRBatch qy;
         qy.build(q2, s);
         qy.run(W2.as<double>(), dst, lev, s);
@@ -662,6 +805,7 @@ double peel_trace(rsf_handle_s* F, rsf_handle_s* Fk, double tol, const rsf_opts&
         }
       }
     }
+    if (df) convert_df64(UP + mstart, pool - mstart, 1, s);
     // ---- application descriptors of G^(lev) (bases 0 X, 1 Y, 2 pool, 3 temp)
     {
       std::vector<GemmDesc> gP, gQ, gY;
@@ -676,15 +820,15 @@ double peel_trace(rsf_handle_s* F, rsf_handle_s* Fk, double tol, const rsf_opts&
       }
       for (const PPair& pp : PL.pr) {
         const PBox& A = PL.bx[pp.a];
-        const PBox& B = PL.bx[pp.b];
-        int rab = A.r[pp.sa], rba = B.r[pp.sb];
+        const PBox& Bx = PL.bx[pp.b];
+        int rab = A.r[pp.sa], rba = Bx.r[pp.sb];
         if (rab == 0 || rba == 0) continue;
         // Q_ab^T (nc x r_ab) = P_(b->a)^T (nc x r_ba) M_ab^T
-        gQ.push_back(mk(-1, rab, rba, 3, B.pcol + B.ucol[pp.sb], -1, 0, 2, pp.m, rab, 1, 3,
+        gQ.push_back(mk(-1, rab, rba, 3, Bx.pcol + Bx.ucol[pp.sb], -1, 0, 2, pp.m, rab, 1, 3,
                         PL.sumRa + A.pcol + A.ucol[pp.sa], -1, 1.0, 0.0));
         // Q_ba^T (nc x r_ba) = P_(a->b)^T (nc x r_ab) M_ab
         gQ.push_back(mk(-1, rba, rab, 3, A.pcol + A.ucol[pp.sa], -1, 0, 2, pp.m, rab, 0, 3,
-                        PL.sumRa + B.pcol + B.ucol[pp.sb], -1, 1.0, 0.0));
+                        PL.sumRa + Bx.pcol + Bx.ucol[pp.sb], -1, 1.0, 0.0));
       }
       PL.gP.build(gP, s);
       PL.gQ.build(gQ, s);
@@ -701,18 +845,18 @@ double peel_trace(rsf_handle_s* F, rsf_handle_s* Fk, double tol, const rsf_opts&
   DBuf E, H;
   E.alloc(sizeof(double) * n64 * nl, s);
   H.alloc(sizeof(double) * n64 * nl, s);
-  LAUNCH(unit_cols_kernel, cdiv(n64 * nl, 256), 256, 0, s, dlp.as<int>(), n64, nl, E.as<double>());
+  LAUNCH(unit_cols_kernel, cdiv(n64 * nl, 256), 256, 0, s, dlp.as<int>(), n64, nl, E.as<double>(), df);
   int tk = prof_begin(s);
   applyG(E.as<double>(), H.as<double>(), nl);
   prof_end(tk, s, PROF_PEEL_APPLY, 0, 0);
   tk = prof_begin(s);
-  for (int m = 1; m <= L; m++) apply_level(levels[m], E.as<double>(), H.as<double>(), nl, tmpP, s);
+  for (int m = 1; m <= L; m++) apply_level(levels[m], E.as<double>(), H.as<double>(), nl, tmpP, s, df);
   prof_end(tk, s, PROF_PEEL_SUB, 0, 0);
   int nb = (int)std::min<int64_t>(1024, std::max<int64_t>(1, cdiv(n64, 256)));
   DBuf part, res;
   part.alloc(sizeof(double) * nb, s);
   res.alloc(sizeof(double), s);
-  LAUNCH(diag_trace_kernel, nb, 256, 0, s, H.as<double>(), dlp.as<int>(), n64, nl, part.as<double>());
+  LAUNCH(diag_trace_kernel, nb, 256, 0, s, H.as<double>(), dlp.as<int>(), n64, nl, part.as<double>(), df);
   double* outp = d_out ? d_out : res.as<double>();
   LAUNCH(sum_parts_kernel, 1, 256, 0, s, part.as<double>(), nb, outp);
   double tr = 0;

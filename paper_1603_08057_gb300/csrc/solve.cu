@@ -14,35 +14,67 @@
 // operation of a level is one batched GEMM launch.
 #include <algorithm>
 
+#include "df64.cuh"
 #include "internal.cuh"
 
 namespace rsf {
 
-// X_lev[row] = src >= 0 ? X_up[src] : in[-(1 + src)]   (row length q)
+// X_lev[row] = src >= 0 ? X_up[src] : in[-(1 + src)]   (row length q); rows
+// taken from the input are converted to df64 pairs when cvt is set.
 __global__ void gather_rows_kernel(const int* __restrict__ src, int64_t nrows, int q,
                                    const double* __restrict__ child, const double* __restrict__ in,
-                                   double* __restrict__ out) {
+                                   double* __restrict__ out, int cvt) {
   int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   int lane = threadIdx.x & 31;
   if (row >= nrows) return;
   int s = src[row];
   const double* from = s >= 0 ? child + (int64_t)s * q : in + (int64_t)(-(1 + s)) * q;
   double* to = out + row * q;
-  for (int c = lane; c < q; c += 32) to[c] = from[c];
+  if (cvt && s < 0) {
+    for (int c = lane; c < q; c += 32) {
+      df64 v = df_from_double(from[c]);
+      reinterpret_cast<float2*>(to)[c] = make_float2(v.hi, v.lo);
+    }
+  } else {
+    for (int c = lane; c < q; c += 32) to[c] = from[c];
+  }
 }
 
 // Inverse of the gather: rows with src >= 0 go back to the level below, leaf
 // rows to the output.
 __global__ void scatter_rows_kernel(const int* __restrict__ src, int64_t nrows, int q,
                                     const double* __restrict__ lev, double* __restrict__ child,
-                                    double* __restrict__ out) {
+                                    double* __restrict__ out, int cvt) {
   int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   int lane = threadIdx.x & 31;
   if (row >= nrows) return;
   int s = src[row];
   double* to = s >= 0 ? child + (int64_t)s * q : out + (int64_t)(-(1 + s)) * q;
   const double* from = lev + row * q;
-  for (int c = lane; c < q; c += 32) to[c] = from[c];
+  if (cvt && s < 0) {
+    for (int c = lane; c < q; c += 32) {
+      float2 f = reinterpret_cast<const float2*>(from)[c];
+      to[c] = df_to_double({f.x, f.y});
+    }
+  } else {
+    for (int c = lane; c < q; c += 32) to[c] = from[c];
+  }
+}
+
+__global__ void convert_df64_kernel(double* __restrict__ p, int64_t n, int to) {
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  if (to) {
+    df64 v = df_from_double(p[g]);
+    reinterpret_cast<float2*>(p)[g] = make_float2(v.hi, v.lo);
+  } else {
+    float2 f = reinterpret_cast<const float2*>(p)[g];
+    p[g] = df_to_double({f.x, f.y});
+  }
+}
+
+void convert_df64(double* p, int64_t n, int to, cudaStream_t s) {
+  if (n > 0) LAUNCH(convert_df64_kernel, cdiv(n, 256), 256, 0, s, p, n, to);
 }
 
 // Copy the R rows (ranges) of a level between two buffers.
@@ -57,15 +89,19 @@ __global__ void copy_ranges_kernel(const int64_t* __restrict__ rr, int nrr, int 
 }
 
 static void run_level_gemm(const GemmBatch& g, double* X, double* tmp, double* pool, int q, double alpha,
-                           cudaStream_t s) {
+                           cudaStream_t s, int df) {
   GemmBases b{};
+  b.df = df;
   b.p[0] = X; b.p[1] = tmp; b.p[2] = pool; b.p[3] = nullptr;
   b.sc[0] = q; b.sc[1] = q; b.sc[2] = 1; b.sc[3] = 1;
   b.M = q; b.ld = q; b.alpha_scale = alpha;
   g.run(b, s);
 }
 
-void solve_rows(rsf_handle_s* h, int op, const double* in, double* out, int q) {
+void solve_rows(rsf_handle_s* h, int op, const double* in, double* out, int q, int io_df) {
+  const int df = h->df ? 1 : 0;
+  const int cvt = (df && !io_df) ? 1 : 0;
+  RSF_CHECK(!io_df || df, RSF_EINVAL, "df64 input needs a mixed-precision factorization");
   cudaStream_t s = h->stream;
   const int L = (int)h->levels.size() - 1;
   RSF_CHECK(q >= 1, RSF_EINVAL, "nrhs must be >= 1");
@@ -97,15 +133,15 @@ void solve_rows(rsf_handle_s* h, int op, const double* in, double* out, int q) {
     LevelData& Lv = h->levels[l];
     if (Lv.nrows == 0) continue;
     const double* child = (l < L) ? Xl(l + 1) : nullptr;
-    LAUNCH(gather_rows_kernel, cdiv(Lv.nrows, 8), 256, 0, s, Lv.src.as<int>(), Lv.nrows, q, child, in, Xl(l));
+    LAUNCH(gather_rows_kernel, cdiv(Lv.nrows, 8), 256, 0, s, Lv.src.as<int>(), Lv.nrows, q, child, in, Xl(l), cvt);
     if (l == 0) break;
     double* F = Lv.fpool.as<double>();
     if (up == 1) {
-      run_level_gemm(Lv.gRS_T, Xl(l), tmp.as<double>(), F, q, -1.0, s);
-      run_level_gemm(Lv.gSR_Et, Xl(l), tmp.as<double>(), F, q, -1.0, s);
+      run_level_gemm(Lv.gRS_T, Xl(l), tmp.as<double>(), F, q, -1.0, s, df);
+      run_level_gemm(Lv.gSR_Et, Xl(l), tmp.as<double>(), F, q, -1.0, s, df);
     } else if (up == 2) {
-      run_level_gemm(Lv.gSR_Tt, Xl(l), tmp.as<double>(), F, q, 1.0, s);
-      run_level_gemm(Lv.gRS_E, Xl(l), tmp.as<double>(), F, q, 1.0, s);
+      run_level_gemm(Lv.gSR_Tt, Xl(l), tmp.as<double>(), F, q, 1.0, s, df);
+      run_level_gemm(Lv.gRS_E, Xl(l), tmp.as<double>(), F, q, 1.0, s, df);
     }
   }
   // block-diagonal middle factor on the R rows of every level
@@ -121,6 +157,7 @@ void solve_rows(rsf_handle_s* h, int op, const double* in, double* out, int q) {
       b.p[0] = from_tmp ? t : x; b.p[1] = from_tmp ? x : t; b.p[2] = F; b.p[3] = nullptr;
       b.sc[0] = q; b.sc[1] = q; b.sc[2] = 1; b.sc[3] = 1;
       b.M = q; b.ld = q; b.alpha_scale = 1.0;
+      b.df = df;
       Lv.gMid[v].run(b, s);
     };
     auto copy_to_tmp = [&]() {
@@ -145,15 +182,15 @@ void solve_rows(rsf_handle_s* h, int op, const double* in, double* out, int q) {
     double* F = Lv.fpool.as<double>();
     if (l > 0) {
       if (down == 1) {
-        run_level_gemm(Lv.gRS_E, Xl(l), tmp.as<double>(), F, q, -1.0, s);
-        run_level_gemm(Lv.gSR_Tt, Xl(l), tmp.as<double>(), F, q, -1.0, s);
+        run_level_gemm(Lv.gRS_E, Xl(l), tmp.as<double>(), F, q, -1.0, s, df);
+        run_level_gemm(Lv.gSR_Tt, Xl(l), tmp.as<double>(), F, q, -1.0, s, df);
       } else if (down == 2) {
-        run_level_gemm(Lv.gSR_Et, Xl(l), tmp.as<double>(), F, q, 1.0, s);
-        run_level_gemm(Lv.gRS_T, Xl(l), tmp.as<double>(), F, q, 1.0, s);
+        run_level_gemm(Lv.gSR_Et, Xl(l), tmp.as<double>(), F, q, 1.0, s, df);
+        run_level_gemm(Lv.gRS_T, Xl(l), tmp.as<double>(), F, q, 1.0, s, df);
       }
     }
     double* child = (l < L) ? Xl(l + 1) : nullptr;
-    LAUNCH(scatter_rows_kernel, cdiv(Lv.nrows, 8), 256, 0, s, Lv.src.as<int>(), Lv.nrows, q, Xl(l), child, out);
+    LAUNCH(scatter_rows_kernel, cdiv(Lv.nrows, 8), 256, 0, s, Lv.src.as<int>(), Lv.nrows, q, Xl(l), child, out, cvt);
   }
 }
 
