@@ -148,6 +148,26 @@ rsf_status rsf_logdet(rsf_handle h, double* out);
  * original point order).  Stream-ordered (does not synchronise). */
 rsf_status rsf_solve(rsf_handle h, double* B, int64_t ldb, int nrhs, int op);
 
+/* rsf_solve without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory at
+ * solve time -- code running inside another framework's memory budget (its
+ * caching allocator has already reserved the device memory, so cudaMalloc
+ * would fail or fragment that pool) and latency-critical loops that must not
+ * pay for an allocation's implicit synchronisation.
+ *
+ * Same arguments, result and errors as rsf_solve, but every work buffer is
+ * carved from one file-scope device array of RSF_NOALLOC_SCRATCH_DOUBLES
+ * doubles (32 MiB), which every GPU that loads the library holds until the
+ * process exits.  A call needs nrhs * (2 n + the active DOFs of all levels +
+ * those of the largest level) doubles; larger requests return RSF_EINVAL
+ * without touching B.  The first call on a device (with that device current)
+ * looks up the array's device address; make that first call before any
+ * stream capture.  All calls share the one array and nothing in it needs to
+ * start at zero, but calls whose work overlaps on the GPU (different streams,
+ * or concurrent host threads) race on it: serialise them. */
+#define RSF_NOALLOC_SCRATCH_DOUBLES (1 << 22)
+rsf_status rsf_solve_noalloc(rsf_handle h, double* B, int64_t ldb, int nrhs, int op);
+
 /* Trace by weak peeling (Sec. 3) to *trace (host): Tr(F^-1) when Fk is NULL,
  * else Tr((F^-1 Fk + Fk F^-1)/2) (Algorithm 1).  tol_peel is the relative
  * cut-off of the sibling-block ranks.  Synchronises. */

@@ -25,7 +25,8 @@ STATUS = {0: "RSF_OK", 1: "RSF_EINVAL", 2: "RSF_ENOMEM", 3: "RSF_ENOTPD",
 EXPORTS = ["rsf_opts_default", "rsf_last_error", "rsf_tree_build", "rsf_tree_destroy",
            "rsf_build", "rsf_build_on_tree", "rsf_logdet", "rsf_solve", "rsf_peel_trace",
            "gp_loglik", "gp_score", "gp_loglik_and_score", "rsf_get_info",
-           "rsf_launch_count", "rsf_profile_enable", "rsf_profile_read", "rsf_destroy"]
+           "rsf_launch_count", "rsf_profile_enable", "rsf_profile_read", "rsf_destroy",
+           "rsf_solve_noalloc"]
 
 
 class RsfKernel(C.Structure):
@@ -78,6 +79,7 @@ def lib():
                                         C.POINTER(RsfOpts), C.POINTER(vp)]
         L.rsf_logdet.argtypes = [vp, dp]
         L.rsf_solve.argtypes = [vp, vp, i64, ip, ip]
+        L.rsf_solve_noalloc.argtypes = [vp, vp, i64, ip, ip]
         L.rsf_peel_trace.argtypes = [vp, vp, C.c_double, C.POINTER(RsfOpts), dp]
         L.gp_loglik.argtypes = [vp, vp, vp, dp, dp]
         L.gp_score.argtypes = [vp, vp, C.c_double, C.c_double, C.POINTER(RsfOpts), dp, dp]
@@ -208,6 +210,16 @@ class Factorization:
         # column-major n x nrhs = transpose of a row-major nrhs x n array
         Xc = X.t().contiguous()
         _check(lib().rsf_solve(self.h, Xc.data_ptr(), self.n, Xc.shape[0], op))
+        out = Xc.t()
+        return out.reshape(-1) if vec else out.contiguous()
+
+    def solve_noalloc(self, B: torch.Tensor, op=OP_INV) -> torch.Tensor:
+        """op(F) B through rsf_solve_noalloc (no device allocation inside the
+        library call; its work buffers live in the library's fixed scratch)."""
+        vec = B.dim() == 1
+        X = _dev(B).reshape(self.n, -1)
+        Xc = X.t().contiguous()
+        _check(lib().rsf_solve_noalloc(self.h, Xc.data_ptr(), self.n, Xc.shape[0], op))
         out = Xc.t()
         return out.reshape(-1) if vec else out.contiguous()
 

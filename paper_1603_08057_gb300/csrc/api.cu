@@ -160,6 +160,9 @@ __global__ void sum_logdet_kernel(const double* __restrict__ parts, int n, doubl
   if (threadIdx.x == 0) *out = red[0];
 }
 
+// rsf_solve with its work buffers in the library's fixed scratch (noalloc.cu).
+void solve_noalloc(rsf_handle_s* h, double* B, int64_t ldb, int nrhs, int op);
+
 // Two trees are interchangeable when their box tables and point orders agree
 // (e.g. built twice from the same points).
 static bool same_tree(rsf_tree_s* a, rsf_tree_s* b) {
@@ -333,6 +336,17 @@ rsf_status rsf_solve(rsf_handle h, double* B, int64_t ldb, int nrhs, int op) {
   LAUNCH(to_tree_kernel, cdiv(n * nrhs, 256), 256, 0, s, B, ldb, nrhs, perm, n, X.as<double>());
   solve_rows(h, op, X.as<double>(), Y.as<double>(), nrhs);
   LAUNCH(from_tree_kernel, cdiv(n * nrhs, 256), 256, 0, s, Y.as<double>(), n, nrhs, perm, B, ldb);
+  API_END
+}
+
+rsf_status rsf_solve_noalloc(rsf_handle h, double* B, int64_t ldb, int nrhs, int op) {
+  API_BEGIN
+  RSF_CHECK(h && B, RSF_EINVAL, "handle and B must not be NULL");
+  const int64_t n = h->tree_raw->t.n;
+  RSF_CHECK(nrhs >= 1 && ldb >= n, RSF_EINVAL, "need nrhs >= 1 and ldb >= n");
+  RSF_CHECK(op >= RSF_OP_INV && op <= RSF_OP_INV_SQRT_T, RSF_EINVAL, "unknown op");
+  RSF_CHECK(h->spd || op == RSF_OP_APPLY, RSF_EINVAL, "only APPLY is defined for a derivative factorization");
+  solve_noalloc(h, B, ldb, nrhs, op);
   API_END
 }
 
