@@ -120,6 +120,20 @@ def dist_env():
     return ws, rank, local
 
 
+def replica_throughput(ms_local: float, steps: int, device=None) -> tuple[float, float]:
+    """Whole-job throughput of independent replicas: every rank ran `steps`
+    evaluations in `ms_local` ms; the job time is the max over ranks (needs an
+    initialised process group when WORLD_SIZE > 1).  Returns (evals/s, max ms)."""
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ws * steps / (ms_max / 1e3), ms_max
+
+
 def workload_config(n):
     wl = WL.WORKLOADS[WORKLOAD]
     return wl, {"workload": f"matern32 nu=3/2 mixture n={n}", "n": n, "points": "uniform+4 clusters (sigma 0.03)",
@@ -232,11 +246,7 @@ def run_gpu(args):
     launches = B.launch_count(reset=True)
     prof = {c: B.profile_read(c, reset=True) for c in range(len(B.PROF_NAMES))}
     B.profile(False)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = ws * args.steps / (ms_max / 1e3)
+    value, ms_max = replica_throughput(ms, args.steps, device="cuda")
 
     # end to end through the public API with host buffers: H2D of points and
     # z every step, the call, D2H of the log-likelihood and score
