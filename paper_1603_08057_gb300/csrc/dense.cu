@@ -11,6 +11,9 @@ namespace rsf {
 // Tile BM x BN = 64 x 32, BK = 16, 128 threads; each thread owns a 4 x 4
 // register tile (rows tm + 16 i, cols tn + 8 j).  fp64 FMA.
 constexpr int BM = 64, BN = 32, BK = 16, GT = 128;
+#ifndef GEMM_MIN_BLOCKS
+#define GEMM_MIN_BLOCKS 1
+#endif
 
 __device__ __forceinline__ int find_prob(const int* prefix, int nprob, int tile) {
   int lo = 0, hi = nprob - 1;
@@ -20,6 +23,16 @@ __device__ __forceinline__ int find_prob(const int* prefix, int nprob, int tile)
   }
   return lo;
 }
+
+// Asynchronous 8-byte global -> shared copy (zero-fill when !pred).
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool pred) {
+  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  int sz = pred ? 8 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(sz) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // Element access for the two arithmetic modes: fp64, or df64 (8-byte
 // float2 pairs, products accumulated with error-free transformations).
@@ -60,7 +73,7 @@ template <> struct Arith<true> {
 };
 
 template <bool DF>
-__global__ void __launch_bounds__(GT) gemm_kernel(const GemmDesc* __restrict__ descs,
+__global__ void __launch_bounds__(GT, GEMM_MIN_BLOCKS) gemm_kernel(const GemmDesc* __restrict__ descs,
                                                   const int* __restrict__ prefix, int nprob,
                                                   GemmBases bases) {
   typedef Arith<DF> AR;
@@ -89,8 +102,11 @@ __global__ void __launch_bounds__(GT) gemm_kernel(const GemmDesc* __restrict__ d
   if (d.triB == 1) k0 = min(n0, K);
   if (d.triB == 2) k1 = min(K, n0 + BN);
 
-  __shared__ T sA[BK][BM + 1];
-  __shared__ T sB[BK][BN + 1];
+  // Two shared-memory stages filled with cp.async: the loads of tile k+1 are
+  // in flight while tile k is multiplied.  Out-of-range and masked elements
+  // are zero-filled by the copy itself (source size 0).
+  __shared__ __align__(16) T sA[2][BK][BM + 1];
+  __shared__ __align__(16) T sB[2][BK][BN + 1];
   const int t = threadIdx.x;
   const int tm = t & 15, tn = t >> 4;
   typename AR::Acc acc[4][4];
@@ -99,19 +115,20 @@ __global__ void __launch_bounds__(GT) gemm_kernel(const GemmDesc* __restrict__ d
 #pragma unroll
     for (int j = 0; j < 4; j++) acc[i][j] = AR::acc0();
 
-  for (int kb = k0; kb < k1; kb += BK) {
+  auto load_tile = [&](int kb, int st) {
 #pragma unroll
     for (int r = 0; r < (BM * BK) / GT; r++) {
       int idx = t + r * GT;
       int mm, kk;
       if (!d.ta) { mm = idx % BM; kk = idx / BM; } else { kk = idx % BK; mm = idx / BK; }
       int gm = m0 + mm, gk = kb + kk;
-      T v = AR::zero();
-      if (gm < M && gk < k1) {
-        if (d.gatherK) v = AR::load(A + gm + (int64_t)bases.kidx[d.kofs + gk] * lda);
-        else v = AR::load(d.ta ? A + gk + (int64_t)gm * lda : A + gm + (int64_t)gk * lda);
+      bool ok = gm < M && gk < k1;
+      const double* src = A;
+      if (ok) {
+        if (d.gatherK) src = A + gm + (int64_t)bases.kidx[d.kofs + gk] * lda;
+        else src = d.ta ? A + gk + (int64_t)gm * lda : A + gm + (int64_t)gk * lda;
       }
-      sA[kk][mm] = v;
+      cp_async8(&sA[st][kk][mm], src, ok);
     }
 #pragma unroll
     for (int r = 0; r < (BN * BK) / GT; r++) {
@@ -119,28 +136,40 @@ __global__ void __launch_bounds__(GT) gemm_kernel(const GemmDesc* __restrict__ d
       int nn, kk;
       if (!d.tb) { kk = idx % BK; nn = idx / BK; } else { nn = idx % BN; kk = idx / BN; }
       int gn = n0 + nn, gk = kb + kk;
-      T v = AR::zero();
-      if (gn < N && gk < k1) {
-        bool zero = (d.triB == 1 && gk < gn) || (d.triB == 2 && gk > gn);
-        if (d.gatherK) v = AR::load(B + (bases.kidx[d.kofs + gk] - d.kb0) + (int64_t)gn * ldb);
-        else if (!zero) v = AR::load(d.tb ? B + gn + (int64_t)gk * ldb : B + gk + (int64_t)gn * ldb);
+      bool ok = gn < N && gk < k1;
+      if (ok && !d.gatherK && !d.gatherN) ok = !((d.triB == 1 && gk < gn) || (d.triB == 2 && gk > gn));
+      const double* src = B;
+      if (ok) {
+        if (d.gatherK) src = B + (bases.kidx[d.kofs + gk] - d.kb0) + (int64_t)gn * ldb;
+        else if (d.gatherN) src = B + (bases.kidx[d.nofs + gn] - d.nb0) + (int64_t)gk * ldb;
+        else src = d.tb ? B + gn + (int64_t)gk * ldb : B + gk + (int64_t)gn * ldb;
       }
-      sB[kk][nn] = v;
+      cp_async8(&sB[st][kk][nn], src, ok);
     }
+    cp_async_commit();
+  };
+
+  int st = 0;
+  if (k0 < k1) load_tile(k0, 0);
+  for (int kb = k0; kb < k1; kb += BK) {
+    const bool more = kb + BK < k1;
+    if (more) load_tile(kb + BK, st ^ 1);
+    if (more) cp_async_wait<1>(); else cp_async_wait<0>();
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; kk++) {
       T a[4], b[4];
 #pragma unroll
-      for (int i = 0; i < 4; i++) a[i] = sA[kk][tm + 16 * i];
+      for (int i = 0; i < 4; i++) a[i] = sA[st][kk][tm + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; j++) b[j] = sB[kk][tn + 8 * j];
+      for (int j = 0; j < 4; j++) b[j] = sB[st][kk][tn + 8 * j];
 #pragma unroll
       for (int i = 0; i < 4; i++)
 #pragma unroll
         for (int j = 0; j < 4; j++) AR::mac(acc[i][j], a[i], b[j]);
     }
     __syncthreads();
+    st ^= 1;
   }
   const double alpha = d.alpha * bases.alpha_scale, beta = d.beta;
 #pragma unroll
@@ -152,7 +181,8 @@ __global__ void __launch_bounds__(GT) gemm_kernel(const GemmDesc* __restrict__ d
       int gn = n0 + tn + 8 * j;
       if (gn >= N) continue;
       if (d.lowC && gm < gn) continue;
-      AR::store(C + gm + (int64_t)gn * ldc, acc[i][j], alpha, beta);
+      const int64_t cn = d.gatherN ? (int64_t)bases.kidx[d.nofs + gn] : (int64_t)gn;
+      AR::store(C + gm + cn * ldc, acc[i][j], alpha, beta);
     }
   }
 }

@@ -24,6 +24,10 @@ struct GemmDesc {
   double alpha, beta;
   int64_t kofs;
   int64_t kb0;
+  int8_t gatherN;  // 1: the N index runs over kidx[nofs .. nofs + N): B row
+                   //    of op(B) (tb = 1) kidx[.] - nb0, C column kidx[.]
+  int64_t nofs;
+  int64_t nb0;
 };
 
 struct GemmBases {
