@@ -357,10 +357,12 @@ rsf_status rsf_peel_trace(rsf_handle F, rsf_handle Fk, double tol_peel, const rs
   RSF_CHECK(!Fk || same_tree(Fk->tree_raw, F->tree_raw), RSF_EINVAL, "F and Fk must be built on the same tree");
   RSF_CHECK(tol_peel > 0.0 && tol_peel < 1.0, RSF_EINVAL, "tol_peel must be in (0, 1)");
   rsf_opts o = resolve_opts(opts);
-  double t = peel_trace(F, Fk, tol_peel, o, nullptr);
+  double* const dnone[2] = {nullptr, nullptr};
+  double t[2] = {0.0, 0.0};
+  peel_traces(F, Fk, false, tol_peel, o, dnone, t);
   check_status(F);
   if (Fk) check_status(Fk);
-  *trace = t;
+  *trace = Fk ? t[1] : t[0];
   API_END
 }
 
@@ -415,8 +417,10 @@ rsf_status gp_score(rsf_handle F, const double* alpha, double tol_fact, double t
   dot_into(at.as<double>(), ft.as<double>(), n, sc.as<double>() + S_QL, s);
   solve_rows(F, RSF_OP_APPLY, at.as<double>(), ft.as<double>(), 1);
   dot_into(at.as<double>(), ft.as<double>(), n, sc.as<double>() + S_QF, s);
-  peel_trace(F, nullptr, tol_peel, o, sc.as<double>() + S_TNUG);
-  peel_trace(F, Fl.get(), tol_peel, o, sc.as<double>() + S_TL);
+  // Tr(F^-1) and Tr(G_l) peeled together on shared test matrices
+  double* const dtr[2] = {sc.as<double>() + S_TNUG, sc.as<double>() + S_TL};
+  double htr[2];
+  peel_traces(F, Fl.get(), true, tol_peel, o, dtr, htr);
   LAUNCH(score_kernel, 1, 32, 0, s, sc.as<double>(), n, F->kp.s2, F->kp.nug);
   double h[S_NSLOTS];
   d2h(h, sc.as<double>(), S_NSLOTS, s);

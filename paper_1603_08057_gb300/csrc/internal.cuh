@@ -154,7 +154,11 @@ void check_status(rsf_handle_s* h);
 void solve_rows(rsf_handle_s* h, int op, const double* in, double* out, int q, int io_df = 0);
 // In-place conversion of n doubles to df64 pairs (to = 1) or back (to = 0).
 void convert_df64(double* p, int64_t n, int to, cudaStream_t s);
-double peel_trace(rsf_handle_s* F, rsf_handle_s* Fk, double tol, const rsf_opts& o, double* d_out);
+// Peeled traces (Sec. 3) of G_0 = F^-1 (when want0 or Fk is null) and of
+// G_1 = (F^-1 Fk + Fk F^-1)/2 (when Fk is given), sharing every test matrix.
+// Operator i's trace goes to d_out[i] (a device scalar, may be null) and h_out[i].
+void peel_traces(rsf_handle_s* F, rsf_handle_s* Fk, bool want0, double tol, const rsf_opts& o,
+                 double* const d_out[2], double h_out[2]);
 // device reductions
 double dot_device(const double* a, const double* b, int64_t n, cudaStream_t s);
 // a . b into a device scalar (stream ordered, no synchronisation)

@@ -354,12 +354,48 @@ void apply_level_sparse(const PLevel& P, const double* X, double* Y, int qc, con
   b.M = nc; b.ld = nc; b.alpha_scale = 1.0;
   b.df = df;
   P.gQ.run(b, s);
-  P.gY.run(b, s);
+  // Y(rows of slot s, column block k)^T -= Q_a(block k)^T Ucat_a(rows, :)^T for
+  // k != s only: a box's own-slot samples are never used, and rows outside
+  // the level's sibling boxes need none
+  std::vector<GemmDesc> gy;
+  for (const PBox& A : P.bx) {
+    if (A.Ra == 0) continue;
+    for (int sl = 0; sl < 4; sl++) {
+      auto b0 = slotlist.begin() + sb[sl], b1 = slotlist.begin() + sb[sl + 1];
+      auto lo = std::lower_bound(b0, b1, A.start), hi = std::lower_bound(b0, b1, A.start + A.cnt);
+      if (hi == lo) continue;
+      for (int k = 0; k < 4; k++) {
+        if (k == sl) continue;
+        GemmDesc d = mk(qc, (int)(hi - lo), A.Ra, 3, (P.sumRa + A.pcol) * nc + (int64_t)k * qc, nc, 0, 2, A.ucat,
+                        A.cnt, 1, 1, (int64_t)k * qc, nc, -1.0, 1.0);
+        d.gatherN = 1;
+        d.nofs = lo - slotlist.begin();
+        d.nb0 = A.start;
+        gy.push_back(d);
+      }
+    }
+  }
+  GemmBatch gb;
+  gb.build(gy, s);
+  GemmBases c{};
+  c.p[0] = const_cast<double*>(X); c.p[1] = Y; c.p[2] = P.pool.as<double>(); c.p[3] = tmp.as<double>();
+  c.sc[0] = c.sc[1] = c.sc[2] = c.sc[3] = 1;
+  c.alpha_scale = 1.0;
+  c.df = df;
+  c.kidx = d_slotlist;
+  gb.run(c, s);
 }
 
 }  // namespace
 
-double peel_trace(rsf_handle_s* F, rsf_handle_s* Fk, double tol, const rsf_opts& o, double* d_out) {
+// Peels the traces of up to two symmetric operators together (Sec. 3):
+//   operator 0: G_0 = F^-1                          (when want0)
+//   operator 1: G_1 = (F^-1 F_k + F_k F^-1) / 2     (when Fk is given)
+// Both share every test matrix and sketch, and F^-1 W -- one of the four
+// multi-RHS applications G_1 W needs -- is G_0 W, so peeling both costs the
+// applications of G_1 alone.
+void peel_traces(rsf_handle_s* F, rsf_handle_s* Fk, bool want0, double tol, const rsf_opts& o,
+                 double* const d_out[2], double h_out[2]) {
   cudaStream_t s = F->stream;
   TreeData& T = F->tree_raw->t;
   const int64_t n = T.n;
@@ -368,48 +404,61 @@ double peel_trace(rsf_handle_s* F, rsf_handle_s* Fk, double tol, const rsf_opts&
   DevStatus* dst = F->status.as<DevStatus>();
   int64_t n64 = n;
   const int df = F->df ? 1 : 0;
+  std::vector<int> ops;
+  if (want0 || !Fk) ops.push_back(0);
+  if (Fk) ops.push_back(1);
+  const int nops = (int)ops.size();
 
-  // G application on row-major tree-order blocks
-  DBuf ga, gb2, gw;
-  auto applyG = [&](const double* in, double* out, int q) {
+  // G_o W for the wanted operators, row-major tree-order blocks in F's
+  // arithmetic (df64 pairs when F is mixed precision)
+  DBuf ga, gb2, gw, gx;
+  auto applyG = [&](const double* in, double* const out[2], int q) {
+    const int64_t cnt = n64 * q;
+    const int64_t bytes = sizeof(double) * cnt;
     if (!Fk) {
-      solve_rows(F, RSF_OP_INV, in, out, q, df);
+      solve_rows(F, RSF_OP_INV, in, out[0], q, df);
       return;
     }
-    int64_t bytes = sizeof(double) * n64 * q;
     if ((int64_t)ga.bytes < bytes) ga.alloc(bytes, s);
     if ((int64_t)gb2.bytes < bytes) gb2.alloc(bytes, s);
     if (df && !Fk->df) {
       // F in df64, F_k in fp64: work on doubles, return df64 pairs
       if ((int64_t)gw.bytes < bytes) gw.alloc(bytes, s);
+      if ((int64_t)gx.bytes < bytes) gx.alloc(bytes, s);
       RSF_CUDA(cudaMemcpyAsync(gw.p, in, bytes, cudaMemcpyDeviceToDevice, s));
-      convert_df64(gw.as<double>(), n64 * q, 0, s);
+      convert_df64(gw.as<double>(), cnt, 0, s);
+      solve_rows(F, RSF_OP_INV, gw.as<double>(), gx.as<double>(), q, 0);     // F^-1 W
+      if (want0) {
+        RSF_CUDA(cudaMemcpyAsync(out[0], gx.p, bytes, cudaMemcpyDeviceToDevice, s));
+        convert_df64(out[0], cnt, 1, s);
+      }
       solve_rows(Fk, RSF_OP_APPLY, gw.as<double>(), ga.as<double>(), q, 0);
       solve_rows(F, RSF_OP_INV, ga.as<double>(), gb2.as<double>(), q, 0);   // F^-1 F_k W
-      solve_rows(F, RSF_OP_INV, gw.as<double>(), ga.as<double>(), q, 0);
-      solve_rows(Fk, RSF_OP_APPLY, ga.as<double>(), out, q, 0);             // F_k F^-1 W
-      LAUNCH(average_kernel, cdiv(n64 * q, 256), 256, 0, s, out, gb2.as<double>(), n64 * q, 0);
-      convert_df64(out, n64 * q, 1, s);
+      solve_rows(Fk, RSF_OP_APPLY, gx.as<double>(), out[1], q, 0);          // F_k F^-1 W
+      LAUNCH(average_kernel, cdiv(cnt, 256), 256, 0, s, out[1], gb2.as<double>(), cnt, 0);
+      convert_df64(out[1], cnt, 1, s);
       return;
     }
+    double* x3 = want0 ? out[0] : gb2.as<double>();
+    solve_rows(F, RSF_OP_INV, in, x3, q, df);                              // F^-1 W
+    solve_rows(Fk, RSF_OP_APPLY, x3, out[1], q, df);                       // F_k F^-1 W
     solve_rows(Fk, RSF_OP_APPLY, in, ga.as<double>(), q, df);
-    solve_rows(F, RSF_OP_INV, ga.as<double>(), gb2.as<double>(), q, df);   // F^-1 F_k W
-    solve_rows(F, RSF_OP_INV, in, ga.as<double>(), q, df);
-    solve_rows(Fk, RSF_OP_APPLY, ga.as<double>(), out, q, df);             // F_k F^-1 W
-    LAUNCH(average_kernel, cdiv(n64 * q, 256), 256, 0, s, out, gb2.as<double>(), n64 * q, df);
+    double* x2 = want0 ? gb2.as<double>() : x3;
+    solve_rows(F, RSF_OP_INV, ga.as<double>(), x2, q, df);                 // F^-1 F_k W
+    LAUNCH(average_kernel, cdiv(cnt, 256), 256, 0, s, out[1], x2, cnt, df);
   };
 
-  std::vector<PLevel> levels(L + 1);
+  std::vector<PLevel> levels[2];
+  levels[0].resize(L + 1);
+  levels[1].resize(L + 1);
   DBuf tmpP;  // P/Q temps for apply_level
   std::vector<int> slotrow(n);
   DBuf dslot;
-  int r_prev = 0;
-  int max_rank_seen = 0;
+  int r_prev[2] = {0, 0};
 
   for (int lev = 1; lev <= L; lev++) {
-    PLevel& PL = levels[lev];
-    PL.lev = lev;
-    // boxes at this level with at least one sibling
+    PLevel TL;  // the level's boxes and sibling pairs (shared by both operators)
+    TL.lev = lev;
     std::vector<int> idx_of(T.level.size(), -1);
     for (int b : T.by_level[lev]) {
       int par = T.parent[b];
@@ -418,12 +467,11 @@ double peel_trace(rsf_handle_s* F, rsf_handle_s* Fk, double tol, const rsf_opts&
       if (nsib < 2) continue;
       PBox pb{};
       pb.box = b; pb.start = T.start[b]; pb.cnt = T.count[b]; pb.slot = T.slot[b];
-      idx_of[b] = (int)PL.bx.size();
-      PL.bx.push_back(pb);
+      idx_of[b] = (int)TL.bx.size();
+      TL.bx.push_back(pb);
     }
-    if (PL.bx.empty()) continue;
-    PL.active = true;
-    for (auto& pb : PL.bx) {
+    if (TL.bx.empty()) continue;
+    for (auto& pb : TL.bx) {
       int par = T.parent[pb.box];
       pb.nsib = 0;
       for (int sl = 0; sl < 4; sl++) {
@@ -431,20 +479,20 @@ double peel_trace(rsf_handle_s* F, rsf_handle_s* Fk, double tol, const rsf_opts&
         if (c >= 0 && c != pb.box) pb.sib[pb.nsib++] = idx_of[c];
       }
     }
-    for (int a = 0; a < (int)PL.bx.size(); a++)
-      for (int t = 0; t < PL.bx[a].nsib; t++) {
-        int b = PL.bx[a].sib[t];
+    for (int a = 0; a < (int)TL.bx.size(); a++)
+      for (int t = 0; t < TL.bx[a].nsib; t++) {
+        int b = TL.bx[a].sib[t];
         if (a < b) {
           PPair pp{};
           pp.a = a; pp.b = b; pp.sa = t;
-          for (int u = 0; u < PL.bx[b].nsib; u++)
-            if (PL.bx[b].sib[u] == a) pp.sb = u;
-          PL.pr.push_back(pp);
+          for (int u = 0; u < TL.bx[b].nsib; u++)
+            if (TL.bx[b].sib[u] == a) pp.sb = u;
+          TL.pr.push_back(pp);
         }
       }
-    const int nbx = (int)PL.bx.size();
+    const int nbx = (int)TL.bx.size();
     std::fill(slotrow.begin(), slotrow.end(), -1);
-    for (auto& pb : PL.bx)
+    for (auto& pb : TL.bx)
       for (int i = 0; i < pb.cnt; i++) slotrow[pb.start + i] = pb.slot;
     upload(dslot, slotrow, s);
     // rows of each slot in tree order (the nonzero rows of W_k)
@@ -463,378 +511,445 @@ double peel_trace(rsf_handle_s* F, rsf_handle_s* Fk, double tol, const rsf_opts&
     struct OPair { int a, t; };
     std::vector<OPair> op;
     for (int a = 0; a < nbx; a++)
-      for (int t = 0; t < PL.bx[a].nsib; t++) op.push_back({a, t});
+      for (int t = 0; t < TL.bx[a].nsib; t++) op.push_back({a, t});
     const int nop = (int)op.size();
     std::vector<int> opbase(nbx + 1, 0);
-    for (int a = 0; a < nbx; a++) opbase[a + 1] = opbase[a] + PL.bx[a].nsib;
+    for (int a = 0; a < nbx; a++) opbase[a + 1] = opbase[a] + TL.bx[a].nsib;
     auto opidx = [&](int a, int t) { return opbase[a] + t; };
 
-    // Initial sample count: at level 1 nine tenths of the largest level-1
-    // skeleton of F (the sibling-block ranks at eps_peel sit below the ID
-    // ranks at eps_fact), deeper down nine tenths of the previous level's
-    // largest rank (ranks shrink slowly towards the leaves).
-    int q0 = 8;
-    if (lev == 1) {
-      q0 = std::max(o.q0, 1);
-      if (F->levels.size() > 1)
-        for (int kk : F->levels[1].k) q0 = std::max(q0, (9 * kk) / 10);
-    } else {
-      q0 = std::max(8, (9 * r_prev) / 10);
+    // Per-operator sample counts.  Initial guess: at level 1 nine tenths of
+    // the largest level-1 skeleton of F (the sibling-block ranks at eps_peel
+    // sit below the ID ranks at eps_fact); below, a fraction of the operator's
+    // largest rank on the previous level -- nine tenths near the top, where a
+    // retry (a new sketch of large blocks) is costly, seven tenths deeper,
+    // where surplus columns cost more than a retry.  The applications are
+    // shared: the columns drawn are those of the operator that needs the
+    // most, and each operator compresses with the first q_o of them (the
+    // columns are i.i.d., so any prefix is itself a valid test matrix).
+    struct OpState {
+      int qo = 0;
+      bool done = true;
+      std::vector<int> rank;
+      QRBatch qb;
+      DBuf Yb, Sb, Sqr;
+      std::vector<int64_t> yoff, soff;
+    };
+    OpState st[2];
+    for (int oi : ops) {
+      int g = 8;
+      if (lev == 1) {
+        g = std::max(o.q0, 1);
+        if (F->levels.size() > 1)
+          for (int kk : F->levels[1].k) g = std::max(g, (9 * kk) / 10);
+      } else {
+        g = std::max(g, (lev <= 3 ? 9 : 7) * r_prev[oi] / 10);
+      }
+      st[oi].qo = g + c_over;
+      st[oi].done = false;
+      st[oi].rank.assign(nop, 0);
+      st[oi].yoff.assign(nop + 1, 0);
+      st[oi].soff.assign(nop + 1, 0);
     }
-    int q = q0 + c_over;
+    const int qcap = (int)std::min<int64_t>(n64, 1 << 15);
     std::vector<int> chunk_q, chunk_col0;
-    std::vector<DBuf> Wch, Ych;
-    std::vector<int> rank(nop, 0);
-    QRBatch qb;
-    DBuf Yb, WV, Sb, Sqr;
-    std::vector<int64_t> yoff(nop + 1, 0), woff(nbx + 1, 0), soff(nop + 1, 0);
+    std::vector<DBuf> Wch, Ych[2];
+    DBuf WV;
+    std::vector<int64_t> woff(nbx + 1, 0);
     int qtot = 0;
     while (true) {
-      int qc = q - qtot;
-      {
-        DBuf W, Y;
-        W.alloc(sizeof(double) * n64 * 4 * qc, s);
-        Y.alloc(sizeof(double) * n64 * 4 * qc, s);
+      int q = qtot;
+      for (int oi : ops)
+        if (!st[oi].done) q = std::max(q, st[oi].qo);
+      if (q > qtot) {
+        const int qc = q - qtot;
+        DBuf Wn, Y[2];
+        Wn.alloc(sizeof(double) * n64 * 4 * qc, s);
+        for (int oi : ops) Y[oi].alloc(sizeof(double) * n64 * 4 * qc, s);
         LAUNCH(gen_w_kernel, cdiv(n64 * 4 * qc, 256), 256, 0, s, dslot.as<int>(), n64, qc, qtot, lev,
-               (unsigned long long)o.seed, W.as<double>(), df);
+               (unsigned long long)o.seed, Wn.as<double>(), df);
         int tk = prof_begin(s);
-        applyG(W.as<double>(), Y.as<double>(), 4 * qc);
+        double* const outs[2] = {Y[0].as<double>(), Y[1].as<double>()};
+        applyG(Wn.as<double>(), outs, 4 * qc);
         prof_end(tk, s, PROF_PEEL_APPLY, 0, 0);
         tk = prof_begin(s);
-        for (int m = 1; m < lev; m++)
-          apply_level_sparse(levels[m], W.as<double>(), Y.as<double>(), qc, slotlist, sbeg, dslotlist.as<int>(), tmpP,
-                             s, df);
+        for (int oi : ops)
+          if (!st[oi].done)
+            for (int m = 1; m < lev; m++)
+              apply_level_sparse(levels[oi][m], Wn.as<double>(), Y[oi].as<double>(), qc, slotlist, sbeg,
+                                 dslotlist.as<int>(), tmpP, s, df);
         prof_end(tk, s, PROF_PEEL_SUB, 0, 0);
         chunk_q.push_back(qc);
         chunk_col0.push_back(qtot);
-        Wch.push_back(std::move(W));
-        Ych.push_back(std::move(Y));
-      }
-      qtot = q;
-      int tq = prof_begin(s);
-      // Y_ab (|I_a| x q) per ordered pair and [W_a V_a] (|I_a| x 2q) per box,
-      // column-major, in the arithmetic of the applications (df64 or fp64)
-      for (int i = 0; i < nop; i++) yoff[i + 1] = yoff[i] + (int64_t)PL.bx[op[i].a].cnt * q;
-      for (int a = 0; a < nbx; a++) woff[a + 1] = woff[a] + (int64_t)PL.bx[a].cnt * 3 * q;
-      for (int i = 0; i < nop; i++) soff[i + 1] = soff[i] + (int64_t)3 * q * q;
-      Yb.alloc(sizeof(double) * std::max<int64_t>(1, yoff[nop]), s);
-      WV.alloc(sizeof(double) * std::max<int64_t>(1, woff[nbx]), s);
-      for (size_t ch = 0; ch < Ych.size(); ch++) {
-        int qq = chunk_q[ch];
-        std::vector<ExtractProb> ey, ew;
-        std::vector<int64_t> py(1, 0), pw(1, 0);
-        for (int i = 0; i < nop; i++) {
-          const PBox& A = PL.bx[op[i].a];
-          const PBox& Bx = PL.bx[A.sib[op[i].t]];
-          ey.push_back({(int64_t)A.start, yoff[i], A.cnt, Bx.slot * qq});
-          py.push_back(py.back() + (int64_t)A.cnt * qq);
+        Wch.push_back(std::move(Wn));
+        for (int oi : ops) Ych[oi].push_back(std::move(Y[oi]));
+        qtot = q;
+        // [W_a V_a] (|I_a| x 3q) per box, column-major: the box's rows of its
+        // slot's test columns, then 2q sketch columns V_a independent of them
+        for (int a = 0; a < nbx; a++) woff[a + 1] = woff[a] + (int64_t)TL.bx[a].cnt * 3 * q;
+        WV.alloc(sizeof(double) * std::max<int64_t>(1, woff[nbx]), s);
+        for (size_t ch = 0; ch < Wch.size(); ch++) {
+          int qq = chunk_q[ch];
+          std::vector<ExtractProb> ew;
+          std::vector<int64_t> pw(1, 0);
+          for (int a = 0; a < nbx; a++) {
+            const PBox& A = TL.bx[a];
+            ew.push_back({(int64_t)A.start, woff[a], A.cnt, A.slot * qq});
+            pw.push_back(pw.back() + (int64_t)A.cnt * qq);
+          }
+          DBuf d3, d4;
+          upload_prefix(d3, d4, ew, pw, s);
+          LAUNCH(extract_kernel, cdiv(pw.back(), 256), 256, 0, s, d3.as<ExtractProb>(), d4.as<int64_t>(), nbx,
+                 pw.back(), qq, 4 * qq, chunk_col0[ch], Wch[ch].as<double>(), WV.as<double>(), 0);
         }
-        for (int a = 0; a < nbx; a++) {
-          const PBox& A = PL.bx[a];
-          ew.push_back({(int64_t)A.start, woff[a], A.cnt, A.slot * qq});
-          pw.push_back(pw.back() + (int64_t)A.cnt * qq);
-        }
-        DBuf d1, d2, d3, d4;
-        upload_prefix(d1, d2, ey, py, s);
-        LAUNCH(extract_kernel, cdiv(py.back(), 256), 256, 0, s, d1.as<ExtractProb>(), d2.as<int64_t>(), nop,
-               py.back(), qq, 4 * qq, chunk_col0[ch], Ych[ch].as<double>(), Yb.as<double>(), 0);
-        upload_prefix(d3, d4, ew, pw, s);
-        LAUNCH(extract_kernel, cdiv(pw.back(), 256), 256, 0, s, d3.as<ExtractProb>(), d4.as<int64_t>(), nbx,
-               pw.back(), qq, 4 * qq, chunk_col0[ch], Wch[ch].as<double>(), WV.as<double>(), 0);
-      }
-      {
         std::vector<VBox> vb(nbx);
         std::vector<int64_t> pv(nbx + 1, 0);
         for (int a = 0; a < nbx; a++) {
-          vb[a] = {(int64_t)PL.bx[a].start, woff[a] + (int64_t)PL.bx[a].cnt * q, PL.bx[a].cnt};
-          pv[a + 1] = pv[a] + (int64_t)PL.bx[a].cnt * 2 * q;
+          vb[a] = {(int64_t)TL.bx[a].start, woff[a] + (int64_t)TL.bx[a].cnt * q, TL.bx[a].cnt};
+          pv[a + 1] = pv[a] + (int64_t)TL.bx[a].cnt * 2 * q;
         }
         DBuf d1, d2;
         upload_prefix(d1, d2, vb, pv, s);
         LAUNCH(gen_v_kernel, cdiv(pv.back(), 256), 256, 0, s, d1.as<VBox>(), d2.as<int64_t>(), nbx, pv.back(), q,
                lev, (unsigned long long)o.seed, WV.as<double>(), df);
       }
-      // [W_a V_a]^T Y_ab (3q x q): rows 0..q-1 are Z_ab = W_a^T Y_ab (for the
-      // core of Eq. (lowrankapprox)), rows q..3q-1 the sketch S_ab = V_a^T Y_ab
-      // with V_a independent of the test matrices
-      Sb.alloc(sizeof(double) * std::max<int64_t>(1, soff[nop]), s);
-      {
-        std::vector<GemmDesc> g;
-        for (int i = 0; i < nop; i++) {
-          const PBox& A = PL.bx[op[i].a];
-          g.push_back(mk(3 * q, q, A.cnt, 0, woff[op[i].a], A.cnt, 1, 1, yoff[i], A.cnt, 0, 2, soff[i], 3 * q, 1.0,
-                         0.0));
+      int tq = prof_begin(s);
+      bool all_done = true;
+      for (int oi : ops) {
+        OpState& S = st[oi];
+        if (S.done) continue;
+        const int qo = S.qo;
+        // Y_ab (|I_a| x q_o) per ordered pair, column-major, in the arithmetic
+        // of the applications (df64 or fp64)
+        for (int i = 0; i < nop; i++) S.yoff[i + 1] = S.yoff[i] + (int64_t)TL.bx[op[i].a].cnt * qo;
+        for (int i = 0; i < nop; i++) S.soff[i + 1] = S.soff[i] + (int64_t)3 * qo * qo;
+        S.Yb.alloc(sizeof(double) * std::max<int64_t>(1, S.yoff[nop]), s);
+        for (size_t ch = 0; ch < Wch.size(); ch++) {
+          const int qq = chunk_q[ch];
+          const int take = std::min(qq, qo - chunk_col0[ch]);
+          if (take <= 0) continue;
+          std::vector<ExtractProb> ey;
+          std::vector<int64_t> py(1, 0);
+          for (int i = 0; i < nop; i++) {
+            const PBox& A = TL.bx[op[i].a];
+            const PBox& Bx = TL.bx[A.sib[op[i].t]];
+            ey.push_back({(int64_t)A.start, S.yoff[i], A.cnt, Bx.slot * qq});
+            py.push_back(py.back() + (int64_t)A.cnt * take);
+          }
+          DBuf d1, d2;
+          upload_prefix(d1, d2, ey, py, s);
+          LAUNCH(extract_kernel, cdiv(py.back(), 256), 256, 0, s, d1.as<ExtractProb>(), d2.as<int64_t>(), nop,
+                 py.back(), take, 4 * qq, chunk_col0[ch], Ych[oi][ch].as<double>(), S.Yb.as<double>(), 0);
         }
-        run_gemm(g, WV.as<double>(), Yb.as<double>(), Sb.as<double>(), nullptr, s, 1, 1, 1, 1, df);
-        if (df) convert_df64(Sb.as<double>(), soff[nop], 0, s);
+        // S_ab = [W_a(:, :q_o) V_a(:, :2 q_o)]^T Y_ab (3q_o x q_o): rows
+        // 0..q_o-1 are Z_ab = W_a^T Y_ab (for the core of Eq. (lowrankapprox)),
+        // rows q_o..3q_o-1 the sketch of Y_ab by V_a
+        S.Sb.alloc(sizeof(double) * std::max<int64_t>(1, S.soff[nop]), s);
+        {
+          std::vector<GemmDesc> g;
+          for (int i = 0; i < nop; i++) {
+            const PBox& A = TL.bx[op[i].a];
+            g.push_back(mk(qo, qo, A.cnt, 0, woff[op[i].a], A.cnt, 1, 1, S.yoff[i], A.cnt, 0, 2, S.soff[i], 3 * qo,
+                           1.0, 0.0));
+            g.push_back(mk(2 * qo, qo, A.cnt, 0, woff[op[i].a] + (int64_t)A.cnt * qtot, A.cnt, 1, 1, S.yoff[i],
+                           A.cnt, 0, 2, S.soff[i] + qo, 3 * qo, 1.0, 0.0));
+          }
+          run_gemm(g, WV.as<double>(), S.Yb.as<double>(), S.Sb.as<double>(), nullptr, s, 1, 1, 1, 1, df);
+          if (df) convert_df64(S.Sb.as<double>(), S.soff[nop], 0, s);
+        }
+        // rank-revealing pivoted QR of the sketches (fp64, 2q_o x q_o each)
+        S.Sqr.alloc(sizeof(double) * std::max<int64_t>(1, (int64_t)nop * 2 * qo * qo), s);
+        {
+          std::vector<CopyProb> cp(nop);
+          for (int i = 0; i < nop; i++)
+            cp[i] = {2 * qo, qo, 3 * qo, 2 * qo, S.soff[i] + qo, (int64_t)i * 2 * qo * qo, 0};
+          copy_batched(cp, S.Sb.as<double>(), S.Sqr.as<double>(), s);
+        }
+        std::vector<QRProb> qp(nop);
+        for (int i = 0; i < nop; i++) {
+          qp[i] = QRProb{};
+          qp[i].m = 2 * qo; qp[i].c = qo; qp[i].cpiv = qo; qp[i].maxk = qo;
+          qp[i].lda = 2 * qo; qp[i].a = (int64_t)i * 2 * qo * qo; qp[i].tol = tol;
+        }
+        S.qb = QRBatch();
+        S.qb.build(qp, s);
+        S.qb.run(S.Sqr.as<double>(), dst, lev, s);
+        std::vector<QRState> hst(nop);
+        d2h(hst.data(), S.qb.d_state(), nop, s);
+        sync(s);
+        int rm = 0;
+        for (int i = 0; i < nop; i++) {
+          S.rank[i] = hst[i].k;
+          rm = std::max(rm, S.rank[i]);
+        }
+        if (verbose())
+          fprintf(stderr, "[rsf] peel op %d level %d: q %d, max rank %d, pairs %d, boxes %d\n", oi, lev, qo, rm, nop,
+                  nbx);
+        if (rm <= qo - c_over || qo >= qcap) {
+          S.done = true;
+        } else {
+          // saturated: grow geometrically; otherwise just past the detected rank
+          if (rm >= qo - 1) S.qo = std::max(qo + c_over, (4 * qo) / 3);
+          else S.qo = rm + c_over + std::max(4, rm / 16);
+          S.qo = std::min(S.qo, qcap);
+          all_done = false;
+        }
       }
-      // rank-revealing pivoted QR of the sketches (fp64, 2q x q each)
-      Sqr.alloc(sizeof(double) * std::max<int64_t>(1, (int64_t)nop * 2 * q * q), s);
-      {
-        std::vector<CopyProb> cp(nop);
-        for (int i = 0; i < nop; i++) cp[i] = {2 * q, q, 3 * q, 2 * q, soff[i] + q, (int64_t)i * 2 * q * q, 0};
-        copy_batched(cp, Sb.as<double>(), Sqr.as<double>(), s);
-      }
-      std::vector<QRProb> qp(nop);
-      for (int i = 0; i < nop; i++) {
-        qp[i] = QRProb{};
-        qp[i].m = 2 * q; qp[i].c = q; qp[i].cpiv = q; qp[i].maxk = q;
-        qp[i].lda = 2 * q; qp[i].a = (int64_t)i * 2 * q * q; qp[i].tol = tol;
-      }
-      qb = QRBatch();
-      qb.build(qp, s);
-      qb.run(Sqr.as<double>(), dst, lev, s);
       prof_end(tq, s, PROF_PEEL_QR, 0, 0);
-      std::vector<QRState> hst(nop);
-      d2h(hst.data(), qb.d_state(), nop, s);
-      sync(s);
-      int rmax = 0;
-      for (int i = 0; i < nop; i++) {
-        rank[i] = hst[i].k;
-        rmax = std::max(rmax, rank[i]);
-      }
-      if (verbose())
-        fprintf(stderr, "[rsf] peel level %d: q %d, max rank %d, pairs %d, boxes %d\n", lev, q, rmax, nop, nbx);
-      if (rmax <= q - c_over || q >= (int)std::min<int64_t>(n64, 1 << 15)) break;
-      // saturated: grow geometrically; otherwise just past the detected rank
-      if (rmax >= q - 1) q = std::max(q + c_over, (4 * q) / 3);
-      else q = rmax + c_over + std::max(4, rmax / 16);
+      if (all_done) break;
     }
     Wch.clear();
-    Ych.clear();
+    for (int oi : ops) Ych[oi].clear();
     WV.release();
-    // a block whose row or column space is empty is dropped in both directions
-    for (const PPair& pp : PL.pr) {
-      int iab = opidx(pp.a, pp.sa), iba = opidx(pp.b, pp.sb);
-      if (rank[iab] == 0 || rank[iba] == 0) rank[iab] = rank[iba] = 0;
-    }
-    r_prev = 0;
-    for (int i = 0; i < nop; i++) r_prev = std::max(r_prev, rank[i]);
-    max_rank_seen = std::max(max_rank_seen, r_prev);
+    for (int oi : ops) {
+      OpState& S = st[oi];
+      PLevel& PL = levels[oi][lev];
+      PL.lev = lev;
+      PL.bx = TL.bx;
+      PL.pr = TL.pr;
+      PL.active = true;
+      const int q = S.qo;
+      std::vector<int>& rank = S.rank;
+      std::vector<int64_t>& yoff = S.yoff;
+      std::vector<int64_t>& soff = S.soff;
+      QRBatch& qb = S.qb;
+      DBuf& Yb = S.Yb;
+      DBuf& Sb = S.Sb;
+      DBuf& Sqr = S.Sqr;
+      int& rp = r_prev[oi];
+      // a block whose row or column space is empty is dropped in both directions
+      for (const PPair& pp : PL.pr) {
+        int iab = opidx(pp.a, pp.sa), iba = opidx(pp.b, pp.sb);
+        if (rank[iab] == 0 || rank[iba] == 0) rank[iab] = rank[iba] = 0;
+      }
+      rp = 0;
+      for (int i = 0; i < nop; i++) rp = std::max(rp, rank[i]);
 
-    int trest = prof_begin(s);
-    // ---- pool layout: U_ab blocks (Ucat_a per box), then the cores M_ab
-    int64_t pool = 0;
-    PL.sumRa = 0;
-    for (int i = 0; i < nop; i++) PL.bx[op[i].a].r[op[i].t] = rank[i];
-    for (int a = 0; a < nbx; a++) {
-      PBox& A = PL.bx[a];
-      A.Ra = 0;
-      for (int t = 0; t < A.nsib; t++) { A.ucol[t] = A.Ra; A.Ra += A.r[t]; }
-      A.ucat = pool;
-      pool += (int64_t)A.cnt * A.Ra;
-      A.pcol = PL.sumRa;
-      PL.sumRa += A.Ra;
-    }
-    const int64_t mstart = pool;
-    for (auto& pp : PL.pr) {
-      pp.m = pool;
-      pool += (int64_t)PL.bx[pp.a].r[pp.sa] * PL.bx[pp.b].r[pp.sb];
-    }
-    PL.pool.alloc(sizeof(double) * std::max<int64_t>(1, pool), s);
-    PL.pool.zero();
-    double* UP = PL.pool.as<double>();
-    // ---- R11^-1 of every sketch QR, U_ab = Y_ab(:, piv) R11^-1 and
-    //      B_ab = W_a^T U_ab = Z_ab(:, piv) R11^-1 with Z_ab = W_a^T Y_ab
-    std::vector<int64_t> roff(nop + 1, 0), poff(nop + 1, 0), zpoff(nop + 1, 0), boff(nop + 1, 0);
-    for (int i = 0; i < nop; i++) {
-      int rows = PL.bx[op[i].a].cnt;
-      roff[i + 1] = roff[i] + (int64_t)rank[i] * rank[i];
-      poff[i + 1] = poff[i] + (int64_t)rows * rank[i];
-      zpoff[i + 1] = zpoff[i] + (int64_t)q * rank[i];
-      boff[i + 1] = boff[i] + (int64_t)q * rank[i];
-    }
-    DBuf Rinv, Ypiv, Zpiv, Bm;
-    Rinv.alloc(sizeof(double) * std::max<int64_t>(1, roff[nop]), s);
-    {
-      std::vector<TrsmProb> tp(nop);
-      for (int i = 0; i < nop; i++) tp[i] = {rank[i], -1, roff[i]};
-      qr_trsm(qb, tp, nullptr, Sqr.as<double>(), Rinv.as<double>(), dst, lev, s);
-    }
-    Ypiv.alloc(sizeof(double) * std::max<int64_t>(1, poff[nop]), s);
-    Zpiv.alloc(sizeof(double) * std::max<int64_t>(1, zpoff[nop]), s);
-    Bm.alloc(sizeof(double) * std::max<int64_t>(1, boff[nop]), s);
-    {
-      std::vector<PivGather> pg(nop), pz(nop);
-      std::vector<int64_t> gp(nop + 1, 0), gz(nop + 1, 0);
+      int trest = prof_begin(s);
+      // ---- pool layout: U_ab blocks (Ucat_a per box), then the cores M_ab
+      int64_t pool = 0;
+      PL.sumRa = 0;
+      for (int i = 0; i < nop; i++) PL.bx[op[i].a].r[op[i].t] = rank[i];
+      for (int a = 0; a < nbx; a++) {
+        PBox& A = PL.bx[a];
+        A.Ra = 0;
+        for (int t = 0; t < A.nsib; t++) { A.ucol[t] = A.Ra; A.Ra += A.r[t]; }
+        A.ucat = pool;
+        pool += (int64_t)A.cnt * A.Ra;
+        A.pcol = PL.sumRa;
+        PL.sumRa += A.Ra;
+      }
+      const int64_t mstart = pool;
+      for (auto& pp : PL.pr) {
+        pp.m = pool;
+        pool += (int64_t)PL.bx[pp.a].r[pp.sa] * PL.bx[pp.b].r[pp.sb];
+      }
+      PL.pool.alloc(sizeof(double) * std::max<int64_t>(1, pool), s);
+      PL.pool.zero();
+      double* UP = PL.pool.as<double>();
+      // ---- R11^-1 of every sketch QR, U_ab = Y_ab(:, piv) R11^-1 and
+      //      B_ab = W_a^T U_ab = Z_ab(:, piv) R11^-1 with Z_ab = W_a^T Y_ab
+      std::vector<int64_t> roff(nop + 1, 0), poff(nop + 1, 0), zpoff(nop + 1, 0), boff(nop + 1, 0);
       for (int i = 0; i < nop; i++) {
         int rows = PL.bx[op[i].a].cnt;
-        pg[i] = {yoff[i], poff[i], qb.colprefix_h[i], rows, rows};
-        pz[i] = {soff[i], zpoff[i], qb.colprefix_h[i], q, 3 * q};
-        gp[i + 1] = gp[i] + (int64_t)rows * rank[i];
-        gz[i + 1] = gz[i] + (int64_t)q * rank[i];
+        roff[i + 1] = roff[i] + (int64_t)rank[i] * rank[i];
+        poff[i + 1] = poff[i] + (int64_t)rows * rank[i];
+        zpoff[i + 1] = zpoff[i] + (int64_t)q * rank[i];
+        boff[i + 1] = boff[i] + (int64_t)q * rank[i];
       }
-      if (gp[nop] > 0) {
-        DBuf d1, d2, d3, d4;
-        upload_prefix(d1, d2, pg, gp, s);
-        LAUNCH(pivgather_kernel, cdiv(gp[nop], 256), 256, 0, s, d1.as<PivGather>(), d2.as<int64_t>(), nop,
-               gp[nop], qb.d_piv(), qb.d_state(), Yb.as<double>(), Ypiv.as<double>());
-        upload_prefix(d3, d4, pz, gz, s);
-        LAUNCH(pivgather_kernel, cdiv(gz[nop], 256), 256, 0, s, d3.as<PivGather>(), d4.as<int64_t>(), nop,
-               gz[nop], qb.d_piv(), qb.d_state(), Sb.as<double>(), Zpiv.as<double>());
+      DBuf Rinv, Ypiv, Zpiv, Bm;
+      Rinv.alloc(sizeof(double) * std::max<int64_t>(1, roff[nop]), s);
+      {
+        std::vector<TrsmProb> tp(nop);
+        for (int i = 0; i < nop; i++) tp[i] = {rank[i], -1, roff[i]};
+        qr_trsm(qb, tp, nullptr, Sqr.as<double>(), Rinv.as<double>(), dst, lev, s);
       }
-      std::vector<GemmDesc> gu, gb;
-      for (int i = 0; i < nop; i++) {
-        const PBox& A = PL.bx[op[i].a];
-        int r = rank[i];
-        if (r == 0) continue;
-        // U = Ypiv (rows x r) * Rinv (r x r, upper) into Ucat_a
-        gu.push_back(mk(A.cnt, r, r, 0, poff[i], A.cnt, 0, 1, roff[i], r, 0, 2,
-                        A.ucat + (int64_t)A.ucol[op[i].t] * A.cnt, A.cnt, 1.0, 0.0, 2));
-        // B = Zpiv (q x r) * Rinv
-        gb.push_back(mk(q, r, r, 0, zpoff[i], q, 0, 1, roff[i], r, 0, 2, boff[i], q, 1.0, 0.0, 2));
-      }
-      run_gemm(gb, Zpiv.as<double>(), Rinv.as<double>(), Bm.as<double>(), nullptr, s);
-      if (df) convert_df64(Rinv.as<double>(), roff[nop], 1, s);
-      run_gemm(gu, Ypiv.as<double>(), Rinv.as<double>(), UP, nullptr, s, 1, 1, 1, 1, df);
-    }
-    Ypiv.release();
-    Yb.release();
-    // ---- cores M_ab (Eq. (lowrankapprox))
-    {
-      const int npr = (int)PL.pr.size();
-      // X1 = (B_ab)^+ core  via QR of [B_ab | core]  (q x (r_ab + q))
-      std::vector<QRProb> q1;
-      std::vector<CopyProb> cp1;
-      std::vector<CoreProb> cores;
-      std::vector<int> live;
-      int64_t qpool = 0;
-      for (int p = 0; p < npr; p++) {
-        const PPair& pp = PL.pr[p];
-        int iab = opidx(pp.a, pp.sa), iba = opidx(pp.b, pp.sb);
-        int rab = rank[iab], rba = rank[iba];
-        if (rab == 0 || rba == 0) continue;
-        live.push_back(p);
-        QRProb x{};
-        x.m = q; x.c = rab + q; x.cpiv = rab; x.maxk = rab; x.lda = q; x.a = qpool; x.tol = 0.0;
-        cp1.push_back({q, rab, q, q, boff[iab], qpool, 0});
-        cores.push_back({soff[iab], soff[iba], qpool + (int64_t)q * rab, q, 3 * q});
-        qpool += (int64_t)q * (rab + q);
-        q1.push_back(x);
-      }
-      if (!live.empty()) {
-        DBuf W1;
-        W1.alloc(sizeof(double) * qpool, s);
-        copy_batched(cp1, Bm.as<double>(), W1.as<double>(), s);
-        {
-          DBuf dc;
-          upload(dc, cores, s);
-          dim3 grid(cdiv((int64_t)q * q, 256), (unsigned)cores.size());
-          LAUNCH(core_kernel, grid, 256, 0, s, dc.as<CoreProb>(), (int)cores.size(), Sb.as<double>(), W1.as<double>());
+      Ypiv.alloc(sizeof(double) * std::max<int64_t>(1, poff[nop]), s);
+      Zpiv.alloc(sizeof(double) * std::max<int64_t>(1, zpoff[nop]), s);
+      Bm.alloc(sizeof(double) * std::max<int64_t>(1, boff[nop]), s);
+      {
+        std::vector<PivGather> pg(nop), pz(nop);
+        std::vector<int64_t> gp(nop + 1, 0), gz(nop + 1, 0);
+        for (int i = 0; i < nop; i++) {
+          int rows = PL.bx[op[i].a].cnt;
+          pg[i] = {yoff[i], poff[i], qb.colprefix_h[i], rows, rows};
+          pz[i] = {soff[i], zpoff[i], qb.colprefix_h[i], q, 3 * q};
+          gp[i + 1] = gp[i] + (int64_t)rows * rank[i];
+          gz[i + 1] = gz[i] + (int64_t)q * rank[i];
         }
-        QRBatch qx;
-        qx.build(q1, s);
-        qx.run(W1.as<double>(), dst, lev, s);
-        std::vector<int> rhs;
-        std::vector<TrsmProb> tp(live.size());
-        std::vector<int64_t> toff(live.size() + 1, 0);
-        std::vector<PermScatter> ps(live.size());
-        std::vector<int64_t> xoff(live.size() + 1, 0), spre(live.size() + 1, 0);
-        for (size_t j = 0; j < live.size(); j++) {
-          const PPair& pp = PL.pr[live[j]];
-          int rab = rank[opidx(pp.a, pp.sa)];
-          tp[j].nrhs = q;
-          tp[j].rhs0 = (int64_t)rhs.size();
-          tp[j].out0 = toff[j];
-          for (int t = 0; t < q; t++) rhs.push_back(rab + t);
-          toff[j + 1] = toff[j] + (int64_t)rab * q;
-          // X1 (r_ab x q, ld r_ab): X1[piv[i], s] = t[i, s]
-          ps[j] = {toff[j], xoff[j], qx.colprefix_h[j], rab, q, 1, rab};
-          xoff[j + 1] = xoff[j] + (int64_t)rab * q;
-          spre[j + 1] = spre[j] + (int64_t)rab * q;
+        if (gp[nop] > 0) {
+          DBuf d1, d2, d3, d4;
+          upload_prefix(d1, d2, pg, gp, s);
+          LAUNCH(pivgather_kernel, cdiv(gp[nop], 256), 256, 0, s, d1.as<PivGather>(), d2.as<int64_t>(), nop,
+                 gp[nop], qb.d_piv(), qb.d_state(), Yb.as<double>(), Ypiv.as<double>());
+          upload_prefix(d3, d4, pz, gz, s);
+          LAUNCH(pivgather_kernel, cdiv(gz[nop], 256), 256, 0, s, d3.as<PivGather>(), d4.as<int64_t>(), nop,
+                 gz[nop], qb.d_piv(), qb.d_state(), Sb.as<double>(), Zpiv.as<double>());
         }
-        DBuf drhs, tout, X1;
-        upload(drhs, rhs, s);
-        tout.alloc(sizeof(double) * std::max<int64_t>(1, toff.back()), s);
-        X1.alloc(sizeof(double) * std::max<int64_t>(1, xoff.back()), s);
-        X1.zero();
-        qr_trsm(qx, tp, drhs.as<int>(), W1.as<double>(), tout.as<double>(), dst, lev, s);
-        {
-          DBuf d1, d2;
-          upload_prefix(d1, d2, ps, spre, s);
-          LAUNCH(permscatter_kernel, cdiv(spre.back(), 256), 256, 0, s, d1.as<PermScatter>(), d2.as<int64_t>(),
-                 (int)ps.size(), spre.back(), qx.d_piv(), qx.d_state(), tout.as<double>(), X1.as<double>());
+        std::vector<GemmDesc> gu, gb;
+        for (int i = 0; i < nop; i++) {
+          const PBox& A = PL.bx[op[i].a];
+          int r = rank[i];
+          if (r == 0) continue;
+          // U = Ypiv (rows x r) * Rinv (r x r, upper) into Ucat_a
+          gu.push_back(mk(A.cnt, r, r, 0, poff[i], A.cnt, 0, 1, roff[i], r, 0, 2,
+                          A.ucat + (int64_t)A.ucol[op[i].t] * A.cnt, A.cnt, 1.0, 0.0, 2));
+          // B = Zpiv (q x r) * Rinv
+          gb.push_back(mk(q, r, r, 0, zpoff[i], q, 0, 1, roff[i], r, 0, 2, boff[i], q, 1.0, 0.0, 2));
         }
-        // M_ab^T = (B_ba)^+ X1^T via QR of [B_ba | X1^T]  (q x (r_ba + r_ab))
-        std::vector<QRProb> q2;
-        std::vector<CopyProb> cp2, cpx;
-        int64_t qpool2 = 0;
-        for (size_t j = 0; j < live.size(); j++) {
-          const PPair& pp = PL.pr[live[j]];
+        run_gemm(gb, Zpiv.as<double>(), Rinv.as<double>(), Bm.as<double>(), nullptr, s);
+        if (df) convert_df64(Rinv.as<double>(), roff[nop], 1, s);
+        run_gemm(gu, Ypiv.as<double>(), Rinv.as<double>(), UP, nullptr, s, 1, 1, 1, 1, df);
+      }
+      Ypiv.release();
+      Yb.release();
+      // ---- cores M_ab (Eq. (lowrankapprox))
+      {
+        const int npr = (int)PL.pr.size();
+        // X1 = (B_ab)^+ core  via QR of [B_ab | core]  (q x (r_ab + q))
+        std::vector<QRProb> q1;
+        std::vector<CopyProb> cp1;
+        std::vector<CoreProb> cores;
+        std::vector<int> live;
+        int64_t qpool = 0;
+        for (int p = 0; p < npr; p++) {
+          const PPair& pp = PL.pr[p];
           int iab = opidx(pp.a, pp.sa), iba = opidx(pp.b, pp.sb);
           int rab = rank[iab], rba = rank[iba];
+          if (rab == 0 || rba == 0) continue;
+          live.push_back(p);
           QRProb x{};
-          x.m = q; x.c = rba + rab; x.cpiv = rba; x.maxk = rba; x.lda = q; x.a = qpool2; x.tol = 0.0;
-          cp2.push_back({q, rba, q, q, boff[iba], qpool2, 0});
-          cpx.push_back({q, rab, rab, q, xoff[j], qpool2 + (int64_t)q * rba, 1});
-          qpool2 += (int64_t)q * (rba + rab);
-          q2.push_back(x);
+          x.m = q; x.c = rab + q; x.cpiv = rab; x.maxk = rab; x.lda = q; x.a = qpool; x.tol = 0.0;
+          cp1.push_back({q, rab, q, q, boff[iab], qpool, 0});
+          cores.push_back({soff[iab], soff[iba], qpool + (int64_t)q * rab, q, 3 * q});
+          qpool += (int64_t)q * (rab + q);
+          q1.push_back(x);
         }
-        DBuf W2;
-        W2.alloc(sizeof(double) * qpool2, s);
-        copy_batched(cp2, Bm.as<double>(), W2.as<double>(), s);
-        copy_batched(cpx, X1.as<double>(), W2.as<double>(), s);
-        QRBatch qy;
-        qy.build(q2, s);
-        qy.run(W2.as<double>(), dst, lev, s);
-        std::vector<int> rhs2;
-        std::vector<TrsmProb> tp2(live.size());
-        std::vector<int64_t> toff2(live.size() + 1, 0), spre2(live.size() + 1, 0);
-        std::vector<PermScatter> ps2(live.size());
-        for (size_t j = 0; j < live.size(); j++) {
-          const PPair& pp = PL.pr[live[j]];
-          int rab = rank[opidx(pp.a, pp.sa)], rba = rank[opidx(pp.b, pp.sb)];
-          tp2[j].nrhs = rab;
-          tp2[j].rhs0 = (int64_t)rhs2.size();
-          tp2[j].out0 = toff2[j];
-          for (int t = 0; t < rab; t++) rhs2.push_back(rba + t);
-          toff2[j + 1] = toff2[j] + (int64_t)rba * rab;
-          // M^T[piv[i], s] = t[i, s]  ->  M (r_ab x r_ba, ld r_ab): M[s, piv[i]]
-          ps2[j] = {toff2[j], pp.m, qy.colprefix_h[j], rba, rab, rab, 1};
-          spre2[j + 1] = spre2[j] + (int64_t)rba * rab;
-        }
-        DBuf drhs2, tout2;
-        upload(drhs2, rhs2, s);
-        tout2.alloc(sizeof(double) * std::max<int64_t>(1, toff2.back()), s);
-        qr_trsm(qy, tp2, drhs2.as<int>(), W2.as<double>(), tout2.as<double>(), dst, lev, s);
-        {
-          DBuf d1, d2;
-          upload_prefix(d1, d2, ps2, spre2, s);
-          LAUNCH(permscatter_kernel, cdiv(spre2.back(), 256), 256, 0, s, d1.as<PermScatter>(), d2.as<int64_t>(),
-                 (int)ps2.size(), spre2.back(), qy.d_piv(), qy.d_state(), tout2.as<double>(), UP);
+        if (!live.empty()) {
+          DBuf W1;
+          W1.alloc(sizeof(double) * qpool, s);
+          copy_batched(cp1, Bm.as<double>(), W1.as<double>(), s);
+          {
+            DBuf dc;
+            upload(dc, cores, s);
+            dim3 grid(cdiv((int64_t)q * q, 256), (unsigned)cores.size());
+            LAUNCH(core_kernel, grid, 256, 0, s, dc.as<CoreProb>(), (int)cores.size(), Sb.as<double>(), W1.as<double>());
+          }
+          QRBatch qx;
+          qx.build(q1, s);
+          qx.run(W1.as<double>(), dst, lev, s);
+          std::vector<int> rhs;
+          std::vector<TrsmProb> tp(live.size());
+          std::vector<int64_t> toff(live.size() + 1, 0);
+          std::vector<PermScatter> ps(live.size());
+          std::vector<int64_t> xoff(live.size() + 1, 0), spre(live.size() + 1, 0);
+          for (size_t j = 0; j < live.size(); j++) {
+            const PPair& pp = PL.pr[live[j]];
+            int rab = rank[opidx(pp.a, pp.sa)];
+            tp[j].nrhs = q;
+            tp[j].rhs0 = (int64_t)rhs.size();
+            tp[j].out0 = toff[j];
+            for (int t = 0; t < q; t++) rhs.push_back(rab + t);
+            toff[j + 1] = toff[j] + (int64_t)rab * q;
+            // X1 (r_ab x q, ld r_ab): X1[piv[i], s] = t[i, s]
+            ps[j] = {toff[j], xoff[j], qx.colprefix_h[j], rab, q, 1, rab};
+            xoff[j + 1] = xoff[j] + (int64_t)rab * q;
+            spre[j + 1] = spre[j] + (int64_t)rab * q;
+          }
+          DBuf drhs, tout, X1;
+          upload(drhs, rhs, s);
+          tout.alloc(sizeof(double) * std::max<int64_t>(1, toff.back()), s);
+          X1.alloc(sizeof(double) * std::max<int64_t>(1, xoff.back()), s);
+          X1.zero();
+          qr_trsm(qx, tp, drhs.as<int>(), W1.as<double>(), tout.as<double>(), dst, lev, s);
+          {
+            DBuf d1, d2;
+            upload_prefix(d1, d2, ps, spre, s);
+            LAUNCH(permscatter_kernel, cdiv(spre.back(), 256), 256, 0, s, d1.as<PermScatter>(), d2.as<int64_t>(),
+                   (int)ps.size(), spre.back(), qx.d_piv(), qx.d_state(), tout.as<double>(), X1.as<double>());
+          }
+          // M_ab^T = (B_ba)^+ X1^T via QR of [B_ba | X1^T]  (q x (r_ba + r_ab))
+          std::vector<QRProb> q2;
+          std::vector<CopyProb> cp2, cpx;
+          int64_t qpool2 = 0;
+          for (size_t j = 0; j < live.size(); j++) {
+            const PPair& pp = PL.pr[live[j]];
+            int iab = opidx(pp.a, pp.sa), iba = opidx(pp.b, pp.sb);
+            int rab = rank[iab], rba = rank[iba];
+            QRProb x{};
+            x.m = q; x.c = rba + rab; x.cpiv = rba; x.maxk = rba; x.lda = q; x.a = qpool2; x.tol = 0.0;
+            cp2.push_back({q, rba, q, q, boff[iba], qpool2, 0});
+            cpx.push_back({q, rab, rab, q, xoff[j], qpool2 + (int64_t)q * rba, 1});
+            qpool2 += (int64_t)q * (rba + rab);
+            q2.push_back(x);
+          }
+          DBuf W2;
+          W2.alloc(sizeof(double) * qpool2, s);
+          copy_batched(cp2, Bm.as<double>(), W2.as<double>(), s);
+          copy_batched(cpx, X1.as<double>(), W2.as<double>(), s);
+          QRBatch qy;
+          qy.build(q2, s);
+          qy.run(W2.as<double>(), dst, lev, s);
+          std::vector<int> rhs2;
+          std::vector<TrsmProb> tp2(live.size());
+          std::vector<int64_t> toff2(live.size() + 1, 0), spre2(live.size() + 1, 0);
+          std::vector<PermScatter> ps2(live.size());
+          for (size_t j = 0; j < live.size(); j++) {
+            const PPair& pp = PL.pr[live[j]];
+            int rab = rank[opidx(pp.a, pp.sa)], rba = rank[opidx(pp.b, pp.sb)];
+            tp2[j].nrhs = rab;
+            tp2[j].rhs0 = (int64_t)rhs2.size();
+            tp2[j].out0 = toff2[j];
+            for (int t = 0; t < rab; t++) rhs2.push_back(rba + t);
+            toff2[j + 1] = toff2[j] + (int64_t)rba * rab;
+            // M^T[piv[i], s] = t[i, s]  ->  M (r_ab x r_ba, ld r_ab): M[s, piv[i]]
+            ps2[j] = {toff2[j], pp.m, qy.colprefix_h[j], rba, rab, rab, 1};
+            spre2[j + 1] = spre2[j] + (int64_t)rba * rab;
+          }
+          DBuf drhs2, tout2;
+          upload(drhs2, rhs2, s);
+          tout2.alloc(sizeof(double) * std::max<int64_t>(1, toff2.back()), s);
+          qr_trsm(qy, tp2, drhs2.as<int>(), W2.as<double>(), tout2.as<double>(), dst, lev, s);
+          {
+            DBuf d1, d2;
+            upload_prefix(d1, d2, ps2, spre2, s);
+            LAUNCH(permscatter_kernel, cdiv(spre2.back(), 256), 256, 0, s, d1.as<PermScatter>(), d2.as<int64_t>(),
+                   (int)ps2.size(), spre2.back(), qy.d_piv(), qy.d_state(), tout2.as<double>(), UP);
+          }
         }
       }
+      if (df) convert_df64(UP + mstart, pool - mstart, 1, s);
+      // ---- application descriptors of G^(lev) (bases 0 X, 1 Y, 2 pool, 3 temp)
+      {
+        std::vector<GemmDesc> gP, gQ, gY;
+        for (int a = 0; a < nbx; a++) {
+          const PBox& A = PL.bx[a];
+          if (A.Ra == 0) continue;
+          // P_a^T (nc x Ra) = X(I_a)^T Ucat_a
+          gP.push_back(mk(-1, A.Ra, A.cnt, 0, A.start, -1, 0, 2, A.ucat, A.cnt, 0, 3, A.pcol, -1, 1.0, 0.0));
+          // Y(I_a)^T -= Q_a^T Ucat_a^T, Q stored after all P blocks
+          gY.push_back(mk(-1, A.cnt, A.Ra, 3, PL.sumRa + A.pcol, -1, 0, 2, A.ucat, A.cnt, 1, 1, A.start, -1, -1.0,
+                          1.0));
+        }
+        for (const PPair& pp : PL.pr) {
+          const PBox& A = PL.bx[pp.a];
+          const PBox& Bx = PL.bx[pp.b];
+          int rab = A.r[pp.sa], rba = Bx.r[pp.sb];
+          if (rab == 0 || rba == 0) continue;
+          // Q_ab^T (nc x r_ab) = P_(b->a)^T (nc x r_ba) M_ab^T
+          gQ.push_back(mk(-1, rab, rba, 3, Bx.pcol + Bx.ucol[pp.sb], -1, 0, 2, pp.m, rab, 1, 3,
+                          PL.sumRa + A.pcol + A.ucol[pp.sa], -1, 1.0, 0.0));
+          // Q_ba^T (nc x r_ba) = P_(a->b)^T (nc x r_ab) M_ab
+          gQ.push_back(mk(-1, rba, rab, 3, A.pcol + A.ucol[pp.sa], -1, 0, 2, pp.m, rab, 0, 3,
+                          PL.sumRa + Bx.pcol + Bx.ucol[pp.sb], -1, 1.0, 0.0));
+        }
+        PL.gP.build(gP, s);
+        PL.gQ.build(gQ, s);
+        PL.gY.build(gY, s);
+      }
+      prof_end(trest, s, PROF_PEEL_REST, 0, 0);
+      Sqr.release();
+      Sb.release();
     }
-    if (df) convert_df64(UP + mstart, pool - mstart, 1, s);
-    // ---- application descriptors of G^(lev) (bases 0 X, 1 Y, 2 pool, 3 temp)
-    {
-      std::vector<GemmDesc> gP, gQ, gY;
-      for (int a = 0; a < nbx; a++) {
-        const PBox& A = PL.bx[a];
-        if (A.Ra == 0) continue;
-        // P_a^T (nc x Ra) = X(I_a)^T Ucat_a
-        gP.push_back(mk(-1, A.Ra, A.cnt, 0, A.start, -1, 0, 2, A.ucat, A.cnt, 0, 3, A.pcol, -1, 1.0, 0.0));
-        // Y(I_a)^T -= Q_a^T Ucat_a^T, Q stored after all P blocks
-        gY.push_back(mk(-1, A.cnt, A.Ra, 3, PL.sumRa + A.pcol, -1, 0, 2, A.ucat, A.cnt, 1, 1, A.start, -1, -1.0,
-                        1.0));
-      }
-      for (const PPair& pp : PL.pr) {
-        const PBox& A = PL.bx[pp.a];
-        const PBox& Bx = PL.bx[pp.b];
-        int rab = A.r[pp.sa], rba = Bx.r[pp.sb];
-        if (rab == 0 || rba == 0) continue;
-        // Q_ab^T (nc x r_ab) = P_(b->a)^T (nc x r_ba) M_ab^T
-        gQ.push_back(mk(-1, rab, rba, 3, Bx.pcol + Bx.ucol[pp.sb], -1, 0, 2, pp.m, rab, 1, 3,
-                        PL.sumRa + A.pcol + A.ucol[pp.sa], -1, 1.0, 0.0));
-        // Q_ba^T (nc x r_ba) = P_(a->b)^T (nc x r_ab) M_ab
-        gQ.push_back(mk(-1, rba, rab, 3, A.pcol + A.ucol[pp.sa], -1, 0, 2, pp.m, rab, 0, 3,
-                        PL.sumRa + Bx.pcol + Bx.ucol[pp.sb], -1, 1.0, 0.0));
-      }
-      PL.gP.build(gP, s);
-      PL.gQ.build(gQ, s);
-      PL.gY.build(gY, s);
-    }
-    prof_end(trest, s, PROF_PEEL_REST, 0, 0);
     sync(s);
   }
 
@@ -842,28 +957,29 @@ double peel_trace(rsf_handle_s* F, rsf_handle_s* Fk, double tol, const rsf_opts&
   const int nl = std::max(1, T.max_leaf);
   DBuf dlp;
   upload(dlp, T.leafpos, s);
-  DBuf E, H;
+  DBuf E, H[2];
   E.alloc(sizeof(double) * n64 * nl, s);
-  H.alloc(sizeof(double) * n64 * nl, s);
+  for (int oi : ops) H[oi].alloc(sizeof(double) * n64 * nl, s);
   LAUNCH(unit_cols_kernel, cdiv(n64 * nl, 256), 256, 0, s, dlp.as<int>(), n64, nl, E.as<double>(), df);
   int tk = prof_begin(s);
-  applyG(E.as<double>(), H.as<double>(), nl);
+  double* const hout[2] = {H[0].as<double>(), H[1].as<double>()};
+  applyG(E.as<double>(), hout, nl);
   prof_end(tk, s, PROF_PEEL_APPLY, 0, 0);
   tk = prof_begin(s);
-  for (int m = 1; m <= L; m++) apply_level(levels[m], E.as<double>(), H.as<double>(), nl, tmpP, s, df);
+  for (int oi : ops)
+    for (int m = 1; m <= L; m++) apply_level(levels[oi][m], E.as<double>(), H[oi].as<double>(), nl, tmpP, s, df);
   prof_end(tk, s, PROF_PEEL_SUB, 0, 0);
   int nb = (int)std::min<int64_t>(1024, std::max<int64_t>(1, cdiv(n64, 256)));
   DBuf part, res;
   part.alloc(sizeof(double) * nb, s);
-  res.alloc(sizeof(double), s);
-  LAUNCH(diag_trace_kernel, nb, 256, 0, s, H.as<double>(), dlp.as<int>(), n64, nl, part.as<double>(), df);
-  double* outp = d_out ? d_out : res.as<double>();
-  LAUNCH(sum_parts_kernel, 1, 256, 0, s, part.as<double>(), nb, outp);
-  double tr = 0;
-  d2h(&tr, outp, 1, s);
-  sync(s);
-  (void)max_rank_seen;
-  return tr;
+  res.alloc(sizeof(double) * 2, s);
+  for (int oi : ops) {
+    LAUNCH(diag_trace_kernel, nb, 256, 0, s, H[oi].as<double>(), dlp.as<int>(), n64, nl, part.as<double>(), df);
+    double* outp = d_out[oi] ? d_out[oi] : res.as<double>() + oi;
+    LAUNCH(sum_parts_kernel, 1, 256, 0, s, part.as<double>(), nb, outp);
+    d2h(&h_out[oi], outp, 1, s);
+    sync(s);
+  }
 }
 
 }  // namespace rsf
