@@ -286,7 +286,8 @@ def run_gpu(args):
                                  "lower-triangle outputs counted exactly), fp64-equivalent",
                 "launches": g["launches"], "kernel_ms_per_step": g["ms"] / args.steps,
                 "share_of_step": g["ms"] / ms if ms > 0 else None,
-                "phases_ms_per_step": {B.PROF_NAMES[c]: prof[c]["ms"] / args.steps for c in prof}}
+                "phases_ms_per_step": {B.PROF_NAMES[c]: prof[c]["ms"] / args.steps for c in prof
+                                       if prof[c]["launches"] > 0}}
     cpu = None
     if not args.no_cpu:
         xs, zs = cpu_sample(wl)

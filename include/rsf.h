@@ -95,7 +95,17 @@ typedef struct {
                        log-determinant stay fp64, the multi-RHS solves and the
                        peeling products run in double-float (fp32-pair)
                        arithmetic with ~48-bit significands */
+  int trace_form;   /* symmetric operator peeled for Tr(F^-1 F_k) (Sec. 3,
+                       which allows any symmetrized form with the same
+                       trace).  RSF_TRACE_SYM (0, default): the paper's
+                       G = (F^-1 F_k + F_k F^-1) / 2 of Eq. (Gbb), and F^-1
+                       itself for Tr(F^-1).  RSF_TRACE_SQRT (1):
+                       G = F^-1/2 F_k F^-T/2 and, for Tr(F^-1),
+                       F^-1/2 F^-T/2, with F = F^1/2 (F^1/2)^T of Sec. 2.3.2:
+                       half the solve passes per test column */
 } rsf_opts;
+
+enum { RSF_TRACE_SYM = 0, RSF_TRACE_SQRT = 1 };
 
 enum { RSF_PREC_FP64 = 0, RSF_PREC_MIXED = 1 };
 
@@ -206,11 +216,15 @@ rsf_status rsf_get_info(rsf_handle h, rsf_info_t* info);
 int64_t rsf_launch_count(int reset);
 
 /* Kernel timing for reporting: while enabled, the library records CUDA events
- * on the launching stream around its batched GEMM (category 0), pivoted-QR
- * update (1) and pivot (2) launches, with each launch's algorithmic fp64
- * flops and bytes.  rsf_profile_read returns the totals of a category since
- * the last reset (launches, summed event time in ms, flops, bytes; any output
- * may be NULL) and synchronises the recorded events. */
+ * on the launching stream around its batched GEMM launches (category 0 in
+ * fp64, 8 in df64 arithmetic), its pivoted-QR launches (1; category 2 is no
+ * longer used: the pivot steps run inside the same persistent launch) and
+ * around the phases 3-7 (peeling applications, subtraction of coarser levels,
+ * sketch and rank detection, compression of the blocks, factorizations), with
+ * each GEMM launch's algorithmic fp64-equivalent flops.  rsf_profile_read
+ * returns the totals of a category since the last reset (launches, summed
+ * event time in ms, flops, bytes; any output may be NULL) and synchronises
+ * the recorded events. */
 void rsf_profile_enable(int on);
 rsf_status rsf_profile_read(int category, int reset, int64_t* launches, double* ms,
                             double* flops, double* bytes);

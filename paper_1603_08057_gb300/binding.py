@@ -37,10 +37,11 @@ class RsfOpts(C.Structure):
     _fields_ = [("n_occ", C.c_int), ("n_prox", C.c_int), ("n_rings", C.c_int),
                 ("r_near", C.c_double), ("r_in", C.c_double), ("r_out", C.c_double),
                 ("oversample", C.c_int), ("q0", C.c_int), ("seed", C.c_uint64),
-                ("precision", C.c_int)]
+                ("precision", C.c_int), ("trace_form", C.c_int)]
 
 
 PREC_FP64, PREC_MIXED = 0, 1
+TRACE_SYM, TRACE_SQRT = 0, 1
 
 
 class RsfInfo(C.Structure):
@@ -138,7 +139,7 @@ def launch_count(reset=False) -> int:
 
 PROF_GEMM, PROF_QR_UPDATE, PROF_QR_PIVOT = 0, 1, 2
 PROF_PEEL_APPLY, PROF_PEEL_SUB, PROF_PEEL_QR, PROF_PEEL_REST, PROF_FACTOR, PROF_GEMM_DF = 3, 4, 5, 6, 7, 8
-PROF_NAMES = ["gemm_fp64", "qr_update", "qr_pivot", "peel_apply", "peel_sub", "peel_qr", "peel_rest",
+PROF_NAMES = ["gemm_fp64", "qr", "qr_pivot", "peel_apply", "peel_sub", "peel_qr", "peel_rest",
               "factor", "gemm_df64"]
 
 

@@ -181,6 +181,8 @@ static rsf_opts resolve_opts(const rsf_opts* o) {
   rsf_opts r;
   rsf_opts_default(&r);
   if (o) r = *o;
+  RSF_CHECK(r.trace_form == RSF_TRACE_SYM || r.trace_form == RSF_TRACE_SQRT, RSF_EINVAL,
+            "trace_form must be RSF_TRACE_SYM or RSF_TRACE_SQRT");
   return r;
 }
 
@@ -259,6 +261,7 @@ void rsf_opts_default(rsf_opts* o) {
   o->q0 = 64;
   o->seed = 0;
   o->precision = RSF_PREC_MIXED;
+  o->trace_form = RSF_TRACE_SYM;
 }
 
 const char* rsf_last_error(void) { return g_err.c_str(); }

@@ -50,7 +50,7 @@ extern int64_t g_launches;
 // Optional per-category kernel timing: CUDA events recorded on the launching
 // stream around instrumented launches, with the launch's algorithmic flops.
 enum ProfCat {
-  PROF_GEMM = 0, PROF_QR_UPDATE = 1, PROF_QR_PIVOT = 2,
+  PROF_GEMM = 0, PROF_QR_UPDATE = 1 /* the whole persistent pivoted QR */, PROF_QR_PIVOT = 2 /* unused */,
   // phases (spans of many launches)
   PROF_PEEL_APPLY = 3, PROF_PEEL_SUB = 4, PROF_PEEL_QR = 5, PROF_PEEL_REST = 6, PROF_FACTOR = 7,
   PROF_GEMM_DF = 8,  // the GEMM kernel in df64 arithmetic (PROF_GEMM: fp64)

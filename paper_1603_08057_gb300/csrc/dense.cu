@@ -242,6 +242,9 @@ void GemmBatch::run(const GemmBases& b, cudaStream_t s) const {
 }
 
 // ============================================================ pivoted QR
+constexpr int QR_THREADS = 256;
+constexpr long long QR_BARRIER_SPINS = 1ll << 25;   // x ~64 ns sleeps: a few seconds
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -281,52 +284,52 @@ __global__ void qr_reset_kernel(QRState* st, int nprob) {
   st[p].key[0] = 0ull; st[p].key[1] = 0ull;
 }
 
-// Step j, one CTA per problem: choose the pivot, build the Householder
-// reflector H = I - tau v v^T with H x = beta e_j, store v and tau.
-__global__ void __launch_bounds__(256) qr_pivot_kernel(const QRProb* __restrict__ probs,
-                                                       QRState* __restrict__ st, int j,
-                                                       double* __restrict__ pool,
-                                                       int* __restrict__ piv,
-                                                       unsigned char* __restrict__ chosen,
-                                                       double* __restrict__ vbuf,
-                                                       int* __restrict__ ndone,
-                                                       DevStatus* dst, int level) {
-  const int p = blockIdx.x;
-  __shared__ double red[8];
+// Step j for problem p, by one whole CTA: choose the pivot, build the
+// Householder reflector H = I - tau v v^T with H x = beta e_j, store v and tau.
+__device__ void qr_pivot_step(int p, const QRProb* __restrict__ probs, QRState* __restrict__ st, int j,
+                              double* __restrict__ pool, int* __restrict__ piv,
+                              unsigned char* __restrict__ chosen, double* __restrict__ vbuf,
+                              int* __restrict__ ndone, DevStatus* dst, int level) {
+  __shared__ double red[QR_THREADS / 32];
   __shared__ int s_p, s_stop;
   QRState* S = st + p;
-  if (S->done) return;
-  const QRProb q = probs[p];
   const int t = threadIdx.x;
+  // every early return is preceded by a barrier after the shared flag is
+  // read, so the CTA's next problem cannot overwrite it under a slow thread
+  if (t == 0) s_stop = S->done;
+  __syncthreads();
+  const int was_done = s_stop;
+  __syncthreads();
+  if (was_done) return;
+  const QRProb q = probs[p];
   if (t == 0) {
     unsigned long long key = S->key[j & 1];
     int stop = 0;
     if (j >= q.maxk || j >= q.m || j >= q.cpiv || key == 0ull) stop = 1;
     s_p = stop ? -1 : 0xFFFF - (int)(key & 0xFFFFull);
+    if (stop) { S->done = 1; S->k = j; atomicAdd(ndone, 1); }
     s_stop = stop;
   }
   __syncthreads();
-  if (s_stop) {
-    if (t == 0) { S->done = 1; S->k = j; atomicAdd(ndone, 1); }
-    return;
-  }
+  const int stop1 = s_stop;
   const int pc = s_p;
+  __syncthreads();
+  if (stop1) return;
   double* a = pool + q.a + (int64_t)pc * q.lda;
   double s = 0.0;
-  for (int i = j + t; i < q.m; i += 256) s = fma(a[i], a[i], s);
+  for (int i = j + t; i < q.m; i += QR_THREADS) s = fma(a[i], a[i], s);
   s = warp_sum(s);
   if ((t & 31) == 0) red[t >> 5] = s;
   __syncthreads();
   if (t == 0) {
     double tot = 0.0;
-    for (int w = 0; w < 8; w++) tot += red[w];
+    for (int w = 0; w < QR_THREADS / 32; w++) tot += red[w];
     double nrm = sqrt(tot);
     if (!(nrm == nrm) || nrm > DBL_MAX) report(dst, RSF_ENUMERIC, level, p, j);
     if (j == 0) S->r11 = nrm;
     int stop = (nrm == 0.0) || (q.tol > 0.0 && nrm <= q.tol * S->r11) || !(nrm == nrm);
     if (stop) {
       S->done = 1; S->k = j; atomicAdd(ndone, 1);
-      s_stop = 1;
     } else {
       double x0 = a[j];
       double beta = x0 >= 0.0 ? -nrm : nrm;
@@ -337,30 +340,29 @@ __global__ void __launch_bounds__(256) qr_pivot_kernel(const QRProb* __restrict_
       piv[q.col0 + j] = pc;
       chosen[q.col0 + pc] = 1;
       S->key[(j + 1) & 1] = 0ull;
-      s_stop = 0;
     }
+    s_stop = stop;
   }
   __syncthreads();
-  if (s_stop) return;
-  const double inv_v0 = red[0];
-  double* v = vbuf + q.row0;
-  if (t == 0) v[j] = 1.0;
-  for (int i = j + 1 + t; i < q.m; i += 256) {
-    v[i] = a[i] * inv_v0;
-    a[i] = 0.0;
+  if (!s_stop) {
+    const double inv_v0 = red[0];
+    double* v = vbuf + q.row0;
+    if (t == 0) v[j] = 1.0;
+    for (int i = j + 1 + t; i < q.m; i += QR_THREADS) {
+      v[i] = a[i] * inv_v0;
+      a[i] = 0.0;
+    }
   }
+  __syncthreads();   // red and s_* are reused for the CTA's next problem
 }
 
-// Step j: apply H to every unchosen column, recompute its norm below row j
-// and offer it as the next pivot.  One warp per (problem, column).
-__global__ void qr_update_kernel(const QRProb* __restrict__ probs, QRState* __restrict__ st,
-                                 const int* __restrict__ colprefix, int nprob, int64_t ncols,
-                                 int j, double* __restrict__ pool,
-                                 const unsigned char* __restrict__ chosen,
-                                 const double* __restrict__ vbuf) {
-  int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (gw >= ncols) return;
+// Step j for global column gw, by one warp: apply H to the column (if it is
+// not chosen), recompute its norm below row j and offer it as the next pivot.
+__device__ __forceinline__ void qr_update_col(int64_t gw, int lane, const QRProb* __restrict__ probs,
+                                              QRState* __restrict__ st, const int* __restrict__ colprefix,
+                                              int nprob, int j, double* __restrict__ pool,
+                                              const unsigned char* __restrict__ chosen,
+                                              const double* __restrict__ vbuf) {
   int p = find_prob(colprefix, nprob, (int)gw);
   if (st[p].done) return;
   const QRProb q = probs[p];
@@ -379,6 +381,65 @@ __global__ void qr_update_kernel(const QRProb* __restrict__ probs, QRState* __re
   }
   n2 = warp_sum(n2);
   if (lane == 0 && col < q.cpiv) atomicMax(&st[p].key[(j + 1) & 1], pivot_key(n2, col));
+}
+
+// Grid-wide barrier of a cooperative launch (every CTA resident), with a
+// bounded wait: after QR_BARRIER_SPINS polls the CTA reports RSF_ETIMEOUT and
+// the caller leaves the kernel.  bar[0] counts arrivals, bar[1] is the
+// generation.
+__device__ bool qr_grid_barrier(unsigned int* bar, unsigned int nblocks, DevStatus* dst, int level) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* vgen = bar + 1;
+    const unsigned int g = *vgen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(bar, 1u) + 1u == nblocks) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long it = 0;
+      while (*vgen == g) {
+        if (++it > QR_BARRIER_SPINS) {
+          ok = 0;
+          report(dst, RSF_ETIMEOUT, level, -1, 0);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// The whole column-pivoted QR of a batch in one cooperative launch: per step
+// a pivot phase (CTAs over problems) and an update phase (warps over columns),
+// separated by grid barriers.  The loop ends after maxsteps steps or once every
+// problem is done; ndone changes only in a pivot phase, so every CTA reads the
+// same count between the two barriers of a step and all leave together.
+__global__ void __launch_bounds__(QR_THREADS) qr_persistent_kernel(
+    const QRProb* __restrict__ probs, QRState* __restrict__ st, const int* __restrict__ colprefix, int nprob,
+    int64_t ncols, int maxsteps, double* __restrict__ pool, int* __restrict__ piv,
+    unsigned char* __restrict__ chosen, double* __restrict__ vbuf, int* __restrict__ ndone,
+    unsigned int* __restrict__ bar, DevStatus* dst, int level) {
+  const unsigned int nb = gridDim.x;
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = ((int64_t)blockIdx.x * QR_THREADS + threadIdx.x) >> 5;
+  const int64_t nwarps = (int64_t)nb * (QR_THREADS / 32);
+  for (int j = 0; j <= maxsteps; j++) {
+    for (int p = blockIdx.x; p < nprob; p += nb)
+      qr_pivot_step(p, probs, st, j, pool, piv, chosen, vbuf, ndone, dst, level);
+    if (!qr_grid_barrier(bar, nb, dst, level)) return;
+    if (j == maxsteps || *(volatile int*)ndone >= nprob) return;
+    for (int64_t gw = wid; gw < ncols; gw += nwarps)
+      qr_update_col(gw, lane, probs, st, colprefix, nprob, j, pool, chosen, vbuf);
+    if (!qr_grid_barrier(bar, nb, dst, level)) return;
+  }
 }
 
 void QRBatch::build(const std::vector<QRProb>& p, cudaStream_t s) {
@@ -402,7 +463,23 @@ void QRBatch::build(const std::vector<QRProb>& p, cudaStream_t s) {
   piv.alloc(sizeof(int) * std::max<int64_t>(1, ncols), s);
   chosen.alloc(std::max<int64_t>(1, ncols), s);
   vbuf.alloc(sizeof(double) * std::max<int64_t>(1, nrows), s);
-  ndone.alloc(sizeof(int), s);
+  ndone.alloc(sizeof(int) * 4, s);   // [0] problems done, [1..2] the grid barrier
+}
+
+// CTAs of the persistent QR kernel that fit on the device at once (cached per
+// device; a cooperative launch needs all of them resident).
+static int qr_grid_capacity() {
+  static int cached[64] = {};
+  int dev = 0;
+  RSF_CUDA(cudaGetDevice(&dev));
+  if (dev >= 0 && dev < 64 && cached[dev] > 0) return cached[dev];
+  int sms = 0, per_sm = 0;
+  RSF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  RSF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qr_persistent_kernel, QR_THREADS, 0));
+  RSF_CHECK(per_sm > 0, RSF_ECUDA, "qr: the persistent kernel cannot be resident");
+  const int cap = sms * per_sm;
+  if (dev >= 0 && dev < 64) cached[dev] = cap;
+  return cap;
 }
 
 void QRBatch::run(double* pool, DevStatus* st, int level, cudaStream_t s) {
@@ -412,23 +489,29 @@ void QRBatch::run(double* pool, DevStatus* st, int level, cudaStream_t s) {
   int blocksU = cdiv(ncols * 32, 256);
   LAUNCH(qr_init_kernel, blocksU, 256, 0, s, prob.as<QRProb>(), state.as<QRState>(),
          colprefix.as<int>(), nprob, ncols, pool, chosen.as<unsigned char>());
-  int hdone = 0;
-  for (int j = 0; j <= maxsteps; j++) {
-    int tp = prof_begin(s);
-    LAUNCH(qr_pivot_kernel, nprob, 256, 0, s, prob.as<QRProb>(), state.as<QRState>(), j, pool,
-           piv.as<int>(), chosen.as<unsigned char>(), vbuf.as<double>(), ndone.as<int>(), st, level);
-    prof_end(tp, s, PROF_QR_PIVOT, 0.0, 0.0);
-    if (j == maxsteps) break;
-    int tu = prof_begin(s);
-    LAUNCH(qr_update_kernel, blocksU, 256, 0, s, prob.as<QRProb>(), state.as<QRState>(),
-           colprefix.as<int>(), nprob, ncols, j, pool, chosen.as<unsigned char>(), vbuf.as<double>());
-    prof_end(tu, s, PROF_QR_UPDATE, 0.0, 0.0);
-    if ((j & 31) == 31) {
-      d2h(&hdone, ndone.as<int>(), 1, s);
-      sync(s);
-      if (hdone >= nprob) break;
-    }
-  }
+  // one CTA per problem or one warp per column, at most what is resident
+  const int64_t want = std::max<int64_t>(nprob, cdiv(ncols, QR_THREADS / 32));
+  const int grid = (int)std::min<int64_t>(want, qr_grid_capacity());
+  const QRProb* a_probs = prob.as<QRProb>();
+  QRState* a_st = state.as<QRState>();
+  const int* a_cp = colprefix.as<int>();
+  int a_nprob = nprob;
+  int64_t a_ncols = ncols;
+  int a_maxsteps = maxsteps;
+  double* a_pool = pool;
+  int* a_piv = piv.as<int>();
+  unsigned char* a_chosen = chosen.as<unsigned char>();
+  double* a_vbuf = vbuf.as<double>();
+  int* a_ndone = ndone.as<int>();
+  unsigned int* a_bar = reinterpret_cast<unsigned int*>(ndone.as<int>() + 1);
+  DevStatus* a_dst = st;
+  int a_level = level;
+  void* args[] = {&a_probs, &a_st, &a_cp, &a_nprob, &a_ncols, &a_maxsteps, &a_pool,
+                  &a_piv, &a_chosen, &a_vbuf, &a_ndone, &a_bar, &a_dst, &a_level};
+  int tu = prof_begin(s);
+  RSF_CUDA(cudaLaunchCooperativeKernel((const void*)qr_persistent_kernel, dim3(grid), dim3(QR_THREADS), args, 0, s));
+  ::rsf::g_launches++;
+  prof_end(tu, s, PROF_QR_UPDATE, 0.0, 0.0);
 }
 
 // [S, R] split: S in pivot order, R = remaining eligible columns ascending.

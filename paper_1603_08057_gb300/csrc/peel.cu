@@ -410,42 +410,51 @@ void peel_traces(rsf_handle_s* F, rsf_handle_s* Fk, bool want0, double tol, cons
   const int nops = (int)ops.size();
 
   // G_o W for the wanted operators, row-major tree-order blocks in F's
-  // arithmetic (df64 pairs when F is mixed precision)
-  DBuf ga, gb2, gw, gx;
+  // arithmetic (df64 pairs when F is mixed precision).  Two symmetric forms
+  // with the traces of F^-1 and F^-1 F_k:
+  //   sym:  G_0 = F^-1,            G_1 = (F^-1 F_k + F_k F^-1) / 2   (Eq. (Gbb))
+  //   sqrt: G_0 = F^-1/2 F^-T/2,   G_1 = F^-1/2 F_k F^-T/2
+  // (F = F^1/2 F^T/2, so Tr(F^-1/2 F_k F^-T/2) = Tr(F^-T/2 F^-1/2 F_k)).
+  const bool sqrt_form = o.trace_form == RSF_TRACE_SQRT;
+  DBuf ga, gb2, gw;
   auto applyG = [&](const double* in, double* const out[2], int q) {
     const int64_t cnt = n64 * q;
     const int64_t bytes = sizeof(double) * cnt;
-    if (!Fk) {
-      solve_rows(F, RSF_OP_INV, in, out[0], q, df);
-      return;
-    }
-    if ((int64_t)ga.bytes < bytes) ga.alloc(bytes, s);
-    if ((int64_t)gb2.bytes < bytes) gb2.alloc(bytes, s);
-    if (df && !Fk->df) {
-      // F in df64, F_k in fp64: work on doubles, return df64 pairs
+    // doubles in and out when F is df64 but F_k is fp64
+    const bool split = Fk && df && !Fk->df;
+    const int io = split ? 0 : df;
+    const double* x = in;
+    if (split) {
       if ((int64_t)gw.bytes < bytes) gw.alloc(bytes, s);
-      if ((int64_t)gx.bytes < bytes) gx.alloc(bytes, s);
       RSF_CUDA(cudaMemcpyAsync(gw.p, in, bytes, cudaMemcpyDeviceToDevice, s));
       convert_df64(gw.as<double>(), cnt, 0, s);
-      solve_rows(F, RSF_OP_INV, gw.as<double>(), gx.as<double>(), q, 0);     // F^-1 W
-      if (want0) {
-        RSF_CUDA(cudaMemcpyAsync(out[0], gx.p, bytes, cudaMemcpyDeviceToDevice, s));
-        convert_df64(out[0], cnt, 1, s);
-      }
-      solve_rows(Fk, RSF_OP_APPLY, gw.as<double>(), ga.as<double>(), q, 0);
-      solve_rows(F, RSF_OP_INV, ga.as<double>(), gb2.as<double>(), q, 0);   // F^-1 F_k W
-      solve_rows(Fk, RSF_OP_APPLY, gx.as<double>(), out[1], q, 0);          // F_k F^-1 W
-      LAUNCH(average_kernel, cdiv(cnt, 256), 256, 0, s, out[1], gb2.as<double>(), cnt, 0);
-      convert_df64(out[1], cnt, 1, s);
-      return;
+      x = gw.as<double>();
     }
-    double* x3 = want0 ? out[0] : gb2.as<double>();
-    solve_rows(F, RSF_OP_INV, in, x3, q, df);                              // F^-1 W
-    solve_rows(Fk, RSF_OP_APPLY, x3, out[1], q, df);                       // F_k F^-1 W
-    solve_rows(Fk, RSF_OP_APPLY, in, ga.as<double>(), q, df);
-    double* x2 = want0 ? gb2.as<double>() : x3;
-    solve_rows(F, RSF_OP_INV, ga.as<double>(), x2, q, df);                 // F^-1 F_k W
-    LAUNCH(average_kernel, cdiv(cnt, 256), 256, 0, s, out[1], x2, cnt, df);
+    if ((int64_t)ga.bytes < bytes) ga.alloc(bytes, s);
+    if (sqrt_form) {
+      solve_rows(F, RSF_OP_INV_SQRT_T, x, ga.as<double>(), q, io);        // F^-T/2 W
+      if (want0 || !Fk) solve_rows(F, RSF_OP_INV_SQRT, ga.as<double>(), out[0], q, io);
+      if (Fk) {
+        if ((int64_t)gb2.bytes < bytes) gb2.alloc(bytes, s);
+        solve_rows(Fk, RSF_OP_APPLY, ga.as<double>(), gb2.as<double>(), q, io);
+        solve_rows(F, RSF_OP_INV_SQRT, gb2.as<double>(), out[1], q, io);   // F^-1/2 F_k F^-T/2 W
+      }
+    } else {
+      if (!Fk) {
+        solve_rows(F, RSF_OP_INV, x, out[0], q, io);
+        return;
+      }
+      if ((int64_t)gb2.bytes < bytes) gb2.alloc(bytes, s);
+      double* x3 = want0 ? out[0] : gb2.as<double>();
+      solve_rows(F, RSF_OP_INV, x, x3, q, io);                            // F^-1 W
+      solve_rows(Fk, RSF_OP_APPLY, x3, out[1], q, io);                    // F_k F^-1 W
+      solve_rows(Fk, RSF_OP_APPLY, x, ga.as<double>(), q, io);
+      double* x2 = want0 ? gb2.as<double>() : x3;
+      solve_rows(F, RSF_OP_INV, ga.as<double>(), x2, q, io);              // F^-1 F_k W
+      LAUNCH(average_kernel, cdiv(cnt, 256), 256, 0, s, out[1], x2, cnt, io);
+    }
+    if (split)
+      for (int oi : ops) convert_df64(out[oi], cnt, 1, s);
   };
 
   std::vector<PLevel> levels[2];

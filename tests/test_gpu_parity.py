@@ -108,9 +108,9 @@ def test_derivative_factorizations_apply(B, which):
     assert np.max(np.abs(got - ref)) <= 1e-7 * np.max(np.abs(ref))
 
 
-def _check_loglik_score(B, x, z, fam, th, alpha=0.0):
+def _check_loglik_score(B, x, z, fam, th, alpha=0.0, o=None):
     d = dense.score_dense(x, z, fam, th, alpha)
-    ll, g, terms = B.loglik_and_score(T(x), T(z), fam, th, 1e-9, 1e-6, alpha)
+    ll, g, terms = B.loglik_and_score(T(x), T(z), fam, th, 1e-9, 1e-6, alpha, o)
     assert abs(ll - d["ell"]) <= 1e-6 * abs(d["ell"])
     g = g.numpy()
     assert np.all(np.abs(g - d["g"]) <= 1e-3 * np.abs(d["g"]))
@@ -136,6 +136,33 @@ def test_loglik_and_score_rq_mixture(B):
     th = (0.05, 1.0, 1e-3)
     z = dense.sample_z_dense(x, K.RQ, th, W.standard_normal(3000, 122), 1.0)
     _check_loglik_score(B, x, z, K.RQ, th, 1.0)
+
+
+def test_sqrt_trace_form_matches_dense(B):
+    # the traces peeled on F^-1/2 F_k F^-T/2 and F^-1/2 F^-T/2 (same traces
+    # as F^-1 F_k and F^-1) meet the same bars as the paper's symmetrized form
+    o = B.opts(trace_form=B.TRACE_SQRT)
+    wl = W.WORKLOADS["matern32_uniform_n4096"]
+    x = W.uniform(wl["n"], wl["seed_points"])
+    z = dense.sample_z_dense(x, K.MATERN32, wl["theta"], W.standard_normal(wl["n"], wl["seed_z"]))
+    _check_loglik_score(B, x, z, K.MATERN32, wl["theta"], o=o)
+    x = W.mixture(3000, 121)
+    th = (0.05, 1.0, 1e-3)
+    z = dense.sample_z_dense(x, K.RQ, th, W.standard_normal(3000, 122), 1.0)
+    _check_loglik_score(B, x, z, K.RQ, th, 1.0, o=o)
+
+
+def test_sqrt_trace_form_nugget_identity(B):
+    x = W.mixture(3000, 151)
+    th = (0.05, 2.0, 1e-2)
+    o = B.opts(trace_form=B.TRACE_SQRT)
+    F = B.Factorization(T(x), B.MATERN32, th, B.SIGMA, 1e-9)
+    Fs = B.Factorization(T(x), B.MATERN32, th, B.D_S2, 1e-9)
+    tn = B.peel_trace(F, None, 1e-6, o)
+    ts = B.peel_trace(F, Fs, 1e-6, o)
+    assert th[1] * ts + th[2] * tn == pytest.approx(3000, rel=1e-6)
+    exact = np.trace(np.linalg.inv(dense.cov_matrix(x, K.MATERN32, th)))
+    assert abs(tn - exact) <= 1e-6 * abs(exact)
 
 
 @pytest.mark.parametrize("fam", [K.MATERN12, K.MATERN52])
@@ -230,6 +257,9 @@ def test_invalid_arguments_raise(B):
         Fl.logdet()
     with pytest.raises(B.RsfError):
         Fl.solve(T(np.ones(100)), B.OP_INV)
+    with pytest.raises(B.RsfError) as e:
+        B.Factorization(x, B.MATERN32, (0.1, 1.0, 1e-2), B.SIGMA, 1e-9, 0.0, B.opts(trace_form=7))
+    assert e.value.code == 1
 
 
 @pytest.mark.parametrize("prec", [0, 1])
