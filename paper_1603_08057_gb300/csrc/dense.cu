@@ -1,6 +1,7 @@
 // Batched ragged fp64 dense kernels: see dense.cuh.
 #include <algorithm>
 #include <cfloat>
+#include <cstdio>
 
 #include "dense.cuh"
 #include "df64.cuh"
@@ -527,9 +528,25 @@ void QRBatch::run(double* pool, DevStatus* st, int level, cudaStream_t s) {
   void* args[] = {&a_probs, &a_st, &a_cp, &a_nprob, &a_ncols, &a_maxsteps, &a_pool,
                   &a_piv, &a_chosen, &a_vbuf, &a_ndone, &a_bar, &a_dst, &a_level};
   int tu = prof_begin(s);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (verbose()) {
+    RSF_CUDA(cudaEventCreate(&e0));
+    RSF_CUDA(cudaEventCreate(&e1));
+    RSF_CUDA(cudaEventRecord(e0, s));
+  }
   RSF_CUDA(cudaLaunchCooperativeKernel((const void*)qr_persistent_kernel, dim3(grid), dim3(QR_THREADS), args, 0, s));
   ::rsf::g_launches++;
   prof_end(tu, s, PROF_QR_UPDATE, 0.0, 0.0);
+  if (verbose()) {
+    RSF_CUDA(cudaEventRecord(e1, s));
+    RSF_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    RSF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    fprintf(stderr, "[rsf] qr batch (level %d): %d problems, %lld columns, %lld rows, %d steps max, %.2f ms\n", level,
+            nprob, (long long)ncols, (long long)nrows, maxsteps, ms);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
 }
 
 // [S, R] split: S in pivot order, R = remaining eligible columns ascending.

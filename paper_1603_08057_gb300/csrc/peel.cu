@@ -528,13 +528,20 @@ void peel_traces(rsf_handle_s* F, rsf_handle_s* Fk, bool want0, double tol, cons
 
     // Per-operator sample counts.  Initial guess: at level 1 nine tenths of
     // the largest level-1 skeleton of F (the sibling-block ranks at eps_peel
-    // sit below the ID ranks at eps_fact); below, a fraction of the operator's
-    // largest rank on the previous level -- nine tenths near the top, where a
-    // retry (a new sketch of large blocks) is costly, seven tenths deeper,
-    // where surplus columns cost more than a retry.  The applications are
-    // shared: the columns drawn are those of the operator that needs the
-    // most, and each operator compresses with the first q_o of them (the
-    // columns are i.i.d., so any prefix is itself a valid test matrix).
+    // sit below the ID ranks at eps_fact); below, the operator's largest rank
+    // on the previous level times a per-level factor.  The factors follow the
+    // rank profiles measured for Matern 3/2 on clustered points at n = 65,536
+    // and 262,144 (from level 2 to 3 the ranks grow by up to 1.2x, deeper
+    // levels shrink them by 0.35-0.85x per level); a short guess costs a
+    // second sketch and QR of the level, a long one surplus columns, and the
+    // adaptive retry below keeps the result independent of the guess.
+    // The applications are shared: the columns drawn are those of the
+    // operator that needs the most, and each operator compresses with the
+    // first q_o of them (the columns are i.i.d., so any prefix is itself a
+    // valid test matrix).
+    auto level_factor = [](int l) {
+      return l <= 2 ? 0.9 : l == 3 ? 1.25 : l == 4 ? 0.85 : l == 5 ? 0.75 : l <= 7 ? 0.7 : 0.6;
+    };
     struct OpState {
       int qo = 0;
       bool done = true;
@@ -551,7 +558,7 @@ void peel_traces(rsf_handle_s* F, rsf_handle_s* Fk, bool want0, double tol, cons
         if (F->levels.size() > 1)
           for (int kk : F->levels[1].k) g = std::max(g, (9 * kk) / 10);
       } else {
-        g = std::max(g, (lev <= 3 ? 9 : 7) * r_prev[oi] / 10);
+        g = std::max(g, (int)(level_factor(lev) * r_prev[oi]));
       }
       st[oi].qo = g + c_over;
       st[oi].done = false;
@@ -560,6 +567,15 @@ void peel_traces(rsf_handle_s* F, rsf_handle_s* Fk, bool want0, double tol, cons
       st[oi].soff.assign(nop + 1, 0);
     }
     const int qcap = (int)std::min<int64_t>(n64, 1 << 15);
+    if (verbose()) {
+      int kf = 0, kfp = 0;
+      if ((int)F->levels.size() > lev)
+        for (int kk : F->levels[lev].k) kf = std::max(kf, kk);
+      if (lev > 1 && (int)F->levels.size() > lev - 1)
+        for (int kk : F->levels[lev - 1].k) kfp = std::max(kfp, kk);
+      fprintf(stderr, "[rsf] peel level %d: largest skeleton of F %d (level above %d), previous ranks %d %d\n", lev, kf,
+              kfp, r_prev[0], r_prev[1]);
+    }
     std::vector<int> chunk_q, chunk_col0;
     std::vector<DBuf> Wch, Ych[2];
     DBuf WV;
@@ -651,7 +667,10 @@ void peel_traces(rsf_handle_s* F, rsf_handle_s* Fk, bool want0, double tol, cons
         }
         // S_ab = [W_a(:, :q_o) V_a(:, :2 q_o)]^T Y_ab (3q_o x q_o): rows
         // 0..q_o-1 are Z_ab = W_a^T Y_ab (for the core of Eq. (lowrankapprox)),
-        // rows q_o..3q_o-1 the sketch of Y_ab by V_a
+        // rows q_o..3q_o-1 the sketch of Y_ab by V_a.  A box with at most 2 q_o
+        // rows needs no sketch: its rank-revealing QR runs on Y_ab itself.
+        std::vector<char> direct(nop);
+        for (int i = 0; i < nop; i++) direct[i] = TL.bx[op[i].a].cnt <= 2 * qo;
         S.Sb.alloc(sizeof(double) * std::max<int64_t>(1, S.soff[nop]), s);
         {
           std::vector<GemmDesc> g;
@@ -659,25 +678,44 @@ void peel_traces(rsf_handle_s* F, rsf_handle_s* Fk, bool want0, double tol, cons
             const PBox& A = TL.bx[op[i].a];
             g.push_back(mk(qo, qo, A.cnt, 0, woff[op[i].a], A.cnt, 1, 1, S.yoff[i], A.cnt, 0, 2, S.soff[i], 3 * qo,
                            1.0, 0.0));
-            g.push_back(mk(2 * qo, qo, A.cnt, 0, woff[op[i].a] + (int64_t)A.cnt * qtot, A.cnt, 1, 1, S.yoff[i],
-                           A.cnt, 0, 2, S.soff[i] + qo, 3 * qo, 1.0, 0.0));
+            if (!direct[i])
+              g.push_back(mk(2 * qo, qo, A.cnt, 0, woff[op[i].a] + (int64_t)A.cnt * qtot, A.cnt, 1, 1, S.yoff[i],
+                             A.cnt, 0, 2, S.soff[i] + qo, 3 * qo, 1.0, 0.0));
           }
           run_gemm(g, WV.as<double>(), S.Yb.as<double>(), S.Sb.as<double>(), nullptr, s, 1, 1, 1, 1, df);
           if (df) convert_df64(S.Sb.as<double>(), S.soff[nop], 0, s);
         }
-        // rank-revealing pivoted QR of the sketches (fp64, 2q_o x q_o each)
-        S.Sqr.alloc(sizeof(double) * std::max<int64_t>(1, (int64_t)nop * 2 * qo * qo), s);
+        // rank-revealing pivoted QR (fp64): the blocks taken from Y_ab first
+        // (one contiguous range, converted from df64 in place), then the
+        // 2q_o x q_o sketches
+        std::vector<int> qrows(nop);
+        std::vector<int64_t> qoff(nop, 0);
+        int64_t ndirect = 0, nqr = 0;
+        for (int i = 0; i < nop; i++) {
+          qrows[i] = direct[i] ? TL.bx[op[i].a].cnt : 2 * qo;
+          if (direct[i]) { qoff[i] = nqr; nqr += (int64_t)qrows[i] * qo; }
+        }
+        ndirect = nqr;
+        for (int i = 0; i < nop; i++)
+          if (!direct[i]) { qoff[i] = nqr; nqr += (int64_t)qrows[i] * qo; }
+        S.Sqr.alloc(sizeof(double) * std::max<int64_t>(1, nqr), s);
         {
-          std::vector<CopyProb> cp(nop);
-          for (int i = 0; i < nop; i++)
-            cp[i] = {2 * qo, qo, 3 * qo, 2 * qo, S.soff[i] + qo, (int64_t)i * 2 * qo * qo, 0};
-          copy_batched(cp, S.Sb.as<double>(), S.Sqr.as<double>(), s);
+          std::vector<CopyProb> cy, cs;
+          for (int i = 0; i < nop; i++) {
+            if (direct[i]) cy.push_back({qrows[i], qo, qrows[i], qrows[i], S.yoff[i], qoff[i], 0});
+            else cs.push_back({2 * qo, qo, 3 * qo, 2 * qo, S.soff[i] + qo, qoff[i], 0});
+          }
+          if (!cy.empty()) {
+            copy_batched(cy, S.Yb.as<double>(), S.Sqr.as<double>(), s);
+            if (df) convert_df64(S.Sqr.as<double>(), ndirect, 0, s);
+          }
+          if (!cs.empty()) copy_batched(cs, S.Sb.as<double>(), S.Sqr.as<double>(), s);
         }
         std::vector<QRProb> qp(nop);
         for (int i = 0; i < nop; i++) {
           qp[i] = QRProb{};
-          qp[i].m = 2 * qo; qp[i].c = qo; qp[i].cpiv = qo; qp[i].maxk = qo;
-          qp[i].lda = 2 * qo; qp[i].a = (int64_t)i * 2 * qo * qo; qp[i].tol = tol;
+          qp[i].m = qrows[i]; qp[i].c = qo; qp[i].cpiv = qo; qp[i].maxk = qo;
+          qp[i].lda = std::max(1, qrows[i]); qp[i].a = qoff[i]; qp[i].tol = tol;
         }
         S.qb = QRBatch();
         S.qb.build(qp, s);
