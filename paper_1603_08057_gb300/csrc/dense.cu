@@ -263,6 +263,7 @@ void GemmBatch::run(const GemmBases& b, cudaStream_t s) const {
 // ============================================================ pivoted QR
 constexpr int QR_THREADS = 256;
 constexpr long long QR_BARRIER_SPINS = 1ll << 25;   // x ~64 ns sleeps: a few seconds
+constexpr double QR_TOL3Z = 1.4901161193847656e-08;  // sqrt(2^-52)
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -280,7 +281,8 @@ __device__ __forceinline__ unsigned long long pivot_key(double norm2, int col) {
 // Initial column norms: one warp per (problem, eligible column).
 __global__ void qr_init_kernel(const QRProb* __restrict__ probs, QRState* __restrict__ st,
                                const int* __restrict__ colprefix, int nprob, int64_t ncols,
-                               const double* __restrict__ pool, unsigned char* __restrict__ chosen) {
+                               const double* __restrict__ pool, unsigned char* __restrict__ chosen,
+                               double* __restrict__ nu2, double* __restrict__ nuref2) {
   int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (gw >= ncols) return;
@@ -293,7 +295,11 @@ __global__ void qr_init_kernel(const QRProb* __restrict__ probs, QRState* __rest
   double s = 0.0;
   for (int i = lane; i < q.m; i += 32) s = fma(a[i], a[i], s);
   s = warp_sum(s);
-  if (lane == 0) atomicMax(&st[p].key[0], pivot_key(s, col));
+  if (lane == 0) {
+    nu2[q.col0 + col] = s;
+    nuref2[q.col0 + col] = s;
+    atomicMax(&st[p].key[0], pivot_key(s, col));
+  }
 }
 
 __global__ void qr_reset_kernel(QRState* st, int nprob) {
@@ -376,12 +382,19 @@ __device__ void qr_pivot_step(int p, const QRProb* __restrict__ probs, QRState* 
 }
 
 // Step j for global column gw, by one warp: apply H to the column (if it is
-// not chosen), recompute its norm below row j and offer it as the next pivot.
+// not chosen) and offer it as the next pivot.  The norm below row j is
+// downdated, nu^2 <- nu^2 - a_j^2 (a_j the updated entry in row j, since H is
+// orthogonal on rows >= j), and recomputed from the updated column whenever
+// the downdate has lost more than half the digits: nu^2 <= sqrt(eps) times
+// the norm^2 of the last exact computation (the safeguard of the LAPACK
+// pivoted QR, Drmac & Bujanovic 2008).  That saves one of the three fp64
+// multiply-adds per element and step.
 __device__ __forceinline__ void qr_update_col(int64_t gw, int lane, const QRProb* __restrict__ probs,
                                               QRState* __restrict__ st, const int* __restrict__ colprefix,
                                               int nprob, int j, double* __restrict__ pool,
                                               const unsigned char* __restrict__ chosen,
-                                              const double* __restrict__ vbuf) {
+                                              const double* __restrict__ vbuf, double* __restrict__ nu2,
+                                              double* __restrict__ nuref2) {
   int p = find_prob(colprefix, nprob, (int)gw);
   if (st[p].done) return;
   const QRProb q = probs[p];
@@ -392,14 +405,32 @@ __device__ __forceinline__ void qr_update_col(int64_t gw, int lane, const QRProb
   double s = 0.0;
   for (int i = j + lane; i < q.m; i += 32) s = fma(v[i], a[i], s);
   s = warp_sum(s) * st[p].tau;
+  const bool track = col < q.cpiv;
+  double nu = 0.0, nref = 0.0;
+  bool recompute = false;
+  if (track) {
+    const double xj = a[j] - s;   // v[j] = 1
+    nref = nuref2[q.col0 + col];
+    nu = nu2[q.col0 + col] - xj * xj;
+    recompute = !(nu > QR_TOL3Z * nref);
+  }
+  __syncwarp();   // every lane has read a[j] before lane 0 overwrites it
   double n2 = 0.0;
   for (int i = j + lane; i < q.m; i += 32) {
     double x = fma(-s, v[i], a[i]);
     a[i] = x;
-    if (i > j) n2 = fma(x, x, n2);
+    if (recompute && i > j) n2 = fma(x, x, n2);
   }
-  n2 = warp_sum(n2);
-  if (lane == 0 && col < q.cpiv) atomicMax(&st[p].key[(j + 1) & 1], pivot_key(n2, col));
+  if (recompute) {
+    n2 = warp_sum(n2);
+    nu = n2;
+    nref = n2;
+  }
+  if (lane == 0 && track) {
+    nu2[q.col0 + col] = nu;
+    nuref2[q.col0 + col] = nref;
+    atomicMax(&st[p].key[(j + 1) & 1], pivot_key(nu, col));
+  }
 }
 
 // Grid-wide barrier of a cooperative launch (every CTA resident), with a
@@ -444,8 +475,9 @@ __device__ bool qr_grid_barrier(unsigned int* bar, unsigned int nblocks, DevStat
 __global__ void __launch_bounds__(QR_THREADS) qr_persistent_kernel(
     const QRProb* __restrict__ probs, QRState* __restrict__ st, const int* __restrict__ colprefix, int nprob,
     int64_t ncols, int maxsteps, double* __restrict__ pool, int* __restrict__ piv,
-    unsigned char* __restrict__ chosen, double* __restrict__ vbuf, int* __restrict__ ndone,
-    unsigned int* __restrict__ bar, DevStatus* dst, int level) {
+    unsigned char* __restrict__ chosen, double* __restrict__ vbuf, double* __restrict__ nu2,
+    double* __restrict__ nuref2, int* __restrict__ ndone, unsigned int* __restrict__ bar, DevStatus* dst,
+    int level) {
   const unsigned int nb = gridDim.x;
   const int lane = threadIdx.x & 31;
   const int64_t wid = ((int64_t)blockIdx.x * QR_THREADS + threadIdx.x) >> 5;
@@ -456,7 +488,7 @@ __global__ void __launch_bounds__(QR_THREADS) qr_persistent_kernel(
     if (!qr_grid_barrier(bar, nb, dst, level)) return;
     if (j == maxsteps || *(volatile int*)ndone >= nprob) return;
     for (int64_t gw = wid; gw < ncols; gw += nwarps)
-      qr_update_col(gw, lane, probs, st, colprefix, nprob, j, pool, chosen, vbuf);
+      qr_update_col(gw, lane, probs, st, colprefix, nprob, j, pool, chosen, vbuf, nu2, nuref2);
     if (!qr_grid_barrier(bar, nb, dst, level)) return;
   }
 }
@@ -482,6 +514,8 @@ void QRBatch::build(const std::vector<QRProb>& p, cudaStream_t s) {
   piv.alloc(sizeof(int) * std::max<int64_t>(1, ncols), s);
   chosen.alloc(std::max<int64_t>(1, ncols), s);
   vbuf.alloc(sizeof(double) * std::max<int64_t>(1, nrows), s);
+  nu2.alloc(sizeof(double) * std::max<int64_t>(1, ncols), s);
+  nuref2.alloc(sizeof(double) * std::max<int64_t>(1, ncols), s);
   ndone.alloc(sizeof(int) * 4, s);   // [0] problems done, [1..2] the grid barrier
 }
 
@@ -507,7 +541,8 @@ void QRBatch::run(double* pool, DevStatus* st, int level, cudaStream_t s) {
   ndone.zero();
   int blocksU = cdiv(ncols * 32, 256);
   LAUNCH(qr_init_kernel, blocksU, 256, 0, s, prob.as<QRProb>(), state.as<QRState>(),
-         colprefix.as<int>(), nprob, ncols, pool, chosen.as<unsigned char>());
+         colprefix.as<int>(), nprob, ncols, pool, chosen.as<unsigned char>(), nu2.as<double>(),
+         nuref2.as<double>());
   // one CTA per problem or one warp per column, at most what is resident
   const int64_t want = std::max<int64_t>(nprob, cdiv(ncols, QR_THREADS / 32));
   const int grid = (int)std::min<int64_t>(want, qr_grid_capacity());
@@ -521,12 +556,14 @@ void QRBatch::run(double* pool, DevStatus* st, int level, cudaStream_t s) {
   int* a_piv = piv.as<int>();
   unsigned char* a_chosen = chosen.as<unsigned char>();
   double* a_vbuf = vbuf.as<double>();
+  double* a_nu2 = nu2.as<double>();
+  double* a_nuref2 = nuref2.as<double>();
   int* a_ndone = ndone.as<int>();
   unsigned int* a_bar = reinterpret_cast<unsigned int*>(ndone.as<int>() + 1);
   DevStatus* a_dst = st;
   int a_level = level;
   void* args[] = {&a_probs, &a_st, &a_cp, &a_nprob, &a_ncols, &a_maxsteps, &a_pool,
-                  &a_piv, &a_chosen, &a_vbuf, &a_ndone, &a_bar, &a_dst, &a_level};
+                  &a_piv, &a_chosen, &a_vbuf, &a_nu2, &a_nuref2, &a_ndone, &a_bar, &a_dst, &a_level};
   int tu = prof_begin(s);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (verbose()) {
