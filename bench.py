@@ -8,6 +8,7 @@ traces and the score.  theta's length scale is perturbed every step
 (l * (1 + 1e-3 i)) so nothing carries over between steps.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                      [--precision mixed|fp64]
 Under torchrun each rank runs its own evaluations (independent theta values;
 replicas, weak scaling) and rank 0 prints one JSON line.
 
@@ -37,6 +38,9 @@ from paper_1603_08057_gb300 import workloads as WL  # noqa: E402
 WORKLOAD = "matern32_mixture_n262144"
 METRIC = "loglik+score evals/s at n=262k: plain FP64 vs batched mixed form at 1e-6 rel err"
 UNIT = "evals/s"
+FORMS = {"mixed": "mixed precision: fp64 IDs, Cholesky/QR factors, log-determinant and rank decisions; "
+                  "df64 (fp32-pair) multi-RHS solves and peeling GEMMs",
+         "fp64": "plain fp64 RSF + weak peeling"}
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 # df64 multiply-add = 12 fp32-pipe instructions (1 mul, 3 fma for the exact
 # product, 6 for TwoSum, 2 for the error accumulation); 128 fp32 lanes per SM
@@ -53,6 +57,9 @@ def parse():
     p.add_argument("--n", type=int, default=None, help="override the point count (testing)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
+                   help="mixed (default): fp64 IDs, Cholesky/QR factors and log-determinant, df64 "
+                        "solves and peeling GEMMs; fp64: every step in fp64 (the plain form)")
     return p.parse_args()
 
 
@@ -217,8 +224,10 @@ def run_gpu(args):
     def theta(i):
         return (th0[0] * (1 + 1e-3 * (i % 7)), th0[1], th0[2])
 
+    o = B.opts(precision=B.PREC_MIXED if args.precision == "mixed" else B.PREC_FP64)
+
     def step(i):
-        return B.loglik_and_score(pts, z, B.MATERN32, theta(i), wl["tol_fact"], wl["tol_peel"])
+        return B.loglik_and_score(pts, z, B.MATERN32, theta(i), wl["tol_fact"], wl["tol_peel"], 0.0, o)
 
     for i in range(args.warmup):
         step(i)
@@ -261,7 +270,7 @@ def run_gpu(args):
         for i in range(max(1, min(args.steps, 1))):
             dp.copy_(hp, non_blocking=True)
             dz.copy_(hz, non_blocking=True)
-            B.loglik_and_score(dp, dz, B.MATERN32, theta(i), wl["tol_fact"], wl["tol_peel"])
+            B.loglik_and_score(dp, dz, B.MATERN32, theta(i), wl["tol_fact"], wl["tol_peel"], 0.0, o)
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
         e2e = {"value": max(1, min(args.steps, 1)) / te, "unit": UNIT, "h2d_bytes_per_step": int(hp.numel() * 8 + hz.numel() * 8),
@@ -298,8 +307,9 @@ def run_gpu(args):
     ll, gsc, terms = results[-1]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(cfg, parallelism=f"replicas x{ws}", form="plain fp64 RSF + weak peeling"),
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+df64" if args.precision == "mixed" else "f64",
+            "data": "synthetic",
+            "config": dict(cfg, parallelism=f"replicas x{ws}", form=FORMS[args.precision]),
             "clocks": clk.summary(), "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
             "e2e": e2e, "last_eval": {"loglik": ll, "score": gsc.tolist(), "terms": terms.tolist()}}
     print(json.dumps(line), flush=True)

@@ -131,6 +131,22 @@ void rsf_opts_default(rsf_opts* o);
 /* Message of the last failing call on this thread ("" if none). */
 const char* rsf_last_error(void);
 
+/* Device-memory hook.  The paper has no counterpart: this lets a host
+ * framework back every device allocation the library makes (factor storage,
+ * solve and peeling work buffers) with its own allocator, e.g. PyTorch's
+ * caching allocator.  alloc(bytes, stream, ctx) returns a device pointer to
+ * at least `bytes` bytes that may be used in stream order on `stream`, or
+ * NULL on failure (the library call then fails with RSF_ENOMEM); free(ptr,
+ * bytes, stream, ctx) returns it, in stream order, on the stream it was
+ * allocated for.  Passing NULL for both restores the default
+ * (cudaMallocAsync / cudaFreeAsync); one NULL and one non-NULL is
+ * RSF_EINVAL.  Memory is always returned through the hook that allocated it,
+ * even if the hook changes in between.  The setting is process-wide: change
+ * it only while no other thread is inside the library. */
+typedef void* (*rsf_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*rsf_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
+rsf_status rsf_set_allocator(rsf_alloc_fn alloc_fn, rsf_free_fn free_fn, void* ctx);
+
 /* Quadtree of Sec. 2.1 / Remark (tree) over `points` (device, n x 2).
  * Split while a box holds more than opts->n_occ points; children in Morton
  * order.  The tree keeps its own copy of the points (tree order) and may be

@@ -26,7 +26,7 @@ EXPORTS = ["rsf_opts_default", "rsf_last_error", "rsf_tree_build", "rsf_tree_des
            "rsf_build", "rsf_build_on_tree", "rsf_logdet", "rsf_solve", "rsf_peel_trace",
            "gp_loglik", "gp_score", "gp_loglik_and_score", "rsf_get_info",
            "rsf_launch_count", "rsf_profile_enable", "rsf_profile_read", "rsf_destroy",
-           "rsf_solve_noalloc"]
+           "rsf_solve_noalloc", "rsf_set_allocator"]
 
 
 class RsfKernel(C.Structure):
@@ -79,6 +79,7 @@ def lib():
         L.rsf_build_on_tree.argtypes = [vp, C.POINTER(RsfKernel), dp, ip, C.c_double,
                                         C.POINTER(RsfOpts), C.POINTER(vp)]
         L.rsf_logdet.argtypes = [vp, dp]
+        L.rsf_set_allocator.argtypes = [_ALLOC_FN, _FREE_FN, vp]
         L.rsf_solve.argtypes = [vp, vp, i64, ip, ip]
         L.rsf_solve_noalloc.argtypes = [vp, vp, i64, ip, ip]
         L.rsf_peel_trace.argtypes = [vp, vp, C.c_double, C.POINTER(RsfOpts), dp]
@@ -141,6 +142,40 @@ PROF_GEMM, PROF_QR_UPDATE, PROF_QR_PIVOT = 0, 1, 2
 PROF_PEEL_APPLY, PROF_PEEL_SUB, PROF_PEEL_QR, PROF_PEEL_REST, PROF_FACTOR, PROF_GEMM_DF = 3, 4, 5, 6, 7, 8
 PROF_NAMES = ["gemm_fp64", "qr", "qr_pivot", "peel_apply", "peel_sub", "peel_qr", "peel_rest",
               "factor", "gemm_df64"]
+
+
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+_hooks = None   # keeps the ctypes callbacks alive while installed
+
+
+def use_torch_allocator(enable: bool = True) -> None:
+    """rsf_set_allocator with PyTorch's caching allocator (enable) or the
+    library's default cudaMallocAsync (disable).  Every device buffer the
+    library allocates afterwards comes from, and returns to, the torch pool of
+    the current device, on the library's stream."""
+    global _hooks
+    if not enable:
+        _check(lib().rsf_set_allocator(_ALLOC_FN(), _FREE_FN(), None))
+        _hooks = None
+        return
+    dev = torch.cuda.current_device()
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), dev, int(stream or 0))
+        except Exception:   # reported by the library as RSF_ENOMEM
+            return None
+
+    def _free(ptr, nbytes, stream, ctx):
+        try:
+            torch.cuda.caching_allocator_delete(ptr)
+        except Exception:   # interpreter shutdown: torch already torn down
+            pass
+
+    hooks = (_ALLOC_FN(_alloc), _FREE_FN(_free))
+    _check(lib().rsf_set_allocator(hooks[0], hooks[1], None))
+    _hooks = hooks
 
 
 def profile(enable: bool) -> None:

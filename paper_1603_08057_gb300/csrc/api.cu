@@ -99,6 +99,13 @@ void prof_end(int token, cudaStream_t s, int cat, double flops, double bytes) {
 
 void fail(rsf_status code, const std::string& msg) { throw Exception{code, msg}; }
 
+static std::mutex g_hook_mu;
+static AllocHook g_hook;
+AllocHook alloc_hook() {
+  std::lock_guard<std::mutex> lk(g_hook_mu);
+  return g_hook;
+}
+
 // Trees handed out through the C ABI; handles share ownership.
 static std::mutex g_tree_mu;
 static std::map<rsf_tree_s*, std::shared_ptr<rsf_tree_s>> g_trees;
@@ -265,6 +272,17 @@ void rsf_opts_default(rsf_opts* o) {
 }
 
 const char* rsf_last_error(void) { return g_err.c_str(); }
+
+rsf_status rsf_set_allocator(rsf_alloc_fn alloc_fn, rsf_free_fn free_fn, void* ctx) {
+  API_BEGIN
+  RSF_CHECK((alloc_fn == nullptr) == (free_fn == nullptr), RSF_EINVAL,
+            "rsf_set_allocator: alloc_fn and free_fn must both be set or both be NULL");
+  std::lock_guard<std::mutex> lk(g_hook_mu);
+  g_hook.alloc = alloc_fn;
+  g_hook.free = free_fn;
+  g_hook.ctx = alloc_fn ? ctx : nullptr;
+  API_END
+}
 
 rsf_status rsf_tree_build(const double* points, int64_t n, const rsf_opts* opts, void* stream, rsf_tree* out) {
   API_BEGIN

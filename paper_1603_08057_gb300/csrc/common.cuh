@@ -78,11 +78,23 @@ __device__ __forceinline__ void report(DevStatus* st, int code, int level, int b
 }
 
 // ---------------------------------------------------------- device memory
-// Stream-ordered allocation; the owner frees on the same stream.
+// Allocator hook set through rsf_set_allocator (null members: the default,
+// stream-ordered cudaMallocAsync / cudaFreeAsync).
+struct AllocHook {
+  rsf_alloc_fn alloc = nullptr;
+  rsf_free_fn free = nullptr;
+  void* ctx = nullptr;
+};
+AllocHook alloc_hook();
+
+// Stream-ordered allocation; the owner frees on the same stream, through the
+// allocator that provided the memory.
 struct DBuf {
   void* p = nullptr;
   size_t bytes = 0;
   cudaStream_t s = nullptr;
+  rsf_free_fn hfree = nullptr;   // non-null: memory from the hook
+  void* hctx = nullptr;
   DBuf() = default;
   DBuf(const DBuf&) = delete;
   DBuf& operator=(const DBuf&) = delete;
@@ -90,8 +102,8 @@ struct DBuf {
   DBuf& operator=(DBuf&& o) noexcept {
     if (this != &o) {
       release();
-      p = o.p; bytes = o.bytes; s = o.s;
-      o.p = nullptr; o.bytes = 0;
+      p = o.p; bytes = o.bytes; s = o.s; hfree = o.hfree; hctx = o.hctx;
+      o.p = nullptr; o.bytes = 0; o.hfree = nullptr; o.hctx = nullptr;
     }
     return *this;
   }
@@ -101,15 +113,31 @@ struct DBuf {
     s = stream;
     bytes = nbytes;
     if (nbytes == 0) return;
-    RSF_CUDA(cudaMallocAsync(&p, nbytes, stream));
+    const AllocHook h = alloc_hook();
+    if (h.alloc) {
+      p = h.alloc(nbytes, (void*)stream, h.ctx);
+      if (!p) {
+        bytes = 0;
+        RSF_CHECK(false, RSF_ENOMEM, "the allocator hook returned NULL for " + std::to_string(nbytes) + " bytes");
+      }
+      hfree = h.free;
+      hctx = h.ctx;
+    } else {
+      RSF_CUDA(cudaMallocAsync(&p, nbytes, stream));
+    }
   }
   void zero() {
     if (bytes) RSF_CUDA(cudaMemsetAsync(p, 0, bytes, s));
   }
   void release() {
-    if (p) cudaFreeAsync(p, s);
+    if (p) {
+      if (hfree) hfree(p, bytes, (void*)s, hctx);
+      else cudaFreeAsync(p, s);
+    }
     p = nullptr;
     bytes = 0;
+    hfree = nullptr;
+    hctx = nullptr;
   }
   template <class T> T* as() const { return static_cast<T*>(p); }
 };
