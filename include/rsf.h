@@ -123,6 +123,7 @@ typedef struct {
   int64_t factor_entries;/* entries of T, E and the diagonal blocks */
   double flops;          /* algorithmic fp64 flops of the factorization */
   double kernel_evals;   /* kernel evaluations during the factorization */
+  int nsets;             /* independent point sets (1 unless built batched) */
 } rsf_info_t;
 
 /* Fills *o with the defaults listed above. */
@@ -166,9 +167,31 @@ rsf_status rsf_build_on_tree(rsf_tree tree, const rsf_kernel* kernel,
                              const double* theta, int which, double tol,
                              const rsf_opts* opts, rsf_handle* out);
 
+/* Batched datasets.  The paper treats one point set; a batch of nsets
+ * independent sets has the block-diagonal covariance diag(Sigma_1, ...),
+ * factored here as one forest: every set gets its own quadtree (own root
+ * square, Sec. 2.1) and the boxes of all sets at one level are skeletonized
+ * by the same level-batched launches (boxes of different sets never
+ * interact).  points (device, offsets[nsets] x 2 row-major) holds set i in
+ * rows offsets[i] .. offsets[i+1]-1; offsets (host, nsets + 1 entries,
+ * offsets[0] = 0, strictly increasing) is read during the call only.  The
+ * handle then acts on the concatenated index space: rsf_solve applies the
+ * block-diagonal operator, rsf_logdet returns the sum over the sets,
+ * rsf_logdet_sets the per-set values.  Same theta for every set.
+ * RSF_EINVAL for nsets outside 1 .. 16384 or an empty set. */
+rsf_status rsf_build_batched(int nsets, const int64_t* offsets, const double* points,
+                             const rsf_kernel* kernel, const double* theta, int which,
+                             double tol, const rsf_opts* opts, void* stream,
+                             rsf_handle* out);
+
 /* log|F| = 2 log|C| (Sec. 2.3.2) to *out (host).  Synchronises the stream.
- * RSF_EINVAL for derivative factorizations. */
+ * For a batched handle the sum over its sets.  RSF_EINVAL for derivative
+ * factorizations. */
 rsf_status rsf_logdet(rsf_handle h, double* out);
+
+/* log|F_i| of every point set i of the handle (rsf_get_info's nsets values,
+ * host array out).  Synchronises the stream. */
+rsf_status rsf_logdet_sets(rsf_handle h, double* out);
 
 /* In place B <- op(F) B for B (device, column-major n x nrhs, ld ldb >= n,
  * original point order).  Stream-ordered (does not synchronise). */
@@ -223,6 +246,19 @@ rsf_status gp_loglik_and_score(const double* points, const double* z, int64_t n,
                                double tol_fact, double tol_peel,
                                const rsf_opts* opts, void* stream,
                                double* loglik, double* score, double* terms);
+
+/* Algorithm 1 for nsets independent datasets in one forest (see
+ * rsf_build_batched for points and offsets; z device, offsets[nsets]
+ * entries in the same order as the points).  Per set i: loglik[i] and, when
+ * score != NULL, score[3 i .. 3 i + 2] and terms[6 i .. 6 i + 5] (host), each
+ * exactly what gp_loglik_and_score returns for that set alone up to the
+ * peeling's test matrices (shared by all sets). */
+rsf_status gp_loglik_and_score_batched(int nsets, const int64_t* offsets,
+                                       const double* points, const double* z,
+                                       const rsf_kernel* kernel, const double* theta,
+                                       double tol_fact, double tol_peel,
+                                       const rsf_opts* opts, void* stream,
+                                       double* loglik, double* score, double* terms);
 
 /* Factorization summary (host struct). */
 rsf_status rsf_get_info(rsf_handle h, rsf_info_t* info);

@@ -10,6 +10,7 @@ from __future__ import annotations
 import ctypes as C
 import os
 
+import numpy as np
 import torch
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -26,7 +27,8 @@ EXPORTS = ["rsf_opts_default", "rsf_last_error", "rsf_tree_build", "rsf_tree_des
            "rsf_build", "rsf_build_on_tree", "rsf_logdet", "rsf_solve", "rsf_peel_trace",
            "gp_loglik", "gp_score", "gp_loglik_and_score", "rsf_get_info",
            "rsf_launch_count", "rsf_profile_enable", "rsf_profile_read", "rsf_destroy",
-           "rsf_solve_noalloc", "rsf_set_allocator"]
+           "rsf_solve_noalloc", "rsf_set_allocator", "rsf_build_batched", "rsf_logdet_sets",
+           "gp_loglik_and_score_batched"]
 
 
 class RsfKernel(C.Structure):
@@ -48,7 +50,7 @@ class RsfInfo(C.Structure):
     _fields_ = [("n", C.c_int64), ("levels", C.c_int), ("boxes", C.c_int64),
                 ("root_size", C.c_int), ("max_rank", C.c_int), ("max_active", C.c_int),
                 ("factor_entries", C.c_int64), ("flops", C.c_double),
-                ("kernel_evals", C.c_double)]
+                ("kernel_evals", C.c_double), ("nsets", C.c_int)]
 
 
 class RsfError(RuntimeError):
@@ -88,6 +90,11 @@ def lib():
         L.gp_loglik_and_score.argtypes = [vp, vp, i64, C.POINTER(RsfKernel), dp, C.c_double,
                                           C.c_double, C.POINTER(RsfOpts), vp, dp, dp, dp]
         L.rsf_get_info.argtypes = [vp, C.POINTER(RsfInfo)]
+        L.rsf_build_batched.argtypes = [ip, C.POINTER(C.c_int64), vp, C.POINTER(RsfKernel), dp, ip,
+                                        C.c_double, C.POINTER(RsfOpts), vp, C.POINTER(vp)]
+        L.rsf_logdet_sets.argtypes = [vp, dp]
+        L.gp_loglik_and_score_batched.argtypes = [ip, C.POINTER(C.c_int64), vp, vp, C.POINTER(RsfKernel), dp,
+                                                  C.c_double, C.c_double, C.POINTER(RsfOpts), vp, dp, dp, dp]
         L.rsf_profile_enable.argtypes = [ip]
         L.rsf_profile_enable.restype = None
         L.rsf_profile_read.argtypes = [ip, ip, C.POINTER(C.c_int64), dp, dp, dp]
@@ -213,11 +220,20 @@ class Factorization:
     dSigma/dtheta (which=D_L, D_S2)."""
 
     def __init__(self, points_or_tree, family, theta, which=SIGMA, tol=1e-9, alpha=0.0,
-                 o: RsfOpts | None = None):
+                 o: RsfOpts | None = None, offsets=None):
+        """offsets (sequence of nsets + 1 ints): points holds nsets independent
+        datasets, set i in rows offsets[i]:offsets[i+1] (rsf_build_batched)."""
         self.kernel = RsfKernel(family, alpha)
         self.h = C.c_void_p()
         th = _theta(theta)
-        if isinstance(points_or_tree, Tree):
+        if offsets is not None:
+            pts = _dev(points_or_tree)
+            self.n = pts.shape[0]
+            self.tree = None
+            off = _offsets(offsets, self.n)
+            _check(lib().rsf_build_batched(len(off) - 1, off, pts.data_ptr(), C.byref(self.kernel), th, which, tol,
+                                           C.byref(o) if o else None, _stream(), C.byref(self.h)))
+        elif isinstance(points_or_tree, Tree):
             self.tree = points_or_tree
             self.n = self.tree.n
             _check(lib().rsf_build_on_tree(self.tree.h, C.byref(self.kernel), th, which, tol,
@@ -233,6 +249,13 @@ class Factorization:
         if getattr(self, "h", None) and _lib is not None:
             _lib.rsf_destroy(self.h)
             self.h = None
+
+    def logdet_sets(self):
+        """rsf_logdet_sets: per-dataset log-determinants (numpy array)."""
+        k = self.info()["nsets"]
+        v = (C.c_double * k)()
+        _check(lib().rsf_logdet_sets(self.h, v))
+        return np.array(list(v))
 
     def logdet(self) -> float:
         v = C.c_double()
@@ -305,6 +328,35 @@ def loglik_and_score(points, z, family, theta, tol_fact=1e-9, tol_peel=1e-6, alp
     if not want_score:
         return ll.value, None, None
     return ll.value, torch.tensor(list(g), dtype=torch.float64), torch.tensor(list(t), dtype=torch.float64)
+
+
+def _offsets(offsets, n):
+    off = [int(v) for v in offsets]
+    if len(off) < 2 or off[0] != 0 or off[-1] != n:
+        raise ValueError("offsets must start at 0 and end at the number of points")
+    return (C.c_int64 * len(off))(*off)
+
+
+def loglik_and_score_batched(points, offsets, z, family, theta, tol_fact=1e-9, tol_peel=1e-6, alpha=0.0,
+                             o: RsfOpts | None = None, want_score=True):
+    """gp_loglik_and_score_batched: Algorithm 1 for nsets independent datasets
+    in one forest.  Returns numpy arrays loglik (nsets,), score (nsets, 3)
+    and terms (nsets, 6); the last two are None when want_score is False."""
+    pts = _dev(points)
+    n = pts.shape[0]
+    zz = _dev(z, (n,))
+    off = _offsets(offsets, n)
+    k = len(off) - 1
+    kern = RsfKernel(family, alpha)
+    ll = (C.c_double * k)()
+    g = (C.c_double * (3 * k))()
+    t = (C.c_double * (6 * k))()
+    _check(lib().gp_loglik_and_score_batched(k, off, pts.data_ptr(), zz.data_ptr(), C.byref(kern), _theta(theta),
+                                             tol_fact, tol_peel, C.byref(o) if o else None, _stream(), ll,
+                                             g if want_score else None, t if want_score else None))
+    if not want_score:
+        return np.array(list(ll)), None, None
+    return np.array(list(ll)), np.array(list(g)).reshape(k, 3), np.array(list(t)).reshape(k, 6)
 
 
 class GPLogLikelihood(torch.autograd.Function):

@@ -132,39 +132,52 @@ __global__ void from_tree_kernel(const double* __restrict__ X, int64_t n, int q,
 enum { S_QUAD = 0, S_LOGDET, S_LOGLIK, S_AA, S_QL, S_QF, S_TNUG, S_TL, S_G0, S_G1, S_G2,
        S_T0, S_T1, S_T2, S_T3, S_T4, S_T5, S_NSLOTS };
 
-// Eq. (loglikelihood): l = -quad/2 - log|F|/2 - n/2 log(2 pi)
-__global__ void loglik_kernel(double* sc, int64_t n) {
-  if (threadIdx.x == 0 && blockIdx.x == 0)
-    sc[S_LOGLIK] = -0.5 * sc[S_QUAD] - 0.5 * sc[S_LOGDET] - 0.5 * (double)n * log(2.0 * 3.141592653589793);
+// Every point set (one for a plain quadtree, several for batched datasets)
+// has its own block of S_NSLOTS scalars.
+
+// Eq. (loglikelihood) per set: l = -quad/2 - log|F|/2 - n/2 log(2 pi)
+__global__ void loglik_kernel(double* sc, const int64_t* __restrict__ set_off, int nsets) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nsets) return;
+  double* c = sc + (int64_t)i * S_NSLOTS;
+  double n = (double)(set_off[i + 1] - set_off[i]);
+  c[S_LOGLIK] = -0.5 * c[S_QUAD] - 0.5 * c[S_LOGDET] - 0.5 * n * log(2.0 * 3.141592653589793);
 }
 
-// Eq. (gradient) with Sigma = s2 Sigma_s2 + nug I:
+// Eq. (gradient) per set, with Sigma = s2 Sigma_s2 + nug I:
 //   g_l   = (a^T F_l a - Tr_l)/2
 //   g_s2  = ((a^T F a - nug a^T a) - (n - nug Tr(F^-1)))/(2 s2)
 //   g_nug = (a^T a - Tr(F^-1))/2
-__global__ void score_kernel(double* sc, int64_t n, double s2, double nug) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double ql = sc[S_QL], qs = (sc[S_QF] - nug * sc[S_AA]) / s2, qn = sc[S_AA];
-  double tl = sc[S_TL], ts = ((double)n - nug * sc[S_TNUG]) / s2, tn = sc[S_TNUG];
-  sc[S_T0] = ql; sc[S_T1] = qs; sc[S_T2] = qn;
-  sc[S_T3] = tl; sc[S_T4] = ts; sc[S_T5] = tn;
-  sc[S_G0] = 0.5 * ql - 0.5 * tl;
-  sc[S_G1] = 0.5 * qs - 0.5 * ts;
-  sc[S_G2] = 0.5 * qn - 0.5 * tn;
+__global__ void score_kernel(double* sc, const int64_t* __restrict__ set_off, int nsets, double s2, double nug) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nsets) return;
+  double* c = sc + (int64_t)i * S_NSLOTS;
+  double n = (double)(set_off[i + 1] - set_off[i]);
+  double ql = c[S_QL], qs = (c[S_QF] - nug * c[S_AA]) / s2, qn = c[S_AA];
+  double tl = c[S_TL], ts = (n - nug * c[S_TNUG]) / s2, tn = c[S_TNUG];
+  c[S_T0] = ql; c[S_T1] = qs; c[S_T2] = qn;
+  c[S_T3] = tl; c[S_T4] = ts; c[S_T5] = tn;
+  c[S_G0] = 0.5 * ql - 0.5 * tl;
+  c[S_G1] = 0.5 * qs - 0.5 * ts;
+  c[S_G2] = 0.5 * qn - 0.5 * tn;
 }
 
-// log|F| = sum of the per-box parts (fixed order)
-__global__ void sum_logdet_kernel(const double* __restrict__ parts, int n, double* __restrict__ out) {
+// log|F| of every set = sum of its boxes' parts (fixed order; one block per
+// set, boxes of other sets skipped)
+__global__ void sum_logdet_kernel(const double* __restrict__ parts, const int* __restrict__ box_set, int n,
+                                  double* __restrict__ out, int64_t stride) {
   __shared__ double red[256];
+  const int set = blockIdx.x;
   double s = 0.0;
-  for (int i = threadIdx.x; i < n; i += 256) s += parts[i];
+  for (int i = threadIdx.x; i < n; i += 256)
+    if (box_set[i] == set) s += parts[i];
   red[threadIdx.x] = s;
   __syncthreads();
   for (int o = 128; o > 0; o >>= 1) {
     if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) *out = red[0];
+  if (threadIdx.x == 0) out[(int64_t)set * stride] = red[0];
 }
 
 // rsf_solve with its work buffers in the library's fixed scratch (noalloc.cu).
@@ -328,17 +341,94 @@ rsf_status rsf_build_on_tree(rsf_tree tree, const rsf_kernel* kernel, const doub
   API_END
 }
 
+// Per-set log-determinants (host), synchronising the stream.
+static std::vector<double> logdet_sets(rsf_handle_s* h) {
+  const TreeData& T = h->tree_raw->t;
+  DBuf d;
+  d.alloc(sizeof(double) * T.nsets, h->stream);
+  LAUNCH(sum_logdet_kernel, T.nsets, 256, 0, h->stream, h->logdet_parts.as<double>(), T.box_set_d.as<int>(),
+         (int)h->nboxes_total, d.as<double>(), (int64_t)1);
+  std::vector<double> v(T.nsets);
+  d2h(v.data(), d.as<double>(), T.nsets, h->stream);
+  check_status(h);
+  return v;
+}
+
+// Log-likelihood scalars of every set into sc (device, nsets x S_NSLOTS):
+// alpha = F^-1 z (tree order, also returned in the caller's order when
+// alpha_out is set), quad = z^T alpha, log|F|, the log-likelihood.
+static void loglik_sets(rsf_handle_s* F, const double* z, double* alpha_out, DBuf& sc) {
+  cudaStream_t s = F->stream;
+  const TreeData& T = F->tree_raw->t;
+  const int64_t n = T.n;
+  const int* perm = T.perm.as<int>();
+  DBuf zt, at;
+  zt.alloc(sizeof(double) * n, s);
+  at.alloc(sizeof(double) * n, s);
+  sc.alloc(sizeof(double) * S_NSLOTS * T.nsets, s);
+  sc.zero();
+  LAUNCH(to_tree_kernel, cdiv(n, 256), 256, 0, s, z, n, 1, perm, n, zt.as<double>());
+  solve_rows(F, RSF_OP_INV, zt.as<double>(), at.as<double>(), 1);
+  for (int i = 0; i < T.nsets; i++) {
+    const int64_t r0 = T.set_off[i], cnt = T.set_off[i + 1] - r0;
+    dot_into(zt.as<double>() + r0, at.as<double>() + r0, cnt, sc.as<double>() + (int64_t)i * S_NSLOTS + S_QUAD, s);
+  }
+  LAUNCH(sum_logdet_kernel, T.nsets, 256, 0, s, F->logdet_parts.as<double>(), T.box_set_d.as<int>(),
+         (int)F->nboxes_total, sc.as<double>() + S_LOGDET, (int64_t)S_NSLOTS);
+  LAUNCH(loglik_kernel, cdiv(T.nsets, 32), 32, 0, s, sc.as<double>(), T.set_off_d.as<int64_t>(), T.nsets);
+  if (alpha_out) LAUNCH(from_tree_kernel, cdiv(n, 256), 256, 0, s, at.as<double>(), n, 1, perm, alpha_out, n);
+}
+
+// Score scalars of every set into sc (filled by loglik_sets or zeroed):
+// a^T a, a^T F_l a, a^T F a per set, the peeled traces per set, the score.
+static void score_sets(rsf_handle_s* F, const double* alpha, double tol_fact, double tol_peel, const rsf_opts& o,
+                       DBuf& sc) {
+  cudaStream_t s = F->stream;
+  const TreeData& T = F->tree_raw->t;
+  const int64_t n = T.n;
+  const int* perm = T.perm.as<int>();
+  rsf_kernel k{F->kp.family, F->kp.alpha};
+  double theta[3] = {F->kp.l, F->kp.s2, F->kp.nug};
+  std::unique_ptr<rsf_handle_s> Fl(make_handle(F->tree, &k, theta, RSF_D_L, tol_fact, o));
+  DBuf at, fl, ff;
+  at.alloc(sizeof(double) * n, s);
+  fl.alloc(sizeof(double) * n, s);
+  ff.alloc(sizeof(double) * n, s);
+  LAUNCH(to_tree_kernel, cdiv(n, 256), 256, 0, s, alpha, n, 1, perm, n, at.as<double>());
+  solve_rows(Fl.get(), RSF_OP_APPLY, at.as<double>(), fl.as<double>(), 1);
+  solve_rows(F, RSF_OP_APPLY, at.as<double>(), ff.as<double>(), 1);
+  for (int i = 0; i < T.nsets; i++) {
+    const int64_t r0 = T.set_off[i], cnt = T.set_off[i + 1] - r0;
+    double* c = sc.as<double>() + (int64_t)i * S_NSLOTS;
+    dot_into(at.as<double>() + r0, at.as<double>() + r0, cnt, c + S_AA, s);
+    dot_into(at.as<double>() + r0, fl.as<double>() + r0, cnt, c + S_QL, s);
+    dot_into(at.as<double>() + r0, ff.as<double>() + r0, cnt, c + S_QF, s);
+  }
+  // Tr(F^-1) and Tr(G_l) of every set, peeled together on shared test matrices
+  double* const dtr[2] = {sc.as<double>() + S_TNUG, sc.as<double>() + S_TL};
+  peel_traces(F, Fl.get(), true, tol_peel, o, dtr, (int64_t)S_NSLOTS, nullptr);
+  LAUNCH(score_kernel, cdiv(T.nsets, 32), 32, 0, s, sc.as<double>(), T.set_off_d.as<int64_t>(), T.nsets,
+         F->kp.s2, F->kp.nug);
+  check_status(Fl.get());
+}
+
 rsf_status rsf_logdet(rsf_handle h, double* out) {
   API_BEGIN
   RSF_CHECK(h && out, RSF_EINVAL, "handle and out must not be NULL");
   RSF_CHECK(h->spd, RSF_EINVAL, "log-determinant of a derivative factorization is not defined here");
-  DBuf d;
-  d.alloc(sizeof(double), h->stream);
-  LAUNCH(sum_logdet_kernel, 1, 256, 0, h->stream, h->logdet_parts.as<double>(), (int)h->nboxes_total, d.as<double>());
-  double v = 0;
-  d2h(&v, d.as<double>(), 1, h->stream);
-  check_status(h);
-  *out = v;
+  std::vector<double> v = logdet_sets(h);
+  double t = 0.0;
+  for (double x : v) t += x;
+  *out = t;
+  API_END
+}
+
+rsf_status rsf_logdet_sets(rsf_handle h, double* out) {
+  API_BEGIN
+  RSF_CHECK(h && out, RSF_EINVAL, "handle and out must not be NULL");
+  RSF_CHECK(h->spd, RSF_EINVAL, "log-determinant of a derivative factorization is not defined here");
+  std::vector<double> v = logdet_sets(h);
+  for (size_t i = 0; i < v.size(); i++) out[i] = v[i];
   API_END
 }
 
@@ -379,11 +469,14 @@ rsf_status rsf_peel_trace(rsf_handle F, rsf_handle Fk, double tol_peel, const rs
   RSF_CHECK(tol_peel > 0.0 && tol_peel < 1.0, RSF_EINVAL, "tol_peel must be in (0, 1)");
   rsf_opts o = resolve_opts(opts);
   double* const dnone[2] = {nullptr, nullptr};
-  double t[2] = {0.0, 0.0};
-  peel_traces(F, Fk, false, tol_peel, o, dnone, t);
+  const int nsets = F->tree_raw->t.nsets;
+  std::vector<double> t(2 * nsets, 0.0);
+  peel_traces(F, Fk, false, tol_peel, o, dnone, 0, t.data());
   check_status(F);
   if (Fk) check_status(Fk);
-  *trace = Fk ? t[1] : t[0];
+  double tot = 0.0;
+  for (int i = 0; i < nsets; i++) tot += t[(Fk ? 1 : 0) * nsets + i];
+  *trace = tot;
   API_END
 }
 
@@ -391,26 +484,19 @@ rsf_status gp_loglik(rsf_handle F, const double* z, double* alpha_out, double* l
   API_BEGIN
   RSF_CHECK(F && z && loglik, RSF_EINVAL, "F, z and loglik must not be NULL");
   RSF_CHECK(F->spd, RSF_EINVAL, "F must factor Sigma");
-  cudaStream_t s = F->stream;
-  const int64_t n = F->tree_raw->t.n;
-  const int* perm = F->tree_raw->t.perm.as<int>();
-  DBuf zt, at, sc;
-  zt.alloc(sizeof(double) * n, s);
-  at.alloc(sizeof(double) * n, s);
-  sc.alloc(sizeof(double) * S_NSLOTS, s);
-  sc.zero();
-  LAUNCH(to_tree_kernel, cdiv(n, 256), 256, 0, s, z, n, 1, perm, n, zt.as<double>());
-  solve_rows(F, RSF_OP_INV, zt.as<double>(), at.as<double>(), 1);
-  dot_into(zt.as<double>(), at.as<double>(), n, sc.as<double>() + S_QUAD, s);
-  LAUNCH(sum_logdet_kernel, 1, 256, 0, s, F->logdet_parts.as<double>(), (int)F->nboxes_total,
-         sc.as<double>() + S_LOGDET);
-  LAUNCH(loglik_kernel, 1, 32, 0, s, sc.as<double>(), n);
-  if (alpha_out) LAUNCH(from_tree_kernel, cdiv(n, 256), 256, 0, s, at.as<double>(), n, 1, perm, alpha_out, n);
-  double h[S_NSLOTS];
-  d2h(h, sc.as<double>(), S_NSLOTS, s);
+  const int nsets = F->tree_raw->t.nsets;
+  DBuf sc;
+  loglik_sets(F, z, alpha_out, sc);
+  std::vector<double> h((size_t)S_NSLOTS * nsets);
+  d2h(h.data(), sc.as<double>(), h.size(), F->stream);
   check_status(F);
-  *loglik = h[S_LOGLIK];
-  if (quad) *quad = h[S_QUAD];
+  double ll = 0.0, q = 0.0;
+  for (int i = 0; i < nsets; i++) {
+    ll += h[(size_t)i * S_NSLOTS + S_LOGLIK];
+    q += h[(size_t)i * S_NSLOTS + S_QUAD];
+  }
+  *loglik = ll;
+  if (quad) *quad = q;
   API_END
 }
 
@@ -420,37 +506,49 @@ rsf_status gp_score(rsf_handle F, const double* alpha, double tol_fact, double t
   RSF_CHECK(F && alpha && score, RSF_EINVAL, "F, alpha and score must not be NULL");
   RSF_CHECK(F->spd, RSF_EINVAL, "F must factor Sigma");
   RSF_CHECK(tol_peel > 0.0 && tol_peel < 1.0, RSF_EINVAL, "tol_peel must be in (0, 1)");
-  cudaStream_t s = F->stream;
-  const int64_t n = F->tree_raw->t.n;
-  const int* perm = F->tree_raw->t.perm.as<int>();
   rsf_opts o = resolve_opts(opts);
-  rsf_kernel k{F->kp.family, F->kp.alpha};
-  double theta[3] = {F->kp.l, F->kp.s2, F->kp.nug};
-  std::unique_ptr<rsf_handle_s> Fl(make_handle(F->tree, &k, theta, RSF_D_L, tol_fact, o));
-  DBuf at, ft, sc;
-  at.alloc(sizeof(double) * n, s);
-  ft.alloc(sizeof(double) * n, s);
-  sc.alloc(sizeof(double) * S_NSLOTS, s);
+  const int nsets = F->tree_raw->t.nsets;
+  DBuf sc;
+  sc.alloc(sizeof(double) * S_NSLOTS * nsets, F->stream);
   sc.zero();
-  LAUNCH(to_tree_kernel, cdiv(n, 256), 256, 0, s, alpha, n, 1, perm, n, at.as<double>());
-  dot_into(at.as<double>(), at.as<double>(), n, sc.as<double>() + S_AA, s);
-  solve_rows(Fl.get(), RSF_OP_APPLY, at.as<double>(), ft.as<double>(), 1);
-  dot_into(at.as<double>(), ft.as<double>(), n, sc.as<double>() + S_QL, s);
-  solve_rows(F, RSF_OP_APPLY, at.as<double>(), ft.as<double>(), 1);
-  dot_into(at.as<double>(), ft.as<double>(), n, sc.as<double>() + S_QF, s);
-  // Tr(F^-1) and Tr(G_l) peeled together on shared test matrices
-  double* const dtr[2] = {sc.as<double>() + S_TNUG, sc.as<double>() + S_TL};
-  double htr[2];
-  peel_traces(F, Fl.get(), true, tol_peel, o, dtr, htr);
-  LAUNCH(score_kernel, 1, 32, 0, s, sc.as<double>(), n, F->kp.s2, F->kp.nug);
-  double h[S_NSLOTS];
-  d2h(h, sc.as<double>(), S_NSLOTS, s);
+  score_sets(F, alpha, tol_fact, tol_peel, o, sc);
+  std::vector<double> h((size_t)S_NSLOTS * nsets);
+  d2h(h.data(), sc.as<double>(), h.size(), F->stream);
   check_status(F);
-  check_status(Fl.get());
-  for (int i = 0; i < 3; i++) score[i] = h[S_G0 + i];
+  for (int i = 0; i < 3; i++) {
+    score[i] = 0.0;
+    for (int j = 0; j < nsets; j++) score[i] += h[(size_t)j * S_NSLOTS + S_G0 + i];
+  }
   if (terms)
-    for (int i = 0; i < 6; i++) terms[i] = h[S_T0 + i];
+    for (int i = 0; i < 6; i++) {
+      terms[i] = 0.0;
+      for (int j = 0; j < nsets; j++) terms[i] += h[(size_t)j * S_NSLOTS + S_T0 + i];
+    }
   API_END
+}
+
+// Algorithm 1 on a forest: per-set log-likelihoods and (score != NULL) scores.
+static void loglik_and_score_forest(std::shared_ptr<rsf_tree_s> t, const double* z, const rsf_kernel* kernel,
+                                    const double* theta, double tol_fact, double tol_peel, const rsf_opts& o,
+                                    double* loglik, double* score, double* terms) {
+  const TreeData& T = t->t;
+  cudaStream_t s = T.stream;
+  std::unique_ptr<rsf_handle_s> F(make_handle(t, kernel, theta, RSF_SIGMA, tol_fact, o));
+  DBuf alpha, sc;
+  alpha.alloc(sizeof(double) * T.n, s);
+  loglik_sets(F.get(), z, alpha.as<double>(), sc);
+  if (score) score_sets(F.get(), alpha.as<double>(), tol_fact, tol_peel, o, sc);
+  std::vector<double> h((size_t)S_NSLOTS * T.nsets);
+  d2h(h.data(), sc.as<double>(), h.size(), s);
+  check_status(F.get());
+  for (int i = 0; i < T.nsets; i++) {
+    const double* c = h.data() + (size_t)i * S_NSLOTS;
+    loglik[i] = c[S_LOGLIK];
+    if (score)
+      for (int j = 0; j < 3; j++) score[3 * i + j] = c[S_G0 + j];
+    if (score && terms)
+      for (int j = 0; j < 6; j++) terms[6 * i + j] = c[S_T0 + j];
+  }
 }
 
 rsf_status gp_loglik_and_score(const double* points, const double* z, int64_t n, const rsf_kernel* kernel,
@@ -458,25 +556,41 @@ rsf_status gp_loglik_and_score(const double* points, const double* z, int64_t n,
                                void* stream, double* loglik, double* score, double* terms) {
   API_BEGIN
   RSF_CHECK(points && z && loglik, RSF_EINVAL, "points, z and loglik must not be NULL");
+  RSF_CHECK(tol_peel > 0.0 && tol_peel < 1.0, RSF_EINVAL, "tol_peel must be in (0, 1)");
   rsf_opts o = resolve_opts(opts);
   check_kernel(kernel, theta);
-  cudaStream_t s = (cudaStream_t)stream;
-  auto t = build_tree(points, n, o, s);
-  std::unique_ptr<rsf_handle_s> F(make_handle(t, kernel, theta, RSF_SIGMA, tol_fact, o));
-  DBuf alpha;
-  alpha.alloc(sizeof(double) * n, s);
-  double ll = 0;
-  rsf_status st = gp_loglik(F.get(), z, alpha.as<double>(), &ll, nullptr);
-  if (st != RSF_OK) fail(st, g_err);
-  if (score) {
-    double g[3], tm[6];
-    st = gp_score(F.get(), alpha.as<double>(), tol_fact, tol_peel, &o, g, tm);
-    if (st != RSF_OK) fail(st, g_err);
-    for (int i = 0; i < 3; i++) score[i] = g[i];
-    if (terms)
-      for (int i = 0; i < 6; i++) terms[i] = tm[i];
-  }
-  *loglik = ll;
+  auto t = build_tree(points, n, o, (cudaStream_t)stream);
+  loglik_and_score_forest(t, z, kernel, theta, tol_fact, tol_peel, o, loglik, score, terms);
+  API_END
+}
+
+static std::vector<int64_t> set_offsets(int nsets, const int64_t* offsets) {
+  RSF_CHECK(nsets >= 1 && offsets != nullptr, RSF_EINVAL, "need nsets >= 1 and an offsets array");
+  return std::vector<int64_t>(offsets, offsets + nsets + 1);
+}
+
+rsf_status rsf_build_batched(int nsets, const int64_t* offsets, const double* points, const rsf_kernel* kernel,
+                             const double* theta, int which, double tol, const rsf_opts* opts, void* stream,
+                             rsf_handle* out) {
+  API_BEGIN
+  RSF_CHECK(points && out, RSF_EINVAL, "points and out must not be NULL");
+  rsf_opts o = resolve_opts(opts);
+  auto t = build_forest(points, set_offsets(nsets, offsets), o, (cudaStream_t)stream);
+  *out = make_handle(t, kernel, theta, which, tol, o);
+  API_END
+}
+
+rsf_status gp_loglik_and_score_batched(int nsets, const int64_t* offsets, const double* points, const double* z,
+                                       const rsf_kernel* kernel, const double* theta, double tol_fact,
+                                       double tol_peel, const rsf_opts* opts, void* stream, double* loglik,
+                                       double* score, double* terms) {
+  API_BEGIN
+  RSF_CHECK(points && z && loglik, RSF_EINVAL, "points, z and loglik must not be NULL");
+  RSF_CHECK(tol_peel > 0.0 && tol_peel < 1.0, RSF_EINVAL, "tol_peel must be in (0, 1)");
+  rsf_opts o = resolve_opts(opts);
+  check_kernel(kernel, theta);
+  auto t = build_forest(points, set_offsets(nsets, offsets), o, (cudaStream_t)stream);
+  loglik_and_score_forest(t, z, kernel, theta, tol_fact, tol_peel, o, loglik, score, terms);
   API_END
 }
 
@@ -494,6 +608,7 @@ rsf_status rsf_get_info(rsf_handle h, rsf_info_t* info) {
   info->factor_entries = h->factor_entries;
   info->flops = h->flops;
   info->kernel_evals = h->kevals;
+  info->nsets = h->tree_raw->t.nsets;
   API_END
 }
 

@@ -329,10 +329,13 @@ void factorize(rsf_handle_s* h) {
   upload(dproxy, ptab, s);
   DBuf rowmap;
   rowmap.alloc(sizeof(int) * n, s);
-  // per-level grid hash for neighbour lookup: key (ix, iy) -> box
+  // per-level grid hash for neighbour lookup: key (set, ix, iy) -> box; boxes
+  // of different point sets are never neighbours
+  auto cell_key = [](int set, int gx, int gy) {
+    return ((uint64_t)(uint32_t)set << 48) | ((uint64_t)(uint32_t)gx << 24) | (uint64_t)(uint32_t)gy;
+  };
   std::vector<std::unordered_map<uint64_t, int>> grid(L + 1);
-  for (int b = 0; b < nboxes; b++)
-    grid[T.level[b]][((uint64_t)(uint32_t)T.ix[b] << 32) | (uint32_t)T.iy[b]] = b;
+  for (int b = 0; b < nboxes; b++) grid[T.level[b]][cell_key(T.box_set[b], T.ix[b], T.iy[b])] = b;
 
   std::vector<int> box2idx(nboxes, -1);   // index of a box within its level
   DBuf prevAII;                           // A_II pool of the level below (children's X_SS)
@@ -432,7 +435,8 @@ void factorize(rsf_handle_s* h) {
             int gx = T.ix[b] + dx, gy = T.iy[b] + dy;
             if (gx < 0 || gy < 0 || gx >= (1 << lev) || gy >= (1 << lev)) continue;
             // distance from the centre to the cell square
-            double x0 = T.lo[0] + gx * w, y0 = T.lo[1] + gy * w;
+            const int bs = T.box_set[b];
+            double x0 = T.set_lo[2 * bs] + gx * w, y0 = T.set_lo[2 * bs + 1] + gy * w;
             double ddx = std::max(0.0, std::max(x0 - T.cx[b], T.cx[b] - (x0 + w)));
             double ddy = std::max(0.0, std::max(y0 - T.cy[b], T.cy[b] - (y0 + w)));
             if (ddx * ddx + ddy * ddy >= R * R) continue;
@@ -440,7 +444,7 @@ void factorize(rsf_handle_s* h) {
             int found = -1;
             for (int lv = lev; lv >= 0; lv--) {
               int sh = lev - lv;
-              auto it = grid[lv].find(((uint64_t)(uint32_t)(gx >> sh) << 32) | (uint32_t)(gy >> sh));
+              auto it = grid[lv].find(cell_key(bs, gx >> sh, gy >> sh));
               if (it != grid[lv].end()) {
                 found = it->second;
                 break;

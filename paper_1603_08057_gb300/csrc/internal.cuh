@@ -87,6 +87,14 @@ struct TreeData {
   std::vector<std::vector<int>> by_level;
   std::vector<int> leafpos;      // host: per tree position, index in its leaf (built lazily)
   int max_leaf = 0;
+  // independent point sets (batched datasets): set i holds tree positions
+  // [set_off[i], set_off[i+1]) and has its own root square
+  int nsets = 1;
+  std::vector<int64_t> set_off;
+  std::vector<double> set_lo, set_side;   // 2 and 1 per set
+  std::vector<int> box_set;               // set of every box
+  DBuf box_set_d;                         // device copies of box_set and set_off
+  DBuf set_off_d;
   cudaStream_t stream = nullptr;
   DBuf xt;     // n x 2 tree-order coordinates
   DBuf perm;   // tree position -> original index (int)
@@ -145,6 +153,10 @@ struct rsf_handle_s {
 };
 
 namespace rsf {
+// A forest over independent point sets: set_off (host, nsets + 1 prefix
+// offsets into points) -- one set gives the plain quadtree.
+std::shared_ptr<rsf_tree_s> build_forest(const double* points, const std::vector<int64_t>& set_off,
+                                         const rsf_opts& o, cudaStream_t s);
 std::shared_ptr<rsf_tree_s> build_tree(const double* points, int64_t n, const rsf_opts& o,
                                        cudaStream_t s);
 void factorize(rsf_handle_s* h);
@@ -156,9 +168,10 @@ void solve_rows(rsf_handle_s* h, int op, const double* in, double* out, int q, i
 void convert_df64(double* p, int64_t n, int to, cudaStream_t s);
 // Peeled traces (Sec. 3) of G_0 = F^-1 (when want0 or Fk is null) and of
 // G_1 = (F^-1 Fk + Fk F^-1)/2 (when Fk is given), sharing every test matrix.
-// Operator i's trace goes to d_out[i] (a device scalar, may be null) and h_out[i].
+// Operator i's trace over point set j goes to d_out[i][j * d_stride] (device,
+// d_out[i] may be null) and to h_sets[i * nsets + j] (host, may be null).
 void peel_traces(rsf_handle_s* F, rsf_handle_s* Fk, bool want0, double tol, const rsf_opts& o,
-                 double* const d_out[2], double h_out[2]);
+                 double* const d_out[2], int64_t d_stride, double* h_sets);
 // device reductions
 double dot_device(const double* a, const double* b, int64_t n, cudaStream_t s);
 // a . b into a device scalar (stream ordered, no synchronisation)

@@ -395,7 +395,7 @@ void apply_level_sparse(const PLevel& P, const double* X, double* Y, int qc, con
 // multi-RHS applications G_1 W needs -- is G_0 W, so peeling both costs the
 // applications of G_1 alone.
 void peel_traces(rsf_handle_s* F, rsf_handle_s* Fk, bool want0, double tol, const rsf_opts& o,
-                 double* const d_out[2], double h_out[2]) {
+                 double* const d_out[2], int64_t d_stride, double* h_sets) {
   cudaStream_t s = F->stream;
   TreeData& T = F->tree_raw->t;
   const int64_t n = T.n;
@@ -1016,17 +1016,23 @@ void peel_traces(rsf_handle_s* F, rsf_handle_s* Fk, bool want0, double tol, cons
   for (int oi : ops)
     for (int m = 1; m <= L; m++) apply_level(levels[oi][m], E.as<double>(), H[oi].as<double>(), nl, tmpP, s, df);
   prof_end(tk, s, PROF_PEEL_SUB, 0, 0);
-  int nb = (int)std::min<int64_t>(1024, std::max<int64_t>(1, cdiv(n64, 256)));
+  // the trace of every point set: its rows are contiguous in tree order
+  const int nsets = T.nsets;
   DBuf part, res;
-  part.alloc(sizeof(double) * nb, s);
-  res.alloc(sizeof(double) * 2, s);
+  part.alloc(sizeof(double) * 1024, s);
+  res.alloc(sizeof(double) * 2 * nsets, s);
   for (int oi : ops) {
-    LAUNCH(diag_trace_kernel, nb, 256, 0, s, H[oi].as<double>(), dlp.as<int>(), n64, nl, part.as<double>(), df);
-    double* outp = d_out[oi] ? d_out[oi] : res.as<double>() + oi;
-    LAUNCH(sum_parts_kernel, 1, 256, 0, s, part.as<double>(), nb, outp);
-    d2h(&h_out[oi], outp, 1, s);
-    sync(s);
+    for (int si = 0; si < nsets; si++) {
+      const int64_t r0 = T.set_off[si], cnt = T.set_off[si + 1] - r0;
+      const int nb = (int)std::min<int64_t>(1024, std::max<int64_t>(1, cdiv(cnt, 256)));
+      LAUNCH(diag_trace_kernel, nb, 256, 0, s, H[oi].as<double>() + r0 * nl, dlp.as<int>() + r0, cnt, nl,
+             part.as<double>(), df);
+      double* outp = d_out[oi] ? d_out[oi] + si * d_stride : res.as<double>() + oi * nsets + si;
+      LAUNCH(sum_parts_kernel, 1, 256, 0, s, part.as<double>(), nb, outp);
+      if (h_sets) d2h(&h_sets[oi * nsets + si], outp, 1, s);
+    }
   }
+  sync(s);
 }
 
 }  // namespace rsf
