@@ -114,9 +114,9 @@ __global__ void __launch_bounds__(GT, GEMM_MIN_BLOCKS) gemm_kernel(const GemmDes
   const int64_t sa = d.abase == 0 ? bases.sc[0] : d.abase == 1 ? bases.sc[1] : d.abase == 2 ? bases.sc[2] : bases.sc[3];
   const int64_t sb = d.bbase == 0 ? bases.sc[0] : d.bbase == 1 ? bases.sc[1] : d.bbase == 2 ? bases.sc[2] : bases.sc[3];
   const int64_t scc = d.cbase == 0 ? bases.sc[0] : d.cbase == 1 ? bases.sc[1] : d.cbase == 2 ? bases.sc[2] : bases.sc[3];
-  const double* __restrict__ A = pa + d.a * sa;
+  const double* __restrict__ A = pa + d.a * sa + d.m0;
   const double* __restrict__ B = pb + d.b * sb;
-  double* __restrict__ C = pc + d.c * scc;
+  double* __restrict__ C = pc + d.c * scc + d.m0;
   int k0 = 0, k1 = K;
   if (d.triB == 1) k0 = min(n0, K);
   if (d.triB == 2) k1 = min(K, n0 + BN);

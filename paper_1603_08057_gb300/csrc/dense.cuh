@@ -28,6 +28,9 @@ struct GemmDesc {
                    //    of op(B) (tb = 1) kidx[.] - nb0, C column kidx[.]
   int64_t nofs;
   int64_t nb0;
+  int m0;          // first row of A and C (ta = 0): the M range [m0, m0 + M)
+                   // of a wider column-major operand, e.g. one column block
+                   // of a row-major multi-RHS block
 };
 
 struct GemmBases {

@@ -765,10 +765,13 @@ void factorize(rsf_handle_s* h) {
       std::vector<GemmDesc> rsT, srE, rsE, srT;
       std::vector<GemmDesc> mid[5];
       std::vector<int64_t> rr;
+      Lv.boxRSE.clear();
+      for (int v = 0; v < 5; v++) Lv.boxMid[v].clear();
       for (int i = 0; i < nb; i++) {
         int k = Lv.k[i], r = Lv.r[i];
         int64_t S0 = Lv.row0[i], R0 = Lv.row0[i] + k;
         if (k > 0 && r > 0) {
+          Lv.boxRSE.push_back(i);
           // row block offsets are rows * ld with ld = q: stored as rows, scaled at launch
           rsT.push_back(gd(-1, r, k, 0, S0, -1, 0, 2, Lv.toff[i], k, 0, 0, R0, -1, 1.0, 1.0));
           srE.push_back(gd(-1, k, r, 0, R0, -1, 0, 2, Lv.eoff[i], k, 1, 0, S0, -1, 1.0, 1.0));
@@ -776,6 +779,8 @@ void factorize(rsf_handle_s* h) {
           srT.push_back(gd(-1, k, r, 0, R0, -1, 0, 2, Lv.toff[i], k, 1, 0, S0, -1, 1.0, 1.0));
         }
         if (r > 0) {
+          for (int v = 0; v < 5; v++)
+            if ((v < 4) == h->spd) Lv.boxMid[v].push_back(i);
           if (h->spd) {
             mid[0].push_back(gd(-1, r, r, 0, R0, -1, 0, 2, Lv.dioff[i], r, 1, 1, R0, -1, 1.0, 0.0, 2));
             mid[1].push_back(gd(-1, r, r, 0, R0, -1, 0, 2, Lv.dioff[i], r, 0, 1, R0, -1, 1.0, 0.0, 1));
@@ -793,6 +798,11 @@ void factorize(rsf_handle_s* h) {
       Lv.gRS_E.build(rsE, s);
       Lv.gSR_Tt.build(srT, s);
       for (int v = 0; v < 5; v++) Lv.gMid[v].build(mid[v], s);
+      Lv.hRS_T = std::move(rsT);
+      Lv.hSR_Et = std::move(srE);
+      Lv.hRS_E = std::move(rsE);
+      Lv.hSR_Tt = std::move(srT);
+      for (int v = 0; v < 5; v++) Lv.hMid[v] = std::move(mid[v]);
       Lv.nrr = (int)rr.size() / 2;
       upload(Lv.rr, rr, s);
     }

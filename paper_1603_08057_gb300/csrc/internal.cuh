@@ -123,6 +123,10 @@ struct LevelData {
   GemmBatch gSR_Tt;  // X_S += a * T X_R
   // middle (block diagonal) products on R rows: out = in * op(B)
   GemmBatch gMid[5];  // 0: Dinv^T, 1: Dinv, 2: D, 3: D^T, 4: D (full, indefinite)
+  // host copies of the descriptors above and the level box index of each
+  // (for solves whose right-hand sides are column-block sparse)
+  std::vector<GemmDesc> hRS_T, hSR_Et, hRS_E, hSR_Tt, hMid[5];
+  std::vector<int> boxRSE, boxMid[5];
 };
 
 }  // namespace rsf
@@ -163,7 +167,17 @@ void factorize(rsf_handle_s* h);
 void check_status(rsf_handle_s* h);
 // Internal solve on tree-order, row-major (n x q) buffers: out = op(F) in.
 // io_df: in/out hold df64 pairs (else doubles, converted when h->df).
-void solve_rows(rsf_handle_s* h, int op, const double* in, double* out, int q, int io_df = 0);
+// Column-block sparse right-hand sides: the n x q input holds blocks of qc
+// columns, and on every level l >= lev0 the rows of level box i are nonzero
+// only in block slot[l][i] (-1: nowhere).  The upward sweep and the middle
+// factor, which keep that pattern, then run on one block per box.
+struct SparseRHS {
+  int lev0 = 0;
+  int qc = 0;
+  std::vector<std::vector<int>> slot;   // per level, per level box
+};
+void solve_rows(rsf_handle_s* h, int op, const double* in, double* out, int q, int io_df = 0,
+                const SparseRHS* sp = nullptr);
 // In-place conversion of n doubles to df64 pairs (to = 1) or back (to = 0).
 void convert_df64(double* p, int64_t n, int to, cudaStream_t s);
 // Peeled traces (Sec. 3) of G_0 = F^-1 (when want0 or Fk is null) and of

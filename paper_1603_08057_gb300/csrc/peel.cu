@@ -417,7 +417,9 @@ void peel_traces(rsf_handle_s* F, rsf_handle_s* Fk, bool want0, double tol, cons
   // (F = F^1/2 F^T/2, so Tr(F^-1/2 F_k F^-T/2) = Tr(F^-T/2 F^-1/2 F_k)).
   const bool sqrt_form = o.trace_form == RSF_TRACE_SQRT;
   DBuf ga, gb2, gw;
-  auto applyG = [&](const double* in, double* const out[2], int q) {
+  // sp (may be null): the column-block structure of a test matrix, whose
+  // first solves (F^-1 W, F_k W) then skip the zero blocks
+  auto applyG = [&](const double* in, double* const out[2], int q, const SparseRHS* sp) {
     const int64_t cnt = n64 * q;
     const int64_t bytes = sizeof(double) * cnt;
     // doubles in and out when F is df64 but F_k is fp64
@@ -441,14 +443,14 @@ void peel_traces(rsf_handle_s* F, rsf_handle_s* Fk, bool want0, double tol, cons
       }
     } else {
       if (!Fk) {
-        solve_rows(F, RSF_OP_INV, x, out[0], q, io);
+        solve_rows(F, RSF_OP_INV, x, out[0], q, io, sp);
         return;
       }
       if ((int64_t)gb2.bytes < bytes) gb2.alloc(bytes, s);
       double* x3 = want0 ? out[0] : gb2.as<double>();
-      solve_rows(F, RSF_OP_INV, x, x3, q, io);                            // F^-1 W
+      solve_rows(F, RSF_OP_INV, x, x3, q, io, sp);                        // F^-1 W
       solve_rows(Fk, RSF_OP_APPLY, x3, out[1], q, io);                    // F_k F^-1 W
-      solve_rows(Fk, RSF_OP_APPLY, x, ga.as<double>(), q, io);
+      solve_rows(Fk, RSF_OP_APPLY, x, ga.as<double>(), q, io, sp);
       double* x2 = want0 ? gb2.as<double>() : x3;
       solve_rows(F, RSF_OP_INV, ga.as<double>(), x2, q, io);              // F^-1 F_k W
       LAUNCH(average_kernel, cdiv(cnt, 256), 256, 0, s, out[1], x2, cnt, io);
@@ -515,6 +517,20 @@ void peel_traces(rsf_handle_s* F, rsf_handle_s* Fk, bool want0, double tol, cons
     sbeg[4] = (int64_t)slotlist.size();
     DBuf dslotlist;
     upload(dslotlist, slotlist, s);
+    // column-block structure of this level's test matrices on every level
+    // >= lev: a box's rows are nonzero only in its level-lev ancestor's slot
+    SparseRHS sparse;
+    sparse.lev0 = lev;
+    sparse.slot.assign(F->levels.size(), {});
+    for (int l = lev; l < (int)F->levels.size(); l++) {
+      const std::vector<int>& bl = F->levels[l].box;
+      sparse.slot[l].assign(bl.size(), -1);
+      for (size_t i = 0; i < bl.size(); i++) {
+        int a = bl[i];
+        while (T.level[a] > lev) a = T.parent[a];
+        if (idx_of[a] >= 0) sparse.slot[l][i] = T.slot[a];
+      }
+    }
 
     // ordered pairs (a, t): box a with its t-th sibling
     struct OPair { int a, t; };
@@ -594,7 +610,8 @@ void peel_traces(rsf_handle_s* F, rsf_handle_s* Fk, bool want0, double tol, cons
                (unsigned long long)o.seed, Wn.as<double>(), df);
         int tk = prof_begin(s);
         double* const outs[2] = {Y[0].as<double>(), Y[1].as<double>()};
-        applyG(Wn.as<double>(), outs, 4 * qc);
+        sparse.qc = qc;
+        applyG(Wn.as<double>(), outs, 4 * qc, &sparse);
         prof_end(tk, s, PROF_PEEL_APPLY, 0, 0);
         tk = prof_begin(s);
         for (int oi : ops)
@@ -1010,7 +1027,7 @@ void peel_traces(rsf_handle_s* F, rsf_handle_s* Fk, bool want0, double tol, cons
   LAUNCH(unit_cols_kernel, cdiv(n64 * nl, 256), 256, 0, s, dlp.as<int>(), n64, nl, E.as<double>(), df);
   int tk = prof_begin(s);
   double* const hout[2] = {H[0].as<double>(), H[1].as<double>()};
-  applyG(E.as<double>(), hout, nl);
+  applyG(E.as<double>(), hout, nl, nullptr);
   prof_end(tk, s, PROF_PEEL_APPLY, 0, 0);
   tk = prof_begin(s);
   for (int oi : ops)

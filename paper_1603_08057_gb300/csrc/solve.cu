@@ -98,7 +98,23 @@ static void run_level_gemm(const GemmBatch& g, double* X, double* tmp, double* p
   g.run(b, s);
 }
 
-void solve_rows(rsf_handle_s* h, int op, const double* in, double* out, int q, int io_df) {
+// The descriptors of one level restricted to each box's nonzero column block.
+static void restrict_batch(const std::vector<GemmDesc>& d, const std::vector<int>& box, const std::vector<int>& slot,
+                           int qc, cudaStream_t s, GemmBatch& out) {
+  std::vector<GemmDesc> r;
+  r.reserve(d.size());
+  for (size_t j = 0; j < d.size(); j++) {
+    const int sl = slot[box[j]];
+    if (sl < 0) continue;
+    GemmDesc g = d[j];
+    g.M = qc;
+    g.m0 = sl * qc;
+    r.push_back(g);
+  }
+  out.build(r, s);
+}
+
+void solve_rows(rsf_handle_s* h, int op, const double* in, double* out, int q, int io_df, const SparseRHS* sp) {
   const int df = h->df ? 1 : 0;
   const int cvt = (df && !io_df) ? 1 : 0;
   RSF_CHECK(!io_df || df, RSF_EINVAL, "df64 input needs a mixed-precision factorization");
@@ -136,12 +152,28 @@ void solve_rows(rsf_handle_s* h, int op, const double* in, double* out, int q, i
     LAUNCH(gather_rows_kernel, cdiv(Lv.nrows, 8), 256, 0, s, Lv.src.as<int>(), Lv.nrows, q, child, in, Xl(l), cvt);
     if (l == 0) break;
     double* F = Lv.fpool.as<double>();
+    const bool sparse = sp && l >= sp->lev0;
+    GemmBatch r1, r2;
     if (up == 1) {
-      run_level_gemm(Lv.gRS_T, Xl(l), tmp.as<double>(), F, q, -1.0, s, df);
-      run_level_gemm(Lv.gSR_Et, Xl(l), tmp.as<double>(), F, q, -1.0, s, df);
+      const GemmBatch* g1 = &Lv.gRS_T;
+      const GemmBatch* g2 = &Lv.gSR_Et;
+      if (sparse) {
+        restrict_batch(Lv.hRS_T, Lv.boxRSE, sp->slot[l], sp->qc, s, r1);
+        restrict_batch(Lv.hSR_Et, Lv.boxRSE, sp->slot[l], sp->qc, s, r2);
+        g1 = &r1; g2 = &r2;
+      }
+      run_level_gemm(*g1, Xl(l), tmp.as<double>(), F, q, -1.0, s, df);
+      run_level_gemm(*g2, Xl(l), tmp.as<double>(), F, q, -1.0, s, df);
     } else if (up == 2) {
-      run_level_gemm(Lv.gSR_Tt, Xl(l), tmp.as<double>(), F, q, 1.0, s, df);
-      run_level_gemm(Lv.gRS_E, Xl(l), tmp.as<double>(), F, q, 1.0, s, df);
+      const GemmBatch* g1 = &Lv.gSR_Tt;
+      const GemmBatch* g2 = &Lv.gRS_E;
+      if (sparse) {
+        restrict_batch(Lv.hSR_Tt, Lv.boxRSE, sp->slot[l], sp->qc, s, r1);
+        restrict_batch(Lv.hRS_E, Lv.boxRSE, sp->slot[l], sp->qc, s, r2);
+        g1 = &r1; g2 = &r2;
+      }
+      run_level_gemm(*g1, Xl(l), tmp.as<double>(), F, q, 1.0, s, df);
+      run_level_gemm(*g2, Xl(l), tmp.as<double>(), F, q, 1.0, s, df);
     }
   }
   // block-diagonal middle factor on the R rows of every level
@@ -151,14 +183,23 @@ void solve_rows(rsf_handle_s* h, int op, const double* in, double* out, int q, i
     double* F = Lv.fpool.as<double>();
     double* x = Xl(l);
     double* t = tmp.as<double>();
+    const bool sparse = sp && l >= sp->lev0;
     auto prod = [&](int v, bool from_tmp) {
-      // out = in * op(B): descriptors read base 0 and write base 1
+      // out = in * op(B): descriptors read base 0 and write base 1; on a
+      // sparse level only each box's nonzero column block (the others stay
+      // zero in x)
       GemmBases b{};
       b.p[0] = from_tmp ? t : x; b.p[1] = from_tmp ? x : t; b.p[2] = F; b.p[3] = nullptr;
       b.sc[0] = q; b.sc[1] = q; b.sc[2] = 1; b.sc[3] = 1;
       b.M = q; b.ld = q; b.alpha_scale = 1.0;
       b.df = df;
-      Lv.gMid[v].run(b, s);
+      if (sparse) {
+        GemmBatch r;
+        restrict_batch(Lv.hMid[v], Lv.boxMid[v], sp->slot[l], sp->qc, s, r);
+        r.run(b, s);
+      } else {
+        Lv.gMid[v].run(b, s);
+      }
     };
     auto copy_to_tmp = [&]() {
       LAUNCH(copy_ranges_kernel, Lv.nrr, 256, 0, s, Lv.rr.as<int64_t>(), Lv.nrr, q, x, t);
