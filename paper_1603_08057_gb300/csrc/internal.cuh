@@ -171,13 +171,16 @@ void check_status(rsf_handle_s* h);
 // columns, and on every level l >= lev0 the rows of level box i are nonzero
 // only in block slot[l][i] (-1: nowhere).  The upward sweep and the middle
 // factor, which keep that pattern, then run on one block per box.
+// The same structure describes outputs of which a box's rows are needed
+// only outside block slot[l][i] (on levels >= lev0): the middle factor and
+// the downward sweep then skip that block.
 struct SparseRHS {
   int lev0 = 0;
   int qc = 0;
   std::vector<std::vector<int>> slot;   // per level, per level box
 };
 void solve_rows(rsf_handle_s* h, int op, const double* in, double* out, int q, int io_df = 0,
-                const SparseRHS* sp = nullptr);
+                const SparseRHS* sp = nullptr, const SparseRHS* skip_out = nullptr);
 // In-place conversion of n doubles to df64 pairs (to = 1) or back (to = 0).
 void convert_df64(double* p, int64_t n, int to, cudaStream_t s);
 // Peeled traces (Sec. 3) of G_0 = F^-1 (when want0 or Fk is null) and of

@@ -448,11 +448,13 @@ void peel_traces(rsf_handle_s* F, rsf_handle_s* Fk, bool want0, double tol, cons
       }
       if ((int64_t)gb2.bytes < bytes) gb2.alloc(bytes, s);
       double* x3 = want0 ? out[0] : gb2.as<double>();
+      // G_1 W is only read outside each box's own slot block (the sample
+      // blocks Y_ab take the siblings' slots), so the outer solves skip it
       solve_rows(F, RSF_OP_INV, x, x3, q, io, sp);                        // F^-1 W
-      solve_rows(Fk, RSF_OP_APPLY, x3, out[1], q, io);                    // F_k F^-1 W
+      solve_rows(Fk, RSF_OP_APPLY, x3, out[1], q, io, nullptr, sp);       // F_k F^-1 W
       solve_rows(Fk, RSF_OP_APPLY, x, ga.as<double>(), q, io, sp);
       double* x2 = want0 ? gb2.as<double>() : x3;
-      solve_rows(F, RSF_OP_INV, ga.as<double>(), x2, q, io);              // F^-1 F_k W
+      solve_rows(F, RSF_OP_INV, ga.as<double>(), x2, q, io, nullptr, sp); // F^-1 F_k W
       LAUNCH(average_kernel, cdiv(cnt, 256), 256, 0, s, out[1], x2, cnt, io);
     }
     if (split)

@@ -114,7 +114,39 @@ static void restrict_batch(const std::vector<GemmDesc>& d, const std::vector<int
   out.build(r, s);
 }
 
-void solve_rows(rsf_handle_s* h, int op, const double* in, double* out, int q, int io_df, const SparseRHS* sp) {
+// The descriptors of one level without each box's unneeded column block
+// (boxes without a slot keep all columns).
+static void complement_batch(const std::vector<GemmDesc>& d, const std::vector<int>& box,
+                             const std::vector<int>& slot, int qc, int nblk, cudaStream_t s, GemmBatch& out) {
+  std::vector<GemmDesc> r;
+  r.reserve(2 * d.size());
+  for (size_t j = 0; j < d.size(); j++) {
+    const int sl = slot[box[j]];
+    GemmDesc g = d[j];
+    if (sl < 0) {
+      g.M = nblk * qc;
+      g.m0 = 0;
+      r.push_back(g);
+      continue;
+    }
+    if (sl > 0) {
+      g.M = sl * qc;
+      g.m0 = 0;
+      r.push_back(g);
+    }
+    if (sl < nblk - 1) {
+      g.M = (nblk - 1 - sl) * qc;
+      g.m0 = (sl + 1) * qc;
+      r.push_back(g);
+    }
+  }
+  out.build(r, s);
+}
+
+void solve_rows(rsf_handle_s* h, int op, const double* in, double* out, int q, int io_df, const SparseRHS* sp,
+                const SparseRHS* skip_out) {
+  RSF_CHECK(!skip_out || (skip_out->qc > 0 && q % skip_out->qc == 0), RSF_EINVAL, "column blocks must tile q");
+  const int nblk = skip_out ? q / skip_out->qc : 1;
   const int df = h->df ? 1 : 0;
   const int cvt = (df && !io_df) ? 1 : 0;
   RSF_CHECK(!io_df || df, RSF_EINVAL, "df64 input needs a mixed-precision factorization");
@@ -184,6 +216,7 @@ void solve_rows(rsf_handle_s* h, int op, const double* in, double* out, int q, i
     double* x = Xl(l);
     double* t = tmp.as<double>();
     const bool sparse = sp && l >= sp->lev0;
+    const bool skip = skip_out && l >= skip_out->lev0;
     auto prod = [&](int v, bool from_tmp) {
       // out = in * op(B): descriptors read base 0 and write base 1; on a
       // sparse level only each box's nonzero column block (the others stay
@@ -196,6 +229,10 @@ void solve_rows(rsf_handle_s* h, int op, const double* in, double* out, int q, i
       if (sparse) {
         GemmBatch r;
         restrict_batch(Lv.hMid[v], Lv.boxMid[v], sp->slot[l], sp->qc, s, r);
+        r.run(b, s);
+      } else if (skip) {
+        GemmBatch r;
+        complement_batch(Lv.hMid[v], Lv.boxMid[v], skip_out->slot[l], skip_out->qc, nblk, s, r);
         r.run(b, s);
       } else {
         Lv.gMid[v].run(b, s);
@@ -221,14 +258,19 @@ void solve_rows(rsf_handle_s* h, int op, const double* in, double* out, int q, i
     LevelData& Lv = h->levels[l];
     if (Lv.nrows == 0) continue;
     double* F = Lv.fpool.as<double>();
-    if (l > 0) {
-      if (down == 1) {
-        run_level_gemm(Lv.gRS_E, Xl(l), tmp.as<double>(), F, q, -1.0, s, df);
-        run_level_gemm(Lv.gSR_Tt, Xl(l), tmp.as<double>(), F, q, -1.0, s, df);
-      } else if (down == 2) {
-        run_level_gemm(Lv.gSR_Et, Xl(l), tmp.as<double>(), F, q, 1.0, s, df);
-        run_level_gemm(Lv.gRS_T, Xl(l), tmp.as<double>(), F, q, 1.0, s, df);
+    if (l > 0 && down != 0) {
+      const bool skip = skip_out && l >= skip_out->lev0;
+      const GemmBatch* g1 = down == 1 ? &Lv.gRS_E : &Lv.gSR_Et;
+      const GemmBatch* g2 = down == 1 ? &Lv.gSR_Tt : &Lv.gRS_T;
+      GemmBatch r1, r2;
+      if (skip) {
+        complement_batch(down == 1 ? Lv.hRS_E : Lv.hSR_Et, Lv.boxRSE, skip_out->slot[l], skip_out->qc, nblk, s, r1);
+        complement_batch(down == 1 ? Lv.hSR_Tt : Lv.hRS_T, Lv.boxRSE, skip_out->slot[l], skip_out->qc, nblk, s, r2);
+        g1 = &r1; g2 = &r2;
       }
+      const double a = down == 1 ? -1.0 : 1.0;
+      run_level_gemm(*g1, Xl(l), tmp.as<double>(), F, q, a, s, df);
+      run_level_gemm(*g2, Xl(l), tmp.as<double>(), F, q, a, s, df);
     }
     double* child = (l < L) ? Xl(l + 1) : nullptr;
     LAUNCH(scatter_rows_kernel, cdiv(Lv.nrows, 8), 256, 0, s, Lv.src.as<int>(), Lv.nrows, q, Xl(l), child, out, cvt);
