@@ -391,11 +391,11 @@ __device__ void qr_pivot_step(int p, const QRProb* __restrict__ probs, QRState* 
 // multiply-adds per element and step.
 __device__ __forceinline__ void qr_update_col(int64_t gw, int lane, const QRProb* __restrict__ probs,
                                               QRState* __restrict__ st, const int* __restrict__ colprefix,
-                                              int nprob, int j, double* __restrict__ pool,
+                                              const int* __restrict__ colprob, int j, double* __restrict__ pool,
                                               const unsigned char* __restrict__ chosen,
                                               const double* __restrict__ vbuf, double* __restrict__ nu2,
                                               double* __restrict__ nuref2) {
-  int p = find_prob(colprefix, nprob, (int)gw);
+  const int p = colprob[gw];
   if (st[p].done) return;
   const QRProb q = probs[p];
   int col = (int)(gw - colprefix[p]);
@@ -473,8 +473,9 @@ __device__ bool qr_grid_barrier(unsigned int* bar, unsigned int nblocks, DevStat
 // problem is done; ndone changes only in a pivot phase, so every CTA reads the
 // same count between the two barriers of a step and all leave together.
 __global__ void __launch_bounds__(QR_THREADS) qr_persistent_kernel(
-    const QRProb* __restrict__ probs, QRState* __restrict__ st, const int* __restrict__ colprefix, int nprob,
-    int64_t ncols, int maxsteps, double* __restrict__ pool, int* __restrict__ piv,
+    const QRProb* __restrict__ probs, QRState* __restrict__ st, const int* __restrict__ colprefix,
+    const int* __restrict__ colprob, int nprob, int64_t ncols, int maxsteps, double* __restrict__ pool,
+    int* __restrict__ piv,
     unsigned char* __restrict__ chosen, double* __restrict__ vbuf, double* __restrict__ nu2,
     double* __restrict__ nuref2, int* __restrict__ ndone, unsigned int* __restrict__ bar, DevStatus* dst,
     int level) {
@@ -488,7 +489,7 @@ __global__ void __launch_bounds__(QR_THREADS) qr_persistent_kernel(
     if (!qr_grid_barrier(bar, nb, dst, level)) return;
     if (j == maxsteps || *(volatile int*)ndone >= nprob) return;
     for (int64_t gw = wid; gw < ncols; gw += nwarps)
-      qr_update_col(gw, lane, probs, st, colprefix, nprob, j, pool, chosen, vbuf, nu2, nuref2);
+      qr_update_col(gw, lane, probs, st, colprefix, colprob, j, pool, chosen, vbuf, nu2, nuref2);
     if (!qr_grid_barrier(bar, nb, dst, level)) return;
   }
 }
@@ -510,6 +511,13 @@ void QRBatch::build(const std::vector<QRProb>& p, cudaStream_t s) {
   RSF_CHECK(ncols < (int64_t)1 << 31, RSF_EINVAL, "qr: too many columns");
   upload(prob, pp, s);
   upload(colprefix, colprefix_h, s);
+  {
+    // problem of every column (the update phase looks it up once per column)
+    std::vector<int> cp(std::max<int64_t>(1, ncols), 0);
+    for (int i = 0; i < nprob; i++)
+      for (int c = colprefix_h[i]; c < colprefix_h[i + 1]; c++) cp[c] = i;
+    upload(colprob, cp, s);
+  }
   state.alloc(sizeof(QRState) * std::max(1, nprob), s);
   piv.alloc(sizeof(int) * std::max<int64_t>(1, ncols), s);
   chosen.alloc(std::max<int64_t>(1, ncols), s);
@@ -549,6 +557,7 @@ void QRBatch::run(double* pool, DevStatus* st, int level, cudaStream_t s) {
   const QRProb* a_probs = prob.as<QRProb>();
   QRState* a_st = state.as<QRState>();
   const int* a_cp = colprefix.as<int>();
+  const int* a_cprob = colprob.as<int>();
   int a_nprob = nprob;
   int64_t a_ncols = ncols;
   int a_maxsteps = maxsteps;
@@ -562,7 +571,7 @@ void QRBatch::run(double* pool, DevStatus* st, int level, cudaStream_t s) {
   unsigned int* a_bar = reinterpret_cast<unsigned int*>(ndone.as<int>() + 1);
   DevStatus* a_dst = st;
   int a_level = level;
-  void* args[] = {&a_probs, &a_st, &a_cp, &a_nprob, &a_ncols, &a_maxsteps, &a_pool,
+  void* args[] = {&a_probs, &a_st, &a_cp, &a_cprob, &a_nprob, &a_ncols, &a_maxsteps, &a_pool,
                   &a_piv, &a_chosen, &a_vbuf, &a_nu2, &a_nuref2, &a_ndone, &a_bar, &a_dst, &a_level};
   int tu = prof_begin(s);
   cudaEvent_t e0 = nullptr, e1 = nullptr;

@@ -79,7 +79,7 @@ struct QRBatch {
   int64_t ncols = 0, nrows = 0;
   int maxsteps = 0;
   std::vector<int> colprefix_h;   // host copy of the column prefix (for launch sizing)
-  DBuf prob, state, piv, chosen, vbuf, colprefix, ndone, nu2, nuref2;
+  DBuf prob, state, piv, chosen, vbuf, colprefix, colprob, ndone, nu2, nuref2;
   // m (rows) may be finalised on the device (near-field counts) before run().
   void build(const std::vector<QRProb>& p, cudaStream_t s);
   // Runs all steps; pool is the matrix storage; st is the status word.
