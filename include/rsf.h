@@ -132,6 +132,16 @@ void rsf_opts_default(rsf_opts* o);
 /* Message of the last failing call on this thread ("" if none). */
 const char* rsf_last_error(void);
 
+/* Failure detection self-test (no counterpart in the paper).  Every device
+ * wait in this library is bounded: the grid barrier of the persistent
+ * pivoted-QR kernel gives up after a few seconds, records RSF_ETIMEOUT in the
+ * handle's status word and leaves the kernel, so a wait that cannot finish
+ * surfaces as an error instead of a hang.  This call runs that barrier with
+ * one participant more than it launches (a wait nothing can end) and returns
+ * RSF_OK if the wait gave up and reported RSF_ETIMEOUT as designed, RSF_ECUDA
+ * otherwise.  It takes a few seconds and leaves the context usable. */
+rsf_status rsf_selftest_wait_limit(void* stream);
+
 /* Device-memory hook.  The paper has no counterpart: this lets a host
  * framework back every device allocation the library makes (factor storage,
  * solve and peeling work buffers) with its own allocator, e.g. PyTorch's

@@ -28,7 +28,7 @@ EXPORTS = ["rsf_opts_default", "rsf_last_error", "rsf_tree_build", "rsf_tree_des
            "gp_loglik", "gp_score", "gp_loglik_and_score", "rsf_get_info",
            "rsf_launch_count", "rsf_profile_enable", "rsf_profile_read", "rsf_destroy",
            "rsf_solve_noalloc", "rsf_set_allocator", "rsf_build_batched", "rsf_logdet_sets",
-           "gp_loglik_and_score_batched"]
+           "gp_loglik_and_score_batched", "rsf_selftest_wait_limit"]
 
 
 class RsfKernel(C.Structure):
@@ -93,6 +93,7 @@ def lib():
         L.rsf_build_batched.argtypes = [ip, C.POINTER(C.c_int64), vp, C.POINTER(RsfKernel), dp, ip,
                                         C.c_double, C.POINTER(RsfOpts), vp, C.POINTER(vp)]
         L.rsf_logdet_sets.argtypes = [vp, dp]
+        L.rsf_selftest_wait_limit.argtypes = [vp]
         L.gp_loglik_and_score_batched.argtypes = [ip, C.POINTER(C.c_int64), vp, vp, C.POINTER(RsfKernel), dp,
                                                   C.c_double, C.c_double, C.POINTER(RsfOpts), vp, dp, dp, dp]
         L.rsf_profile_enable.argtypes = [ip]
@@ -183,6 +184,13 @@ def use_torch_allocator(enable: bool = True) -> None:
     hooks = (_ALLOC_FN(_alloc), _FREE_FN(_free))
     _check(lib().rsf_set_allocator(hooks[0], hooks[1], None))
     _hooks = hooks
+
+
+def selftest_wait_limit() -> None:
+    """rsf_selftest_wait_limit: runs the bounded grid barrier into its time
+    limit on the current stream; raises RsfError unless it reported
+    RSF_ETIMEOUT and returned."""
+    _check(lib().rsf_selftest_wait_limit(_stream()))
 
 
 def profile(enable: bool) -> None:

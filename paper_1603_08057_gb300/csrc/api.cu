@@ -286,6 +286,14 @@ void rsf_opts_default(rsf_opts* o) {
 
 const char* rsf_last_error(void) { return g_err.c_str(); }
 
+rsf_status rsf_selftest_wait_limit(void* stream) {
+  API_BEGIN
+  const int code = barrier_timeout_selftest((cudaStream_t)stream);
+  RSF_CHECK(code == RSF_ETIMEOUT, RSF_ECUDA,
+            "the bounded grid barrier did not report its timeout (status " + std::to_string(code) + ")");
+  API_END
+}
+
 rsf_status rsf_set_allocator(rsf_alloc_fn alloc_fn, rsf_free_fn free_fn, void* ctx) {
   API_BEGIN
   RSF_CHECK((alloc_fn == nullptr) == (free_fn == nullptr), RSF_EINVAL,

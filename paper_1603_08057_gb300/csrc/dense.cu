@@ -494,6 +494,30 @@ __global__ void __launch_bounds__(QR_THREADS) qr_persistent_kernel(
   }
 }
 
+// Self-test of the bounded grid barrier: every CTA waits for one more CTA
+// than the grid holds, so the wait can only end by its limit.
+__global__ void barrier_timeout_probe_kernel(unsigned int* bar, DevStatus* dst) {
+  qr_grid_barrier(bar, gridDim.x + 1, dst, -1);
+}
+
+int barrier_timeout_selftest(cudaStream_t s) {
+  DBuf bar, st;
+  bar.alloc(2 * sizeof(unsigned int), s);
+  bar.zero();
+  st.alloc(sizeof(DevStatus), s);
+  st.zero();
+  unsigned int* a_bar = bar.as<unsigned int>();
+  DevStatus* a_st = st.as<DevStatus>();
+  void* args[] = {&a_bar, &a_st};
+  RSF_CUDA(cudaLaunchCooperativeKernel((const void*)barrier_timeout_probe_kernel, dim3(2), dim3(QR_THREADS), args, 0,
+                                       s));
+  ::rsf::g_launches++;
+  DevStatus h{};
+  d2h(&h, a_st, 1, s);
+  sync(s);
+  return h.code;
+}
+
 void QRBatch::build(const std::vector<QRProb>& p, cudaStream_t s) {
   nprob = (int)p.size();
   std::vector<QRProb> pp = p;

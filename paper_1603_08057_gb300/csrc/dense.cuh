@@ -94,6 +94,11 @@ struct QRBatch {
 // perm[out0 .. out0 + cpiv) and k to kout.
 void qr_split(const QRBatch& qb, const int64_t* d_out0, int* d_perm, int* d_kout, cudaStream_t s);
 
+// Runs the QR kernel's grid barrier so that its bounded wait must give up
+// (one participant more than launched); returns the device status code
+// (RSF_ETIMEOUT when the limit works).  Takes a few seconds.
+int barrier_timeout_selftest(cudaStream_t s);
+
 // Back-substitution with the QR's upper triangle R11 (k x k, pivot order):
 // for each problem and each right-hand side column listed by rhs (physical
 // column indices of A, count nrhs per problem), solve R11 t = A[0:k, col]
