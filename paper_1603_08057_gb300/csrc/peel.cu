@@ -82,36 +82,41 @@ __global__ void gen_w_kernel(const int* __restrict__ slotrow, int64_t n, int qc,
   store_val(W + g, v, df);
 }
 
-// Sketch block V_a (|I_a| x 2q) of box a: N(0,1) draws from Philox stream 2,
-// written into columns q .. 3q-1 of [W_a V_a].  V_a is independent of the
-// test matrices, so the basis it selects does not depend on W_a.
-struct VBox {
-  int64_t r0, out0;
-  int rows;
-};
-__global__ void gen_v_kernel(const VBox* __restrict__ vb, const int64_t* __restrict__ prefix, int nprob,
-                             int64_t total, int q, int level, unsigned long long seed, double* __restrict__ out,
-                             int df) {
-  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= total) return;
-  int lo = 0, hi = nprob - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (prefix[mid] <= g) lo = mid; else hi = mid - 1;
-  }
-  const VBox v = vb[lo];
-  int64_t x = g - prefix[lo];
-  int i = (int)(x % v.rows), j = (int)(x / v.rows);
-  store_val(out + v.out0 + i + (int64_t)j * v.rows,
-            philox_normal((unsigned)(v.r0 + i), (unsigned)j, (unsigned)level, 2u, seed), df);
-}
-
 // Column block extraction from row-major chunks into column-major matrices:
 // out[i + (col0 + j) * ldo] = in[(r0 + i) * ldi + cb + j], i < rows, j < qc.
 struct ExtractProb {
   int64_t r0, out0;
   int rows, cb;
 };
+// Sparse sign embedding of a sample block: out (ell x q, column-major, ld
+// ell) = Omega Y with Omega given per bucket (row of Omega) as a list of
+// (row of Y << 1 | negative sign), scaled by 1 / sqrt(SKETCH_S).  One thread
+// per output entry, buckets fastest.
+constexpr int SKETCH_S = 8;
+struct SketchProb {
+  int64_t y0, out0;   // Y block (rows x q, column-major, ld rows) and output offsets
+  int rows;
+  int bucket0;        // first bucket pointer of the box's embedding
+};
+__global__ void sparse_sketch_kernel(const SketchProb* __restrict__ sp, int64_t total, int ell, int q,
+                                     const int* __restrict__ bptr, const int* __restrict__ ent,
+                                     const double* __restrict__ Y, double* __restrict__ out, int df) {
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= total) return;
+  const int64_t per = (int64_t)ell * q;
+  const SketchProb P = sp[g / per];
+  const int64_t rem = g % per;
+  const int c = (int)(rem / ell), u = (int)(rem % ell);
+  const double* y = Y + P.y0 + (int64_t)c * P.rows;
+  double acc = 0.0;
+  for (int k = bptr[P.bucket0 + u]; k < bptr[P.bucket0 + u + 1]; k++) {
+    const int e = ent[k];
+    const double v = load_val(y + (e >> 1), df);
+    acc += (e & 1) ? -v : v;
+  }
+  out[P.out0 + u + (int64_t)c * ell] = acc * 0.35355339059327373;   // 1 / sqrt(8)
+}
+
 __global__ void extract_kernel(const ExtractProb* __restrict__ ep, const int64_t* __restrict__ prefix, int nprob,
                                int64_t total, int qc, int ldi, int col0, const double* __restrict__ in,
                                double* __restrict__ out, int df) {
@@ -388,6 +393,20 @@ void apply_level_sparse(const PLevel& P, const double* X, double* Y, int qc, con
 
 }  // namespace
 
+// Hash of the sparse embedding's choices: SplitMix64 (Steele, Lea & Flood
+// 2014) chained over the key (seed, tree position, level, operator, block).
+static inline uint64_t splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+static inline uint64_t sketch_hash(uint64_t seed, uint64_t pos, int lev, int op, int t) {
+  uint64_t h = splitmix64(seed ^ 0x2545F4914F6CDD1Dull);
+  h = splitmix64(h ^ pos);
+  return splitmix64(h ^ ((uint64_t)lev << 16) ^ ((uint64_t)op << 8) ^ (uint64_t)t);
+}
+
 // Peels the traces of up to two symmetric operators together (Sec. 3):
 //   operator 0: G_0 = F^-1                          (when want0)
 //   operator 1: G_1 = (F^-1 F_k + F_k F^-1) / 2     (when Fk is given)
@@ -627,9 +646,9 @@ void peel_traces(rsf_handle_s* F, rsf_handle_s* Fk, bool want0, double tol, cons
         Wch.push_back(std::move(Wn));
         for (int oi : ops) Ych[oi].push_back(std::move(Y[oi]));
         qtot = q;
-        // [W_a V_a] (|I_a| x 3q) per box, column-major: the box's rows of its
-        // slot's test columns, then 2q sketch columns V_a independent of them
-        for (int a = 0; a < nbx; a++) woff[a + 1] = woff[a] + (int64_t)TL.bx[a].cnt * 3 * q;
+        // W_a (|I_a| x q) per box, column-major: the box's rows of its slot's
+        // test columns
+        for (int a = 0; a < nbx; a++) woff[a + 1] = woff[a] + (int64_t)TL.bx[a].cnt * q;
         WV.alloc(sizeof(double) * std::max<int64_t>(1, woff[nbx]), s);
         for (size_t ch = 0; ch < Wch.size(); ch++) {
           int qq = chunk_q[ch];
@@ -645,16 +664,6 @@ void peel_traces(rsf_handle_s* F, rsf_handle_s* Fk, bool want0, double tol, cons
           LAUNCH(extract_kernel, cdiv(pw.back(), 256), 256, 0, s, d3.as<ExtractProb>(), d4.as<int64_t>(), nbx,
                  pw.back(), qq, 4 * qq, chunk_col0[ch], Wch[ch].as<double>(), WV.as<double>(), 0);
         }
-        std::vector<VBox> vb(nbx);
-        std::vector<int64_t> pv(nbx + 1, 0);
-        for (int a = 0; a < nbx; a++) {
-          vb[a] = {(int64_t)TL.bx[a].start, woff[a] + (int64_t)TL.bx[a].cnt * q, TL.bx[a].cnt};
-          pv[a + 1] = pv[a] + (int64_t)TL.bx[a].cnt * 2 * q;
-        }
-        DBuf d1, d2;
-        upload_prefix(d1, d2, vb, pv, s);
-        LAUNCH(gen_v_kernel, cdiv(pv.back(), 256), 256, 0, s, d1.as<VBox>(), d2.as<int64_t>(), nbx, pv.back(), q,
-               lev, (unsigned long long)o.seed, WV.as<double>(), df);
       }
       int tq = prof_begin(s);
       bool all_done = true;
@@ -665,7 +674,7 @@ void peel_traces(rsf_handle_s* F, rsf_handle_s* Fk, bool want0, double tol, cons
         // Y_ab (|I_a| x q_o) per ordered pair, column-major, in the arithmetic
         // of the applications (df64 or fp64)
         for (int i = 0; i < nop; i++) S.yoff[i + 1] = S.yoff[i] + (int64_t)TL.bx[op[i].a].cnt * qo;
-        for (int i = 0; i < nop; i++) S.soff[i + 1] = S.soff[i] + (int64_t)3 * qo * qo;
+        for (int i = 0; i < nop; i++) S.soff[i + 1] = S.soff[i] + (int64_t)qo * qo;
         S.Yb.alloc(sizeof(double) * std::max<int64_t>(1, S.yoff[nop]), s);
         for (size_t ch = 0; ch < Wch.size(); ch++) {
           const int qq = chunk_q[ch];
@@ -684,10 +693,14 @@ void peel_traces(rsf_handle_s* F, rsf_handle_s* Fk, bool want0, double tol, cons
           LAUNCH(extract_kernel, cdiv(py.back(), 256), 256, 0, s, d1.as<ExtractProb>(), d2.as<int64_t>(), nop,
                  py.back(), take, 4 * qq, chunk_col0[ch], Ych[oi][ch].as<double>(), S.Yb.as<double>(), 0);
         }
-        // S_ab = [W_a(:, :q_o) V_a(:, :2 q_o)]^T Y_ab (3q_o x q_o): rows
-        // 0..q_o-1 are Z_ab = W_a^T Y_ab (for the core of Eq. (lowrankapprox)),
-        // rows q_o..3q_o-1 the sketch of Y_ab by V_a.  A box with at most 2 q_o
-        // rows needs no sketch: its rank-revealing QR runs on Y_ab itself.
+        // Z_ab = W_a(:, :q_o)^T Y_ab (q_o x q_o, for the core of Eq.
+        // (lowrankapprox)).  The
+        // rank-revealing QR runs on Y_ab itself when the box has at most 2 q_o
+        // rows, else on a sparse sign embedding Omega_a Y_ab of Y_ab into
+        // ell = 2 q_o rows (rounded up to a multiple of SKETCH_S): every row of
+        // the box is added, with a random sign, to one random row in each of
+        // SKETCH_S blocks of ell / SKETCH_S rows (an OSNAP embedding, Nelson &
+        // Nguyen 2013), independent of the test matrices.
         std::vector<char> direct(nop);
         for (int i = 0; i < nop; i++) direct[i] = TL.bx[op[i].a].cnt <= 2 * qo;
         S.Sb.alloc(sizeof(double) * std::max<int64_t>(1, S.soff[nop]), s);
@@ -695,23 +708,22 @@ void peel_traces(rsf_handle_s* F, rsf_handle_s* Fk, bool want0, double tol, cons
           std::vector<GemmDesc> g;
           for (int i = 0; i < nop; i++) {
             const PBox& A = TL.bx[op[i].a];
-            g.push_back(mk(qo, qo, A.cnt, 0, woff[op[i].a], A.cnt, 1, 1, S.yoff[i], A.cnt, 0, 2, S.soff[i], 3 * qo,
+            g.push_back(mk(qo, qo, A.cnt, 0, woff[op[i].a], A.cnt, 1, 1, S.yoff[i], A.cnt, 0, 2, S.soff[i], qo,
                            1.0, 0.0));
-            if (!direct[i])
-              g.push_back(mk(2 * qo, qo, A.cnt, 0, woff[op[i].a] + (int64_t)A.cnt * qtot, A.cnt, 1, 1, S.yoff[i],
-                             A.cnt, 0, 2, S.soff[i] + qo, 3 * qo, 1.0, 0.0));
           }
           run_gemm(g, WV.as<double>(), S.Yb.as<double>(), S.Sb.as<double>(), nullptr, s, 1, 1, 1, 1, df);
           if (df) convert_df64(S.Sb.as<double>(), S.soff[nop], 0, s);
         }
+        const int bsz = (2 * qo + SKETCH_S - 1) / SKETCH_S;
+        const int ell = bsz * SKETCH_S;
         // rank-revealing pivoted QR (fp64): the blocks taken from Y_ab first
         // (one contiguous range, converted from df64 in place), then the
-        // 2q_o x q_o sketches
+        // ell x q_o sketches
         std::vector<int> qrows(nop);
         std::vector<int64_t> qoff(nop, 0);
         int64_t ndirect = 0, nqr = 0;
         for (int i = 0; i < nop; i++) {
-          qrows[i] = direct[i] ? TL.bx[op[i].a].cnt : 2 * qo;
+          qrows[i] = direct[i] ? TL.bx[op[i].a].cnt : ell;
           if (direct[i]) { qoff[i] = nqr; nqr += (int64_t)qrows[i] * qo; }
         }
         ndirect = nqr;
@@ -719,16 +731,58 @@ void peel_traces(rsf_handle_s* F, rsf_handle_s* Fk, bool want0, double tol, cons
           if (!direct[i]) { qoff[i] = nqr; nqr += (int64_t)qrows[i] * qo; }
         S.Sqr.alloc(sizeof(double) * std::max<int64_t>(1, nqr), s);
         {
-          std::vector<CopyProb> cy, cs;
-          for (int i = 0; i < nop; i++) {
+          std::vector<CopyProb> cy;
+          for (int i = 0; i < nop; i++)
             if (direct[i]) cy.push_back({qrows[i], qo, qrows[i], qrows[i], S.yoff[i], qoff[i], 0});
-            else cs.push_back({2 * qo, qo, 3 * qo, 2 * qo, S.soff[i] + qo, qoff[i], 0});
-          }
           if (!cy.empty()) {
             copy_batched(cy, S.Yb.as<double>(), S.Sqr.as<double>(), s);
             if (df) convert_df64(S.Sqr.as<double>(), ndirect, 0, s);
           }
-          if (!cs.empty()) copy_batched(cs, S.Sb.as<double>(), S.Sqr.as<double>(), s);
+          // the embedding of every sketched box: per bucket (row of Omega_a)
+          // the list of (box row, sign), ordered by box row
+          std::vector<int> bucket_of_box(nbx, -1);
+          std::vector<int> bptr(1, 0), ent;
+          for (int i = 0; i < nop; i++) {
+            const int a = op[i].a;
+            if (direct[i] || bucket_of_box[a] >= 0) continue;
+            const PBox& A = TL.bx[a];
+            bucket_of_box[a] = (int)bptr.size() - 1;
+            std::vector<int> cnt(ell + 1, 0), hu((size_t)A.cnt * SKETCH_S);
+            std::vector<char> neg((size_t)A.cnt * SKETCH_S);
+            for (int r = 0; r < A.cnt; r++)
+              for (int t = 0; t < SKETCH_S; t++) {
+                const uint64_t h = sketch_hash(o.seed, (uint64_t)(A.start + r), lev, oi, t);
+                const int u = t * bsz + (int)(h % (uint64_t)bsz);
+                hu[(size_t)r * SKETCH_S + t] = u;
+                neg[(size_t)r * SKETCH_S + t] = (char)(h >> 63);
+                cnt[u + 1]++;
+              }
+            for (int u = 0; u < ell; u++) cnt[u + 1] += cnt[u];
+            const int base = (int)ent.size();
+            ent.resize(base + (size_t)A.cnt * SKETCH_S);
+            std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+            for (int r = 0; r < A.cnt; r++)
+              for (int t = 0; t < SKETCH_S; t++) {
+                const size_t k = (size_t)r * SKETCH_S + t;
+                ent[base + fill[hu[k]]++] = (r << 1) | neg[k];
+              }
+            for (int u = 1; u <= ell; u++) bptr.push_back(base + cnt[u]);
+          }
+          std::vector<SketchProb> sk;
+          for (int i = 0; i < nop; i++) {
+            if (direct[i]) continue;
+            const PBox& A = TL.bx[op[i].a];
+            sk.push_back({S.yoff[i], qoff[i], A.cnt, bucket_of_box[op[i].a]});
+          }
+          if (!sk.empty()) {
+            DBuf dsk, dbp, den;
+            upload(dsk, sk, s);
+            upload(dbp, bptr, s);
+            upload(den, ent, s);
+            const int64_t total = (int64_t)sk.size() * ell * qo;
+            LAUNCH(sparse_sketch_kernel, cdiv(total, 256), 256, 0, s, dsk.as<SketchProb>(), total, ell, qo,
+                   dbp.as<int>(), den.as<int>(), S.Yb.as<double>(), S.Sqr.as<double>(), df);
+          }
         }
         std::vector<QRProb> qp(nop);
         for (int i = 0; i < nop; i++) {
@@ -838,7 +892,7 @@ void peel_traces(rsf_handle_s* F, rsf_handle_s* Fk, bool want0, double tol, cons
         for (int i = 0; i < nop; i++) {
           int rows = PL.bx[op[i].a].cnt;
           pg[i] = {yoff[i], poff[i], qb.colprefix_h[i], rows, rows};
-          pz[i] = {soff[i], zpoff[i], qb.colprefix_h[i], q, 3 * q};
+          pz[i] = {soff[i], zpoff[i], qb.colprefix_h[i], q, q};
           gp[i + 1] = gp[i] + (int64_t)rows * rank[i];
           gz[i + 1] = gz[i] + (int64_t)q * rank[i];
         }
@@ -886,7 +940,7 @@ void peel_traces(rsf_handle_s* F, rsf_handle_s* Fk, bool want0, double tol, cons
           QRProb x{};
           x.m = q; x.c = rab + q; x.cpiv = rab; x.maxk = rab; x.lda = q; x.a = qpool; x.tol = 0.0;
           cp1.push_back({q, rab, q, q, boff[iab], qpool, 0});
-          cores.push_back({soff[iab], soff[iba], qpool + (int64_t)q * rab, q, 3 * q});
+          cores.push_back({soff[iab], soff[iba], qpool + (int64_t)q * rab, q, q});
           qpool += (int64_t)q * (rab + q);
           q1.push_back(x);
         }
