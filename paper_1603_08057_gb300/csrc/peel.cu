@@ -916,8 +916,14 @@ void peel_traces(rsf_handle_s* F, rsf_handle_s* Fk, bool want0, double tol, cons
           // B = Zpiv (q x r) * Rinv
           gb.push_back(mk(q, r, r, 0, zpoff[i], q, 0, 1, roff[i], r, 0, 2, boff[i], q, 1.0, 0.0, 2));
         }
-        run_gemm(gb, Zpiv.as<double>(), Rinv.as<double>(), Bm.as<double>(), nullptr, s);
-        if (df) convert_df64(Rinv.as<double>(), roff[nop], 1, s);
+        // both products in the arithmetic of the applications; B returns to
+        // fp64 for the least-squares QRs of the cores
+        if (df) {
+          convert_df64(Rinv.as<double>(), roff[nop], 1, s);
+          convert_df64(Zpiv.as<double>(), zpoff[nop], 1, s);
+        }
+        run_gemm(gb, Zpiv.as<double>(), Rinv.as<double>(), Bm.as<double>(), nullptr, s, 1, 1, 1, 1, df);
+        if (df) convert_df64(Bm.as<double>(), boff[nop], 0, s);
         run_gemm(gu, Ypiv.as<double>(), Rinv.as<double>(), UP, nullptr, s, 1, 1, 1, 1, df);
       }
       Ypiv.release();
