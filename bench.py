@@ -186,7 +186,9 @@ def run_reference(args):
     cores = os.cpu_count()
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(cfg, parallelism=f"host cores x{cores} (rank 0)",
+                           form="CPU oracle: plain fp64 NumPy/SciPy RSF + weak peeling"),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"oracle Algorithm 1 on a {CPU_SAMPLE_N}-point subsample, scaled by (n/{CPU_SAMPLE_N})^1.5"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
