@@ -9,9 +9,9 @@
 namespace rsf {
 
 // ===================================================================== GEMM
-// Tile BM x BN (64 x 32), BK = 16; each thread owns a 4 x 4 register tile
-// (rows tm + TM i, cols tn + TN j with TM = BM / 4, TN = BN / 4), so a CTA
-// has TM x TN (128) threads.
+// Tile BM x BN (64 x 32), BK = 16; each thread owns an RM x RN (4 x 4)
+// register tile (rows tm + TM i, cols tn + TN j with TM = BM / RM,
+// TN = BN / RN), so a CTA has TM x TN (128) threads.
 #ifndef GEMM_BM
 #define GEMM_BM 64
 #endif
@@ -23,7 +23,10 @@ namespace rsf {
 #endif
 // Four resident CTAs per SM (registers capped at 128) and a k loop unrolled
 // by two: measured on GB300 against full unrolling with two CTAs per SM,
-// 2.4x on 40 x 40 leaf blocks and 1.3x on 1000 x 1000 blocks in df64.
+// 2.4x on 40 x 40 leaf blocks and 1.3x on 1000 x 1000 blocks in df64.  A
+// 128 x 32 tile with 8 x 4 per thread and BK = 8 is 5-11 % faster on
+// isolated leaf and mid-level shapes but 8 % slower across a whole
+// evaluation (more M-tile waste on the narrow column blocks of the peeling).
 #ifndef GEMM_MIN_BLOCKS
 #define GEMM_MIN_BLOCKS 4
 #endif
@@ -31,7 +34,11 @@ namespace rsf {
 #define GEMM_KUNROLL 2
 #endif
 constexpr int BM = GEMM_BM, BN = GEMM_BN, BK = GEMM_BK;
-constexpr int TM = BM / 4, TN = BN / 4, GT = TM * TN, KUNROLL = GEMM_KUNROLL;
+#ifndef GEMM_RM
+#define GEMM_RM 4
+#endif
+constexpr int RM = GEMM_RM, RN = 4;   // register tile of a thread: RM x RN
+constexpr int TM = BM / RM, TN = BN / RN, GT = TM * TN, KUNROLL = GEMM_KUNROLL;
 static_assert((BM * BK) % GT == 0 && (BN * BK) % GT == 0, "tile loads must split evenly");
 
 __device__ __forceinline__ int find_prob(const int* prefix, int nprob, int tile) {
@@ -128,11 +135,11 @@ __global__ void __launch_bounds__(GT, GEMM_MIN_BLOCKS) gemm_kernel(const GemmDes
   __shared__ __align__(16) T sB[2][BK][BN + 1];
   const int t = threadIdx.x;
   const int tm = t % TM, tn = t / TM;
-  typename AR::Acc acc[4][4];
+  typename AR::Acc acc[RM][RN];
 #pragma unroll
-  for (int i = 0; i < 4; i++)
+  for (int i = 0; i < RM; i++)
 #pragma unroll
-    for (int j = 0; j < 4; j++) acc[i][j] = AR::acc0();
+    for (int j = 0; j < RN; j++) acc[i][j] = AR::acc0();
 
   auto load_tile = [&](int kb, int st) {
 #pragma unroll
@@ -177,26 +184,26 @@ __global__ void __launch_bounds__(GT, GEMM_MIN_BLOCKS) gemm_kernel(const GemmDes
     __syncthreads();
 #pragma unroll KUNROLL
     for (int kk = 0; kk < BK; kk++) {
-      T a[4], b[4];
+      T a[RM], b[RN];
 #pragma unroll
-      for (int i = 0; i < 4; i++) a[i] = sA[st][kk][tm + TM * i];
+      for (int i = 0; i < RM; i++) a[i] = sA[st][kk][tm + TM * i];
 #pragma unroll
-      for (int j = 0; j < 4; j++) b[j] = sB[st][kk][tn + TN * j];
+      for (int j = 0; j < RN; j++) b[j] = sB[st][kk][tn + TN * j];
 #pragma unroll
-      for (int i = 0; i < 4; i++)
+      for (int i = 0; i < RM; i++)
 #pragma unroll
-        for (int j = 0; j < 4; j++) AR::mac(acc[i][j], a[i], b[j]);
+        for (int j = 0; j < RN; j++) AR::mac(acc[i][j], a[i], b[j]);
     }
     __syncthreads();
     st ^= 1;
   }
   const double alpha = d.alpha * bases.alpha_scale, beta = d.beta;
 #pragma unroll
-  for (int i = 0; i < 4; i++) {
+  for (int i = 0; i < RM; i++) {
     int gm = m0 + tm + TM * i;
     if (gm >= M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; j++) {
+    for (int j = 0; j < RN; j++) {
       int gn = n0 + tn + TN * j;
       if (gn >= N) continue;
       if (d.lowC && gm < gn) continue;
