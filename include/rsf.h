@@ -29,8 +29,10 @@
  *     NaN/Inf) are recorded in a device status word and reported by the
  *     call that synchronises next.
  *   - memory: handles own all device memory they allocate (stream-ordered
- *     cudaMallocAsync on the handle's stream) and release it in
- *     rsf_destroy / rsf_tree_destroy.
+ *     cudaMallocAsync on the handle's stream, or the hook installed with
+ *     rsf_set_allocator) and release it in rsf_destroy / rsf_tree_destroy;
+ *   - every device-side wait is bounded (RSF_ETIMEOUT, see
+ *     rsf_selftest_wait_limit).
  */
 #ifndef RSF_H
 #define RSF_H
