@@ -36,7 +36,21 @@ def test_library_builds_loads_and_exports_every_symbol():
     # options defaults are readable without a GPU
     o = binding.RsfOpts()
     lib.rsf_opts_default(ctypes.byref(o))
-    assert (o.n_occ, o.n_prox, o.oversample) == (64, 256, 10)
+    assert (o.n_occ, o.n_prox, o.n_rings, o.oversample, o.q0, o.seed) == (64, 256, 8, 10, 64, 0)
+    assert (o.r_near, o.r_in, o.r_out) == (1.0, 1.0, 2.0)
+    assert (o.precision, o.trace_form) == (binding.PREC_MIXED, binding.TRACE_SYM)
+    # the hook setter rejects a half-set pair without touching the GPU
+    alloc = binding._ALLOC_FN(lambda n, s, c: None)
+    assert binding.lib().rsf_set_allocator(alloc, binding._FREE_FN(), None) == 1
+    assert binding.lib().rsf_set_allocator(binding._ALLOC_FN(), binding._FREE_FN(), None) == 0
+
+
+def test_batched_offsets_are_validated():
+    from paper_1603_08057_gb300 import binding
+    assert list(binding._offsets([0, 3, 10], 10)) == [0, 3, 10]
+    for bad in ([1, 10], [0, 9], [0]):
+        with pytest.raises(ValueError):
+            binding._offsets(bad, 10)
 
 
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
