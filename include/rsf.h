@@ -22,7 +22,9 @@
  *     indices);
  *   - stream: a cudaStream_t passed as void* (NULL = legacy default stream);
  *     all work of a handle runs on the stream it was built with;
- *   - every call returns an rsf_status and never aborts, traps or prints.
+ *   - every call returns an rsf_status and never aborts, traps or prints
+ *     (unless the environment variable RSF_VERBOSE is set: then a few
+ *     diagnostics go to stderr, for debugging).
  *     On error the outputs are left unchanged, handles stay valid (or NULL),
  *     and rsf_last_error() returns a message (thread-local, valid until the
  *     next call on that thread).  Device-side failures (non-positive pivot,
@@ -126,6 +128,12 @@ typedef struct {
   double flops;          /* algorithmic fp64 flops of the factorization */
   double kernel_evals;   /* kernel evaluations during the factorization */
   int nsets;             /* independent point sets (1 unless built batched) */
+  int solve_df64;        /* 1: solves run on df64 (fp32-pair) factors (mixed
+                            precision), 0: fp64 */
+  double probe_rel_diff; /* derivative factorization in mixed precision: the
+                            relative difference of one df64 and one fp64
+                            apply; df64 is kept when it is <= 10 tol.  -1 when
+                            no probe ran */
 } rsf_info_t;
 
 /* Fills *o with the defaults listed above. */
@@ -221,9 +229,10 @@ rsf_status rsf_solve(rsf_handle h, double* B, int64_t ldb, int nrhs, int op);
  * doubles (32 MiB), which every GPU that loads the library holds until the
  * process exits.  A call needs nrhs * (2 n + the active DOFs of all levels +
  * those of the largest level) doubles; larger requests return RSF_EINVAL
- * without touching B.  The first call on a device (with that device current)
- * looks up the array's device address; make that first call before any
- * stream capture.  All calls share the one array and nothing in it needs to
+ * without touching B.  The device the handle was built on must be the
+ * current device (else RSF_EINVAL): the scratch address is per device.  The
+ * first call on a device looks up the array's device address; make that
+ * first call before any stream capture.  All calls share the one array and nothing in it needs to
  * start at zero, but calls whose work overlaps on the GPU (different streams,
  * or concurrent host threads) race on it: serialise them. */
 #define RSF_NOALLOC_SCRATCH_DOUBLES (1 << 22)

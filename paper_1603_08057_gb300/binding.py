@@ -50,7 +50,8 @@ class RsfInfo(C.Structure):
     _fields_ = [("n", C.c_int64), ("levels", C.c_int), ("boxes", C.c_int64),
                 ("root_size", C.c_int), ("max_rank", C.c_int), ("max_active", C.c_int),
                 ("factor_entries", C.c_int64), ("flops", C.c_double),
-                ("kernel_evals", C.c_double), ("nsets", C.c_int)]
+                ("kernel_evals", C.c_double), ("nsets", C.c_int), ("solve_df64", C.c_int),
+                ("probe_rel_diff", C.c_double)]
 
 
 class RsfError(RuntimeError):

@@ -226,6 +226,7 @@ static rsf_handle_s* make_handle(std::shared_ptr<rsf_tree_s> tree, const rsf_ker
   h->opts = o;
   h->tol = tol;
   h->stream = tree->t.stream;
+  RSF_CUDA(cudaGetDevice(&h->device));
   h->spd = (which == RSF_SIGMA);
   RSF_CHECK(o.precision == RSF_PREC_FP64 || o.precision == RSF_PREC_MIXED, RSF_EINVAL, "unknown precision");
   // df64 for the Cholesky-based factorization of Sigma; a derivative
@@ -617,6 +618,8 @@ rsf_status rsf_get_info(rsf_handle h, rsf_info_t* info) {
   info->flops = h->flops;
   info->kernel_evals = h->kevals;
   info->nsets = h->tree_raw->t.nsets;
+  info->solve_df64 = h->df ? 1 : 0;
+  info->probe_rel_diff = h->probe_rel_diff;
   API_END
 }
 

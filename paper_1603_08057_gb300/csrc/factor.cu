@@ -820,8 +820,14 @@ void factorize(rsf_handle_s* h) {
     } else {
       // A derivative matrix is eliminated with indefinite diagonal blocks,
       // which can amplify rounding errors far beyond the ID tolerance.  Probe
-      // one application in fp64 and in df64 and keep df64 only when the two
-      // agree to the ID tolerance (the factorization's own error level).
+      // one application in fp64 and in df64 and keep df64 when the two agree
+      // to DF64_APPLY_TOL_FACTOR x the ID tolerance.  F_l feeds only the
+      // quadratic term alpha^T F_l alpha and the peeled trace of
+      // (F^-1 F_l + F_l F^-1)/2 (Algorithm 1); a relative apply error delta
+      // moves both by about delta of their size, and Sec. 5.3 pairs
+      // eps_fact with eps_peel = 1000 eps_fact, so 10 eps_fact keeps the
+      // rounding two orders of magnitude below the peeling error of the
+      // trace and of the same order as the factorization's own error.
       h->df = false;
       std::vector<double> hx(n);
       uint64_t st = 0x9E3779B97F4A7C15ull;
@@ -849,7 +855,9 @@ void factorize(rsf_handle_s* h) {
       double nn = dot_device(y64.as<double>(), y64.as<double>(), n, s);
       LAUNCH(axpy_neg_kernel, cdiv(n, 256), 256, 0, s, ydf.as<double>(), y64.as<double>(), n);
       double dd = dot_device(ydf.as<double>(), ydf.as<double>(), n, s);
-      bool ok = std::isfinite(dd) && dd <= h->tol * h->tol * nn;
+      const double lim = DF64_APPLY_TOL_FACTOR * h->tol;
+      bool ok = std::isfinite(dd) && dd <= lim * lim * nn;
+      h->probe_rel_diff = std::sqrt(dd / std::max(nn, 1e-300));
       if (verbose())
         fprintf(stderr, "[rsf] derivative factorization: df64 vs fp64 apply rel diff %.3e -> %s\n",
                 std::sqrt(dd / std::max(nn, 1e-300)), ok ? "df64" : "fp64");

@@ -13,6 +13,9 @@ struct rsf_handle_s;
 namespace rsf {
 
 constexpr int DEPTH_BITS = 24;
+// A derivative factorization keeps its df64 solve factors when a df64 apply
+// agrees with the fp64 apply to this multiple of the ID tolerance.
+constexpr double DF64_APPLY_TOL_FACTOR = 10.0;
 
 struct KernelParams {
   int family;
@@ -146,6 +149,7 @@ struct rsf_handle_s {
   bool spd = true;
   bool df = false;                     // solve factors stored as df64 pairs
   cudaStream_t stream = nullptr;
+  int device = -1;                     // CUDA device current when the handle was built
   std::vector<rsf::LevelData> levels;  // index = tree level (0 = root)
   rsf::DBuf status;                    // DevStatus
   rsf::DBuf logdet_parts;              // per box partial log-determinants
@@ -154,6 +158,7 @@ struct rsf_handle_s {
   int max_rank = 0, max_active = 0;
   double flops = 0, kevals = 0;
   int64_t factor_entries = 0;
+  double probe_rel_diff = -1;          // derivative factorization: df64 vs fp64 apply (-1: no probe)
 };
 
 namespace rsf {

@@ -38,10 +38,9 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 double* g_noalloc_ptr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device.
-double* noalloc_scratch() {
-  int dev = 0;
-  RSF_CUDA(cudaGetDevice(&dev));
+// Device address of the scratch array on device dev, which must be current
+// (the symbol lookup resolves on the current device).
+double* noalloc_scratch(int dev) {
   RSF_CHECK(dev >= 0 && dev < kMaxDevices, RSF_EINVAL, "device ordinal out of range");
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
   if (!g_noalloc_ptr[dev]) {
@@ -85,7 +84,14 @@ void solve_noalloc(rsf_handle_s* h, double* B, int64_t ldb, int nrhs, int op) {
   RSF_CHECK(need <= (int64_t)RSF_NOALLOC_SCRATCH_DOUBLES, RSF_EINVAL,
             "rsf_solve_noalloc: nrhs * (2 n + sum of level rows + largest level) = " + std::to_string(need) +
                 " doubles exceeds the scratch of " + std::to_string((int64_t)RSF_NOALLOC_SCRATCH_DOUBLES));
-  double* ws = noalloc_scratch();
+  // The kernels run on the handle's stream, which belongs to the device the
+  // handle was built on; the scratch address must be that device's.
+  int cur = -1;
+  RSF_CUDA(cudaGetDevice(&cur));
+  RSF_CHECK(cur == h->device, RSF_EINVAL,
+            "rsf_solve_noalloc: the current device (" + std::to_string(cur) + ") is not the handle's device (" +
+                std::to_string(h->device) + "); make the handle's device current first");
+  double* ws = noalloc_scratch(h->device);
   // carve: Xin | Xout | level blocks | tmp  (nothing needs to start at zero:
   // every element is written before it is read)
   double* Xin = ws;

@@ -18,6 +18,9 @@ at this size, so the checks are
     Tr(Sigma) = n (s2 + nug)),
   - s2 g_s2 + nug g_nug = (z^T Sigma^-1 z - n) / 2 (Sigma = s2 Sigma_s2 + nug I).
 
+and, for the score itself, central differences of the log-likelihood of
+tight (eps_fact = 1e-12) fp64 factorizations (Eq. (gradient)).
+
 Tolerances: the applied rows carry the ID error, <= 1e-8 of the row's
 absolute sum sum_j |K_ij x_j| (eps_fact = 1e-9 per level, amplified through
 the levels; measured 1.4e-10 on GB300); F^-1 F x = x to 1e-6 of max |x|
@@ -110,3 +113,43 @@ def test_full_size_score_traces_match_logdet_derivatives(B, pts):
         dn[k] -= step
         fd = (logdet_at(tuple(up)) - logdet_at(tuple(dn))) / (2.0 * step)
         assert fd == pytest.approx(tr, rel=1e-5), (k, fd, tr)
+
+
+def test_full_size_score_vs_loglik_differences(B, pts):
+    # Eq. (gradient): g_k = d loglik / d theta_k.  Reference: central
+    # differences (h = 1e-3 theta_k) of the RSF log-likelihood at
+    # eps_fact = 1e-12 in plain fp64, whose log-determinant and quadratic form
+    # are accurate to ~1e-11 relative, so the differences carry ~1e-6
+    # relative error (the O(h^2) truncation).  The score under test is the
+    # benchmark's configuration: mixed precision, eps_fact 1e-9, eps_peel 1e-6,
+    # at theta of one benchmark step (l * 1.005); z = F^1/2 w drawn at the
+    # workload's theta.  Bar: 1e-3 relative per component.
+    n = WL["n"]
+    th0 = WL["theta"]
+    P = T(pts)
+    o64 = B.opts(precision=0)
+    F = B.Factorization(P, B.MATERN32, th0, B.SIGMA, 1e-12, 0.0, o64)
+    z = F.solve(T(W.standard_normal(n, WL["seed_z"])), B.OP_SQRT)
+    del F
+    th = (th0[0] * 1.005, th0[1], th0[2])
+    ll, g, terms = B.loglik_and_score(P, z, B.MATERN32, th, WL["tol_fact"], WL["tol_peel"])
+    g = g.numpy()
+
+    def loglik_at(theta):
+        Fh = B.Factorization(P, B.MATERN32, theta, B.SIGMA, 1e-12, 0.0, o64)
+        v = Fh.loglik(z)[0]
+        del Fh
+        return v
+
+    fd = np.zeros(3)
+    for k in range(3):
+        step = 1e-3 * th[k]
+        up, dn = list(th), list(th)
+        up[k] += step
+        dn[k] -= step
+        fd[k] = (loglik_at(tuple(up)) - loglik_at(tuple(dn))) / (2.0 * step)
+    t = terms.numpy()
+    scale = 0.5 * np.abs(t[:3]) + 0.5 * np.abs(t[3:])
+    print(f"full size score {g} vs loglik differences {fd}: rel {np.abs(g - fd) / np.abs(fd)}, "
+          f"term scale {np.abs(g - fd) / scale}")
+    assert np.all(np.abs(g - fd) <= 1e-3 * np.abs(fd))
