@@ -50,7 +50,9 @@ WORKLOAD = "matern32_mixture_n262144"
 METRIC = "loglik+score evals/s at n=262k: plain FP64 vs batched mixed form at 1e-6 rel err"
 UNIT = "evals/s"
 FORMS = {"mixed": "mixed precision: fp64 IDs, Cholesky/QR factors, log-determinant and rank decisions; "
-                  "df64 (fp32-pair) multi-RHS solves and peeling GEMMs",
+                  "df64 (fp32-pair) solve and peeling operands multiplied on the tcgen05 tensor cores "
+                  "(exact bf16 slices, fp32 accumulation)",
+         "mixed_df64": "mixed precision with the solve and peeling products in df64 arithmetic on the CUDA cores",
          "fp64": "plain fp64 RSF + weak peeling"}
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 # df64 multiply-add = 12 fp32-pipe instructions (1 mul, 3 fma for the exact
@@ -69,15 +71,17 @@ def parse():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--workload", default=WORKLOAD, choices=sorted(WL.WORKLOADS))
     p.add_argument("--n", type=int, default=None, help="override the point count (testing)")
+    p.add_argument("--tol-peel", type=float, default=None, help="override the workload's eps_peel")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-other-form", action="store_true",
                    help="skip the evaluation in the other precision form")
     p.add_argument("--budget-s", type=float, default=WALL_BUDGET_S,
                    help="wall-clock budget of the whole run; the e2e loop runs as many of the K steps as fit")
-    p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
-                   help="mixed (default): fp64 IDs, Cholesky/QR factors and log-determinant, df64 "
-                        "solves and peeling GEMMs; fp64: every step in fp64 (the plain form)")
+    p.add_argument("--precision", default="mixed", choices=["mixed", "mixed_df64", "fp64"],
+                   help="mixed (default): fp64 IDs, Cholesky/QR factors and log-determinant, solve and "
+                        "peeling products on the tensor cores; mixed_df64: those products in df64 on the "
+                        "CUDA cores; fp64: every step in fp64 (the plain form)")
     return p.parse_args()
 
 
@@ -242,6 +246,68 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU arm
+TC_SLICES = 7
+TC_PRODUCTS = TC_SLICES * (TC_SLICES + 1) // 2   # slice products with s + t < 7
+
+
+def measured_peaks():
+    """MEASURED_PEAKS.json (driver-written, the GB300s) or None."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return None
+
+
+def bf16_peak_tflops():
+    """Dense bf16 tensor peak (sustained, for a kernel timed inside a long
+    step) and where it comes from."""
+    mp = measured_peaks()
+    if mp:
+        for key in ("bf16_tflops_sustained", "bf16_tflops"):
+            if isinstance(mp.get(key), (int, float)) and mp[key] > 0:
+                return float(mp[key]), f"MEASURED_PEAKS.json {key} (of measured)"
+    return 1700.0, "profiling recipe fallback: 1.7 PFLOP/s bf16 sustained (of fallback)"
+
+
+def roofline_of(B, prof, ms_prof):
+    """Roofline of the GEMM engine that took the most time in the profiled
+    evaluation: achieved = its algorithmic (fp64-equivalent, 2 M N K per
+    descriptor) flops / its summed CUDA-event time."""
+    cands = [(prof[B.PROF_GEMM_TC], "tc"), (prof[B.PROF_GEMM_DF], "df"), (prof[B.PROF_GEMM], "fp64")]
+    g, kind = max(cands, key=lambda c: c[0]["ms"])
+    achieved = g["flops"] / (g["ms"] / 1e3) / 1e12 if g["ms"] > 0 else None
+    extra = {}
+    if kind == "tc":
+        bf16, src = bf16_peak_tflops()
+        kname = "tc_gemm_kernel (batched ragged GEMM on tcgen05, df64 operands as exact bf16 slices)"
+        bound, peak = "tensor", bf16 / TC_PRODUCTS
+        psrc = (f"dense bf16 tensor peak {bf16:.0f} TFLOP/s from {src}, divided by the {TC_PRODUCTS} bf16 slice "
+                f"multiply-adds ({TC_SLICES} slices per operand, products with s + t < {TC_SLICES}) that make one "
+                "fp64-class multiply-add")
+        extra = {"bf16_peak": bf16, "bf16_slice_flops_per_fp64_flop": TC_PRODUCTS}
+    elif kind == "df":
+        kname = "gemm_kernel<true> (batched ragged GEMM, df64 arithmetic)"
+        bound, peak = "alu", DF64_PEAK_TFLOPS
+        psrc = ("df64 on the fp32 pipe: 152 SMs x 128 lanes x 2.07 GHz / 12 instructions per multiply-add "
+                "x 2 flop (recipe unit counts and clock)")
+    else:
+        kname = "gemm_kernel<false> (batched ragged GEMM, fp64)"
+        bound, peak = "alu", FP64_PEAK_TFLOPS
+        psrc = "fp64 ALU: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (recipe unit counts and clock)"
+    r = {"bound": bound, "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+         "frac": (achieved / peak) if achieved else None, "traffic": None, "peak_source": psrc,
+         "flops_counted": "2 per multiply-add of each GEMM descriptor (M N K, triangular operands and "
+                          "lower-triangle outputs counted exactly), fp64-equivalent",
+         "measured_on": "one profiled evaluation after the timed loop (per-launch CUDA events on the "
+                        "launching stream)",
+         "launches": g["launches"], "kernel_ms": g["ms"], "profiled_eval_ms": ms_prof,
+         "share_of_step": g["ms"] / ms_prof if ms_prof > 0 else None,
+         "phases_ms": {B.PROF_NAMES[c]: prof[c]["ms"] for c in prof if prof[c]["launches"] > 0}}
+    r.update(extra)
+    return r
+
+
 def rel(a, b):
     return float(abs(a - b) / max(abs(b), 1e-300))
 
@@ -262,6 +328,8 @@ def run_gpu(args):
     from paper_1603_08057_gb300 import binding as B
 
     wl, cfg = workload_config(args.workload, args.n)
+    if args.tol_peel:
+        wl["tol_peel"] = cfg["tol_peel"] = args.tol_peel
     n = cfg["n"]
     fam, alpha = wl["family"], wl["alpha"]
     x = WL.make_points(wl["points"], n, wl["seed_points"])
@@ -274,7 +342,7 @@ def run_gpu(args):
     del F
     torch.cuda.synchronize()
 
-    forms = {"mixed": B.PREC_MIXED, "fp64": B.PREC_FP64}
+    forms = {"mixed": B.PREC_MIXED, "mixed_df64": B.PREC_MIXED_DF64, "fp64": B.PREC_FP64}
     o = B.opts(precision=forms[args.precision])
 
     def step(i, opts=o, p=pts, zz=z):
@@ -324,7 +392,7 @@ def run_gpu(args):
     # relative differences of loglik, quadratic form and score components
     other = None
     if not args.no_other_form:
-        oname = "fp64" if args.precision == "mixed" else "mixed"
+        oname = "fp64" if args.precision != "fp64" else "mixed"
         oo = B.opts(precision=forms[oname])
         torch.cuda.synchronize()
         oe0, oe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -375,29 +443,12 @@ def run_gpu(args):
         if ws > 1:
             dist.destroy_process_group()
         return 0
-    gdf, g64 = prof[B.PROF_GEMM_DF], prof[B.PROF_GEMM]
-    if gdf["ms"] >= g64["ms"]:
-        g, kname, peak = gdf, "gemm_kernel<true> (batched ragged GEMM, df64 arithmetic)", DF64_PEAK_TFLOPS
-        psrc = ("df64 on the fp32 pipe: 152 SMs x 128 lanes x 2.07 GHz / 12 instructions per multiply-add "
-                "x 2 flop (recipe unit counts and clock)")
-    else:
-        g, kname, peak = g64, "gemm_kernel<false> (batched ragged GEMM, fp64)", FP64_PEAK_TFLOPS
-        psrc = "fp64 ALU: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (recipe unit counts and clock)"
-    achieved = g["flops"] / (g["ms"] / 1e3) / 1e12 if g["ms"] > 0 else None
-    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": None, "peak_source": psrc,
-                "flops_counted": "2 per multiply-add of each GEMM descriptor (M N K, triangular operands and "
-                                 "lower-triangle outputs counted exactly), fp64-equivalent",
-                "measured_on": "one profiled evaluation after the timed loop (per-launch CUDA events on the "
-                               "launching stream)",
-                "launches": g["launches"], "kernel_ms": g["ms"], "profiled_eval_ms": ms_prof,
-                "share_of_step": g["ms"] / ms_prof if ms_prof > 0 else None,
-                "phases_ms": {B.PROF_NAMES[c]: prof[c]["ms"] for c in prof if prof[c]["launches"] > 0}}
+    roofline = roofline_of(B, prof, ms_prof)
     cpu = None if args.no_cpu else cpu_leg(wl, n)
     ll, gsc, terms = results[-1]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64+df64" if args.precision == "mixed" else "f64",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+df64",
             "data": "synthetic",
             "config": dict(cfg, parallelism=f"replicas x{ws}", form=FORMS[args.precision],
                            library_timers="off in the timed loop"),

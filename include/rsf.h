@@ -96,9 +96,14 @@ typedef struct {
   uint64_t seed;    /* Philox4x32-10 key of the peeling test matrices (0) */
   int precision;    /* RSF_PREC_FP64 (0): every step in fp64.  RSF_PREC_MIXED
                        (1, default): the IDs, Cholesky/QR factors and
-                       log-determinant stay fp64, the multi-RHS solves and the
-                       peeling products run in double-float (fp32-pair)
-                       arithmetic with ~48-bit significands */
+                       log-determinant stay fp64; the multi-RHS solves and
+                       the peeling products keep their operands as
+                       double-float (fp32-pair, ~48-bit) values and multiply
+                       them on the tensor cores, split exactly into seven
+                       bf16 slices per operand with exact fp32 accumulation
+                       (fp64-class products).  RSF_PREC_MIXED_DF64 (2): the
+                       same storage, products in double-float arithmetic on
+                       the CUDA cores */
   int trace_form;   /* symmetric operator peeled for Tr(F^-1 F_k) (Sec. 3,
                        which allows any symmetrized form with the same
                        trace).  RSF_TRACE_SYM (0, default): the paper's
@@ -111,7 +116,7 @@ typedef struct {
 
 enum { RSF_TRACE_SYM = 0, RSF_TRACE_SQRT = 1 };
 
-enum { RSF_PREC_FP64 = 0, RSF_PREC_MIXED = 1 };
+enum { RSF_PREC_FP64 = 0, RSF_PREC_MIXED = 1, RSF_PREC_MIXED_DF64 = 2 };
 
 typedef struct rsf_tree_s* rsf_tree;
 typedef struct rsf_handle_s* rsf_handle;
@@ -128,8 +133,9 @@ typedef struct {
   double flops;          /* algorithmic fp64 flops of the factorization */
   double kernel_evals;   /* kernel evaluations during the factorization */
   int nsets;             /* independent point sets (1 unless built batched) */
-  int solve_df64;        /* 1: solves run on df64 (fp32-pair) factors (mixed
-                            precision), 0: fp64 */
+  int solve_df64;        /* the form of the solves: 0 fp64; df64 (fp32-pair)
+                            factors with tensor-core (1) or CUDA-core (2)
+                            products, as rsf_opts.precision */
   double probe_rel_diff; /* derivative factorization in mixed precision: the
                             relative difference of one df64 and one fp64
                             apply; df64 is kept when it is <= 10 tol.  -1 when
@@ -151,6 +157,20 @@ const char* rsf_last_error(void);
  * RSF_OK if the wait gave up and reported RSF_ETIMEOUT as designed, RSF_ECUDA
  * otherwise.  It takes a few seconds and leaves the context usable. */
 rsf_status rsf_selftest_wait_limit(void* stream);
+
+/* GEMM engine self-check (no counterpart in the paper).  Computes
+ * C <- alpha op(A) op(B) + beta C for one column-major problem (device fp64
+ * arrays A, B, C; op(X) = X^T when ta / tb is nonzero; op(A) is m x k, op(B)
+ * k x n) with one of the batched-GEMM engines that the solves and the
+ * peeling use: 0 fp64 on the CUDA cores, 1 df64 operands multiplied on the
+ * tensor cores (bf16 slices, exact fp32 accumulation; batches with fewer
+ * than 64 rows fall back to engine 2), 2 df64 arithmetic on the CUDA cores.
+ * Operands are copied and, for engines 1 and 2, rounded to df64 pairs first,
+ * so the result carries that rounding (~2^-48 relative per operand).
+ * Synchronises the stream. */
+rsf_status rsf_selftest_gemm(int engine, int m, int n, int k, int ta, int tb, double alpha,
+                             const double* A, int lda, const double* B, int ldb, double beta,
+                             double* C, int ldc, void* stream);
 
 /* Device-memory hook.  The paper has no counterpart: this lets a host
  * framework back every device allocation the library makes (factor storage,
@@ -290,7 +310,8 @@ int64_t rsf_launch_count(int reset);
 
 /* Kernel timing for reporting: while enabled, the library records CUDA events
  * on the launching stream around its batched GEMM launches (category 0 in
- * fp64, 8 in df64 arithmetic), its pivoted-QR launches (1; category 2 is no
+ * fp64, 8 in df64 arithmetic on the CUDA cores, 9 on the tensor cores), its
+ * pivoted-QR launches (1; category 2 is no
  * longer used: the pivot steps run inside the same persistent launch) and
  * around the phases 3-7 (peeling applications, subtraction of coarser levels,
  * sketch and rank detection, compression of the blocks, factorizations), with

@@ -28,7 +28,7 @@ EXPORTS = ["rsf_opts_default", "rsf_last_error", "rsf_tree_build", "rsf_tree_des
            "gp_loglik", "gp_score", "gp_loglik_and_score", "rsf_get_info",
            "rsf_launch_count", "rsf_profile_enable", "rsf_profile_read", "rsf_destroy",
            "rsf_solve_noalloc", "rsf_set_allocator", "rsf_build_batched", "rsf_logdet_sets",
-           "gp_loglik_and_score_batched", "rsf_selftest_wait_limit"]
+           "gp_loglik_and_score_batched", "rsf_selftest_wait_limit", "rsf_selftest_gemm"]
 
 
 class RsfKernel(C.Structure):
@@ -42,7 +42,7 @@ class RsfOpts(C.Structure):
                 ("precision", C.c_int), ("trace_form", C.c_int)]
 
 
-PREC_FP64, PREC_MIXED = 0, 1
+PREC_FP64, PREC_MIXED, PREC_MIXED_DF64 = 0, 1, 2
 TRACE_SYM, TRACE_SQRT = 0, 1
 
 
@@ -95,6 +95,7 @@ def lib():
                                         C.c_double, C.POINTER(RsfOpts), vp, C.POINTER(vp)]
         L.rsf_logdet_sets.argtypes = [vp, dp]
         L.rsf_selftest_wait_limit.argtypes = [vp]
+        L.rsf_selftest_gemm.argtypes = [ip, ip, ip, ip, ip, ip, C.c_double, vp, ip, vp, ip, C.c_double, vp, ip, vp]
         L.gp_loglik_and_score_batched.argtypes = [ip, C.POINTER(C.c_int64), vp, vp, C.POINTER(RsfKernel), dp,
                                                   C.c_double, C.c_double, C.POINTER(RsfOpts), vp, dp, dp, dp]
         L.rsf_profile_enable.argtypes = [ip]
@@ -149,8 +150,9 @@ def launch_count(reset=False) -> int:
 
 PROF_GEMM, PROF_QR_UPDATE, PROF_QR_PIVOT = 0, 1, 2
 PROF_PEEL_APPLY, PROF_PEEL_SUB, PROF_PEEL_QR, PROF_PEEL_REST, PROF_FACTOR, PROF_GEMM_DF = 3, 4, 5, 6, 7, 8
+PROF_GEMM_TC = 9
 PROF_NAMES = ["gemm_fp64", "qr", "qr_pivot", "peel_apply", "peel_sub", "peel_qr", "peel_rest",
-              "factor", "gemm_df64"]
+              "factor", "gemm_df64", "gemm_tc"]
 
 
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -192,6 +194,24 @@ def selftest_wait_limit() -> None:
     limit on the current stream; raises RsfError unless it reported
     RSF_ETIMEOUT and returned."""
     _check(lib().rsf_selftest_wait_limit(_stream()))
+
+
+def selftest_gemm(engine: int, A: torch.Tensor, B: torch.Tensor, C: torch.Tensor | None = None,
+                  ta=False, tb=False, alpha=1.0, beta=0.0) -> torch.Tensor:
+    """rsf_selftest_gemm: alpha op(A) op(B) + beta C with batched-GEMM engine
+    `engine` (0 fp64, 1 tensor cores on df64 operands, 2 df64 CUDA cores) for
+    float64 CUDA matrices in torch's row-major layout.  A row-major matrix is
+    the column-major transpose, so the library computes the column-major
+    C^T = op(B)^T op(A)^T, whose memory is the row-major C."""
+    A, B = _dev(A), _dev(B)
+    m = A.shape[1] if ta else A.shape[0]
+    k = A.shape[0] if ta else A.shape[1]
+    n = B.shape[0] if tb else B.shape[1]
+    out = torch.zeros((m, n), dtype=torch.float64, device=A.device) if C is None else _dev(C, (m, n)).clone()
+    _check(lib().rsf_selftest_gemm(engine, n, m, k, 1 if tb else 0, 1 if ta else 0, alpha,
+                                   B.data_ptr(), B.shape[1], A.data_ptr(), A.shape[1], beta,
+                                   out.data_ptr(), n, _stream()))
+    return out
 
 
 def profile(enable: bool) -> None:

@@ -228,11 +228,12 @@ static rsf_handle_s* make_handle(std::shared_ptr<rsf_tree_s> tree, const rsf_ker
   h->stream = tree->t.stream;
   RSF_CUDA(cudaGetDevice(&h->device));
   h->spd = (which == RSF_SIGMA);
-  RSF_CHECK(o.precision == RSF_PREC_FP64 || o.precision == RSF_PREC_MIXED, RSF_EINVAL, "unknown precision");
+  RSF_CHECK(o.precision == RSF_PREC_FP64 || o.precision == RSF_PREC_MIXED || o.precision == RSF_PREC_MIXED_DF64,
+            RSF_EINVAL, "unknown precision");
   // df64 for the Cholesky-based factorization of Sigma; a derivative
   // factorization is probed at the end of factorize() and falls back to fp64
   // when df64 would cost accuracy.
-  h->df = (o.precision == RSF_PREC_MIXED);
+  h->df = o.precision;
   h->kp.family = kernel->family;
   h->kp.alpha = kernel->alpha;
   h->kp.l = theta[0];
@@ -292,6 +293,17 @@ rsf_status rsf_selftest_wait_limit(void* stream) {
   const int code = barrier_timeout_selftest((cudaStream_t)stream);
   RSF_CHECK(code == RSF_ETIMEOUT, RSF_ECUDA,
             "the bounded grid barrier did not report its timeout (status " + std::to_string(code) + ")");
+  API_END
+}
+
+rsf_status rsf_selftest_gemm(int engine, int m, int n, int k, int ta, int tb, double alpha, const double* A,
+                             int lda, const double* B, int ldb, double beta, double* C, int ldc, void* stream) {
+  API_BEGIN
+  RSF_CHECK(engine >= 0 && engine <= 2, RSF_EINVAL, "engine must be 0, 1 or 2");
+  RSF_CHECK(m >= 1 && n >= 1 && k >= 0 && A && B && C, RSF_EINVAL, "need m, n >= 1, k >= 0 and non-NULL arrays");
+  RSF_CHECK(lda >= (ta ? k : m) && lda >= 1 && ldb >= (tb ? n : k) && ldb >= 1 && ldc >= m, RSF_EINVAL,
+            "leading dimensions too small");
+  gemm_selftest(engine, m, n, k, ta ? 1 : 0, tb ? 1 : 0, alpha, A, lda, B, ldb, beta, C, ldc, (cudaStream_t)stream);
   API_END
 }
 
@@ -618,7 +630,7 @@ rsf_status rsf_get_info(rsf_handle h, rsf_info_t* info) {
   info->flops = h->flops;
   info->kernel_evals = h->kevals;
   info->nsets = h->tree_raw->t.nsets;
-  info->solve_df64 = h->df ? 1 : 0;
+  info->solve_df64 = h->df;
   info->probe_rel_diff = h->probe_rel_diff;
   API_END
 }

@@ -54,7 +54,8 @@ enum ProfCat {
   // phases (spans of many launches)
   PROF_PEEL_APPLY = 3, PROF_PEEL_SUB = 4, PROF_PEEL_QR = 5, PROF_PEEL_REST = 6, PROF_FACTOR = 7,
   PROF_GEMM_DF = 8,  // the GEMM kernel in df64 arithmetic (PROF_GEMM: fp64)
-  PROF_NCAT = 9
+  PROF_GEMM_TC = 9,  // the tensor-core GEMM on df64 operands (tcgemm.cu)
+  PROF_NCAT = 10
 };
 // Diagnostics to stderr when the environment variable RSF_VERBOSE is set.
 bool verbose();

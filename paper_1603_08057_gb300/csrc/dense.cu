@@ -41,14 +41,6 @@ constexpr int RM = GEMM_RM, RN = 4;   // register tile of a thread: RM x RN
 constexpr int TM = BM / RM, TN = BN / RN, GT = TM * TN, KUNROLL = GEMM_KUNROLL;
 static_assert((BM * BK) % GT == 0 && (BN * BK) % GT == 0, "tile loads must split evenly");
 
-__device__ __forceinline__ int find_prob(const int* prefix, int nprob, int tile) {
-  int lo = 0, hi = nprob - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (prefix[mid] <= tile) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
 
 // Asynchronous 8-byte global -> shared copy (zero-fill when !pred).
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool pred) {
@@ -215,12 +207,13 @@ __global__ void __launch_bounds__(GT, GEMM_MIN_BLOCKS) gemm_kernel(const GemmDes
 
 void GemmBatch::build(const std::vector<GemmDesc>& d, cudaStream_t s) {
   nprob = (int)d.size();
-  std::vector<int> pre(nprob + 1, 0);
+  std::vector<int> pre(nprob + 1, 0), pre64(nprob + 1, 0);
   maxM = 0;
   anyLaunchM = false;
   fixedMNK = launchNK = fixedBytes = launchBytesPerM = launchBytes0 = 0;
   for (int i = 0; i < nprob; i++) {
     pre[i + 1] = pre[i] + std::max(0, cdiv(d[i].N, BN));
+    pre64[i + 1] = pre64[i] + std::max(0, cdiv(d[i].N, 64));
     if (d[i].M < 0) anyLaunchM = true; else maxM = std::max(maxM, d[i].M);
     // nonzero (k, n) pairs of op(B) and the computed part of C
     double N = d[i].N, K = d[i].K, nk;
@@ -244,8 +237,10 @@ void GemmBatch::build(const std::vector<GemmDesc>& d, cudaStream_t s) {
     }
   }
   ntilesN = pre[nprob];
+  ntilesN64 = pre64[nprob];
   upload(desc, d, s);
   upload(prefix, pre, s);
+  upload(prefix64, pre64, s);
 }
 
 void GemmBatch::run(const GemmBases& b, cudaStream_t s) const {
@@ -256,13 +251,16 @@ void GemmBatch::run(const GemmBases& b, cudaStream_t s) const {
   dim3 grid(ntilesN, cdiv(M, BM));
   RSF_CHECK(grid.y <= 65535, RSF_EINVAL, "gemm: M too large");
   int tok = prof_begin(s);
-  if (b.df)
+  const bool tensor = b.df == 1 && M >= TC_MIN_M;
+  if (tensor)
+    tc_gemm_run(*this, b, M, s);
+  else if (b.df)
     LAUNCH(gemm_kernel<true>, grid, GT, 0, s, desc.as<GemmDesc>(), prefix.as<int>(), nprob, b);
   else
     LAUNCH(gemm_kernel<false>, grid, GT, 0, s, desc.as<GemmDesc>(), prefix.as<int>(), nprob, b);
   if (tok >= 0) {
     double Ml = anyLaunchM ? (double)b.M : 0.0;
-    prof_end(tok, s, b.df ? PROF_GEMM_DF : PROF_GEMM, 2.0 * (fixedMNK + Ml * launchNK),
+    prof_end(tok, s, tensor ? PROF_GEMM_TC : b.df ? PROF_GEMM_DF : PROF_GEMM, 2.0 * (fixedMNK + Ml * launchNK),
              fixedBytes + (anyLaunchM ? launchBytes0 + Ml * launchBytesPerM : 0.0));
   }
 }

@@ -33,21 +33,34 @@ struct GemmDesc {
                    // of a row-major multi-RHS block
 };
 
+// Index of the problem owning tile `tile` given the per-problem tile prefix.
+__device__ __forceinline__ int find_prob(const int* prefix, int nprob, int tile) {
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= tile) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 struct GemmBases {
   double* p[4];
   int64_t sc[4];  // offset multiplier per base (row-major buffers: the row length)
   int M;       // used where desc.M < 0
   int ld;      // used where desc.lda/ldc < 0
   double alpha_scale;  // multiplies every desc.alpha
-  int df;              // 1: operands and result are df64 pairs (df64.cuh)
+  int df;              // nonzero: operands and result are df64 pairs (df64.cuh),
+                       // multiplied on the tensor cores (1, tcgemm.cu) or in
+                       // df64 arithmetic on the CUDA cores (2)
   const int* kidx;     // K index list of descriptors with gatherK
 };
 
 // Device-resident batch of GEMM problems with its tile prefix.
 struct GemmBatch {
-  DBuf desc, prefix;
+  DBuf desc, prefix, prefix64;
   int nprob = 0;
   int ntilesN = 0;   // sum over problems of ceil(N / BN)
+  int ntilesN64 = 0; // the same for the 64-column tiles of the tensor-core kernel
   int maxM = 0;      // max M over problems with M >= 0
   bool anyLaunchM = false;
   // algorithmic work: flops = 2 (fixedMNK + launchM * launchNK), same for bytes
@@ -55,6 +68,18 @@ struct GemmBatch {
   void build(const std::vector<GemmDesc>& d, cudaStream_t s);
   void run(const GemmBases& b, cudaStream_t s) const;
 };
+
+// Tensor-core (tcgen05) engine for df64 batches (tcgemm.cu): runs g with
+// the launch's largest M; tc_status_take returns and clears the engine's
+// device status (RSF_ETIMEOUT when a bounded wait gave up).
+void tc_gemm_run(const GemmBatch& g, const GemmBases& b, int M, cudaStream_t s);
+int tc_status_take();
+void gemm_selftest(int engine, int m, int n, int k, int ta, int tb, double alpha, const double* A, int lda,
+                   const double* B, int ldb, double beta, double* C, int ldc, cudaStream_t s);
+void convert_df64(double* p, int64_t n, int to, cudaStream_t s);
+// Batches whose largest M is below this run on the CUDA-core df64 kernel
+// (a 128-row tensor-core tile would be mostly empty).
+constexpr int TC_MIN_M = 64;
 
 // ----------------------------------------------------------- pivoted QR
 // One problem: A (m x c, column-major, leading dimension lda) at offset a of

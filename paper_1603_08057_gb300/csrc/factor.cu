@@ -828,7 +828,8 @@ void factorize(rsf_handle_s* h) {
       // eps_fact with eps_peel = 1000 eps_fact, so 10 eps_fact keeps the
       // rounding two orders of magnitude below the peeling error of the
       // trace and of the same order as the factorization's own error.
-      h->df = false;
+      const int form = h->df;
+      h->df = 0;
       std::vector<double> hx(n);
       uint64_t st = 0x9E3779B97F4A7C15ull;
       for (int64_t i = 0; i < n; i++) {
@@ -850,7 +851,7 @@ void factorize(rsf_handle_s* h) {
         keep[l] = std::move(Lv.fpool);
         Lv.fpool = std::move(c);
       }
-      h->df = true;
+      h->df = form;
       solve_rows(h, RSF_OP_APPLY, x.as<double>(), ydf.as<double>(), 1, 0);
       double nn = dot_device(y64.as<double>(), y64.as<double>(), n, s);
       LAUNCH(axpy_neg_kernel, cdiv(n, 256), 256, 0, s, ydf.as<double>(), y64.as<double>(), n);
@@ -863,7 +864,7 @@ void factorize(rsf_handle_s* h) {
                 std::sqrt(dd / std::max(nn, 1e-300)), ok ? "df64" : "fp64");
       if (!ok) {
         for (size_t l = 0; l < h->levels.size(); l++) h->levels[l].fpool = std::move(keep[l]);
-        h->df = false;
+        h->df = 0;
       }
     }
   }
@@ -878,6 +879,8 @@ void check_status(rsf_handle_s* h) {
   DevStatus st{};
   d2h(&st, h->status.as<DevStatus>(), 1, h->stream);
   sync(h->stream);
+  const int tcs = tc_status_take();
+  if (tcs != 0) fail((rsf_status)tcs, "tensor-core GEMM: a bounded wait gave up");
   if (st.code != 0) {
     char buf[160];
     snprintf(buf, sizeof buf, "device status %d at level %d box %d (detail %d)", st.code, st.level, st.box,

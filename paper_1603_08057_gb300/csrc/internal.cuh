@@ -147,7 +147,8 @@ struct rsf_handle_s {
   rsf_opts opts;
   double tol = 0;
   bool spd = true;
-  bool df = false;                     // solve factors stored as df64 pairs
+  int df = 0;                          // solve factors: 0 fp64; df64 pairs multiplied on the
+                                       // tensor cores (1) or on the CUDA cores (2)
   cudaStream_t stream = nullptr;
   int device = -1;                     // CUDA device current when the handle was built
   std::vector<rsf::LevelData> levels;  // index = tree level (0 = root)

@@ -79,7 +79,7 @@ void solve_noalloc(rsf_handle_s* h, double* B, int64_t ldb, int nrhs, int op) {
   const int64_t n = h->tree_raw->t.n;
   const int q = nrhs;
   const int L = (int)h->levels.size() - 1;
-  const int df = h->df ? 1 : 0;
+  const int df = h->df;
   const int64_t need = noalloc_need(h, nrhs);
   RSF_CHECK(need <= (int64_t)RSF_NOALLOC_SCRATCH_DOUBLES, RSF_EINVAL,
             "rsf_solve_noalloc: nrhs * (2 n + sum of level rows + largest level) = " + std::to_string(need) +

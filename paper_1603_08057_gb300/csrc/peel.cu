@@ -422,7 +422,7 @@ void peel_traces(rsf_handle_s* F, rsf_handle_s* Fk, bool want0, double tol, cons
   const int c_over = std::max(0, o.oversample);
   DevStatus* dst = F->status.as<DevStatus>();
   int64_t n64 = n;
-  const int df = F->df ? 1 : 0;
+  const int df = F->df;
   std::vector<int> ops;
   if (want0 || !Fk) ops.push_back(0);
   if (Fk) ops.push_back(1);

@@ -147,7 +147,7 @@ void solve_rows(rsf_handle_s* h, int op, const double* in, double* out, int q, i
                 const SparseRHS* skip_out) {
   RSF_CHECK(!skip_out || (skip_out->qc > 0 && q % skip_out->qc == 0), RSF_EINVAL, "column blocks must tile q");
   const int nblk = skip_out ? q / skip_out->qc : 1;
-  const int df = h->df ? 1 : 0;
+  const int df = h->df;
   const int cvt = (df && !io_df) ? 1 : 0;
   RSF_CHECK(!io_df || df, RSF_EINVAL, "df64 input needs a mixed-precision factorization");
   cudaStream_t s = h->stream;

@@ -1,0 +1,574 @@
+// Batched ragged GEMM on the fifth-generation tensor cores (tcgen05) with
+// fp64-class accuracy, for the mixed-precision solves and peeling products
+// (Sec. 2.3.2 applies and solves, Sec. 3 peeling products).
+//
+// Operands and result are df64 pairs (df64.cuh), exactly as for the CUDA-core
+// df64 GEMM; the descriptors are the same GemmDesc batches.  The product is
+// formed from exact bf16 "slices" (the splitting scheme of Ozaki, Ogita,
+// Oishi and Rump, "Error-free transformations of matrix multiplication by
+// using fast routines of matrix multiplication and its applications", Numer.
+// Algorithms 59 (2012), here with bf16 slices and fp32 accumulation):
+//
+//   * per K-block of at most KB = 384 terms, every row m of op(A) gets the
+//     power of two 2^E_m > max_k |A_mk| and every column n of op(B) the power
+//     2^F_n > max_k |B_kn| (computed in a pre-pass over the block);
+//   * a = A_mk / 2^E_m in (-1, 1) is cut into S = 7 slices a_j, each a
+//     multiple of 2^-7(j+1) with at most 8 significant bits (exact in bf16):
+//     a_j = round-to-nearest of the remainder onto the grid 2^-7(j+1); the
+//     remainder after S slices is below 2^-50;
+//   * slice products a_s b_t are exact in fp32 and multiples of
+//     2^-7(s+t+2); all products of one "diagonal" d = s + t share that grid,
+//     so one fp32 TMEM accumulator per diagonal sums them EXACTLY as long as
+//     the integer sum stays below 2^24: |a_0|, |b_0| <= 128 units, later
+//     slices <= 65, so a diagonal gains at most 16640 + 4225 (d - 1) <=
+//     37765 units per term and KB = 384 terms stay below 2^24;
+//   * diagonals d >= S are dropped (the truncation error is ~S 2^-7(S+1) of
+//     2^(E_m+F_n) per term, below the df64 rounding of the inputs);
+//   * the epilogue reads the S diagonals from TMEM, sums them in df64,
+//     scales by 2^(E_m + F_n) and accumulates the K-blocks, then applies
+//     alpha and beta like the CUDA-core df64 kernel.
+//
+// Work split of one CTA (persistent over the tiles of the batch):
+//   * warps 0-7 (256 threads): pre-pass, slicing of the A tile (128 x 32 per
+//     stage) and B tile (64 x 32) into shared memory in the canonical
+//     K-major, no-swizzle core-matrix layout, and the epilogue;
+//   * warp 8: allocates the 512 TMEM columns; its lane 0 issues the
+//     tcgen05.mma instructions (M = 128, N = 64 or 32, K = 16, bf16 x bf16 ->
+//     fp32) into the S accumulators (columns d * 64), and commits to the
+//     mbarriers that free a shared-memory stage and that hand a finished
+//     K-block to the epilogue.
+// Every wait is bounded (a few seconds): on expiry the CTA records
+// RSF_ETIMEOUT, drains its own MMAs, frees its TMEM and returns.
+#include <algorithm>
+#include <cstdio>
+#include <vector>
+
+#include "dense.cuh"
+#include "df64.cuh"
+
+namespace rsf {
+
+namespace tc {
+constexpr int BM = 128, BN = 64, KC = 32, KB = 384, S = 7, NST = 2;
+constexpr int PW = 8;                          // producer / epilogue warps
+constexpr int NPROD = PW * 32;
+constexpr int NTHREADS = NPROD + 32;           // + the MMA warp
+constexpr int A_SLICE = BM * KC * 2;           // bytes of one bf16 slice of an A stage
+constexpr int B_SLICE = BN * KC * 2;
+constexpr int STAGE = S * (A_SLICE + B_SLICE);
+constexpr int A_LBO = (BM / 8) * 128;          // bytes between k-groups of 8 (core matrices)
+constexpr int B_LBO = (BN / 8) * 128;
+constexpr int AUX = 4096;
+constexpr int SMEM = NST * STAGE + AUX + 1024; // + alignment slack
+constexpr unsigned long long WAIT_NS = 4000000000ull;
+static_assert(S * BN <= 512, "the S accumulators must fit the 512 TMEM columns");
+static_assert(KB % KC == 0, "K-blocks hold whole chunks");
+}  // namespace tc
+
+__device__ DevStatus g_tc_status;
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase of the given parity; false on expiry or when
+// another thread of the CTA already gave up.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  uint64_t t0 = 0;
+  for (uint32_t it = 1;; it++) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 63) == 0) {
+      if (*abort_flag) return false;
+      const uint64_t now = gtimer();
+      if (t0 == 0) t0 = now;
+      else if (now - t0 > tc::WAIT_NS) return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void named_sync_producers() {
+  asm volatile("bar.sync 1, %0;" ::"n"(tc::NPROD) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor (tcgen05): start address, leading-dimension
+// byte offset (between core matrices adjacent in K), stride byte offset
+// (between 8-row groups), descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)((lbo & 0x3FFFF) >> 4) << 16;
+  d |= (uint64_t)((sbo & 0x3FFFF) >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t addr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(addr));
+#pragma unroll
+  for (int i = 0; i < 8; i++) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Power of two strictly above every |v| with max |hi| = m (0 for m = 0),
+// clamped to [-126, 126] so that 2^E and 2^-E are normal fp32 numbers
+// (operands of magnitude >= 2^126 are outside this engine's range).
+__device__ __forceinline__ int block_exponent(float m) {
+  if (!(m > 0.f)) return 0;
+  const int e = (int)((__float_as_uint(m) >> 23) & 0xFF) - 126;
+  return e < -126 ? -126 : (e > 126 ? 126 : e);
+}
+__device__ __forceinline__ float pow2f(int e) { return __uint_as_float((uint32_t)(127 + e) << 23); }
+
+// Next slice of the remainder h + l (|h + l| < 2^-7j) on the grid
+// 2^-7(j+1): g = round(h + l) to the grid (adding and subtracting
+// 1.5 x 2^(23 - 7(j+1)) rounds to that grid in one fp32 addition), then the
+// remainder h - g, which is exact (both are multiples of the finer of their
+// grids and the difference is at most half a grid step).
+__device__ __forceinline__ float next_slice(float& h, float l, float magic) {
+  const float t = __fadd_rn(h, l);
+  const float y = __fadd_rn(t, magic);
+  const float g = __fsub_rn(y, magic);
+  h = __fsub_rn(h, g);
+  return g;
+}
+// Two slices (fp32 values with at most 8 significant bits) packed as bf16x2
+// by truncation, which is exact for them: low half the first.
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo_elem, float hi_elem) {
+  return __byte_perm(__float_as_uint(lo_elem), __float_as_uint(hi_elem), 0x7632);
+}
+
+__device__ __forceinline__ float slice_magic(int j) {
+  // 1.5 x 2^(23 - 7 (j + 1))
+  return 1.5f * pow2f(16 - 7 * j);
+}
+
+// Base array i of the launch (a select chain keeps the parameter struct in
+// registers instead of indexing it through local memory).
+__device__ __forceinline__ double* base_ptr(const GemmBases& b, int i) {
+  return i == 0 ? b.p[0] : i == 1 ? b.p[1] : i == 2 ? b.p[2] : b.p[3];
+}
+__device__ __forceinline__ int64_t base_scale(const GemmBases& b, int i) {
+  return i == 0 ? b.sc[0] : i == 1 ? b.sc[1] : i == 2 ? b.sc[2] : b.sc[3];
+}
+
+__global__ void __launch_bounds__(tc::NTHREADS, 1)
+    tc_gemm_kernel(const GemmDesc* __restrict__ descs, const int* __restrict__ prefix, int nprob, int ntilesN,
+                   int mtiles, GemmBases bases) {
+  using namespace tc;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* aux = sm + NST * STAGE;
+  int* sExpA = reinterpret_cast<int*>(aux);                 // [2][BM]
+  int* sExpB = sExpA + 2 * BM;                              // [2][BN]
+  float* sPart = reinterpret_cast<float*>(sExpB + 2 * BN);  // [NPROD]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sPart + NPROD);
+  // bars: full[NST], empty[NST], accf, acce, drain
+  uint32_t* sTmem = reinterpret_cast<uint32_t*>(bars + 2 * NST + 3);
+  volatile int* sAbort = reinterpret_cast<volatile int*>(sTmem + 1);
+  const uint32_t bFull = su32(bars), bEmpty = su32(bars + NST), bAccF = su32(bars + 2 * NST),
+                 bAccE = su32(bars + 2 * NST + 1), bDrain = su32(bars + 2 * NST + 2);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool producer = warp < PW;
+  if (tid == 0) {
+    for (int i = 0; i < NST; i++) {
+      mbar_init(bFull + 8 * i, NPROD);
+      mbar_init(bEmpty + 8 * i, 1);
+    }
+    mbar_init(bAccF, 1);
+    mbar_init(bAccE, NPROD);
+    mbar_init(bDrain, 1);
+    *sAbort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == PW) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(su32(sTmem)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *sTmem;
+
+  uint32_t chunk_ctr = 0, blk_ctr = 0;
+  bool issued = false;   // the MMA thread issued MMAs (drained on abort)
+  const int ntiles = ntilesN * mtiles;
+  for (int tile = blockIdx.x; tile < ntiles && !*sAbort; tile += gridDim.x) {
+    const int tn = tile / mtiles, tm = tile - tn * mtiles;
+    const int p = find_prob(prefix, nprob, tn);
+    const GemmDesc d = descs[p];
+    const int M = d.M >= 0 ? d.M : bases.M;
+    const int N = d.N, K = d.K;
+    const int n0 = (tn - prefix[p]) * BN;
+    const int m0 = tm * BM;
+    if (m0 >= M || n0 >= N) continue;
+    if (d.lowC && n0 > m0 + BM - 1) continue;
+    const int lda = d.lda >= 0 ? d.lda : bases.ld;
+    const int ldb = d.ldb >= 0 ? d.ldb : bases.ld;
+    const int ldc = d.ldc >= 0 ? d.ldc : bases.ld;
+    const double* __restrict__ A = base_ptr(bases, d.abase) + d.a * base_scale(bases, d.abase) + d.m0;
+    const double* __restrict__ Bm = base_ptr(bases, d.bbase) + d.b * base_scale(bases, d.bbase);
+    double* __restrict__ C = base_ptr(bases, d.cbase) + d.c * base_scale(bases, d.cbase) + d.m0;
+    int k0 = 0, k1 = K;
+    if (d.triB == 1) k0 = min(n0, K);
+    if (d.triB == 2) k1 = min(K, n0 + BN);
+    const int nblk = k1 > k0 ? (k1 - k0 + KB - 1) / KB : 0;
+    const int nvalid = min(BN, N - n0);
+    const int nmma = nvalid <= 32 ? 32 : 64;
+    const bool masktri = d.triB != 0 && !d.gatherK && !d.gatherN;
+
+    // element (m, k) of op(A) and (k, n) of op(B) as df64 {hi, lo}
+    auto addrA = [&](int gm, int gk) -> const double* {
+      if (d.gatherK) return A + gm + (int64_t)bases.kidx[d.kofs + gk] * lda;
+      return d.ta ? A + gk + (int64_t)gm * lda : A + gm + (int64_t)gk * lda;
+    };
+    auto addrB = [&](int gk, int gn) -> const double* {
+      if (d.gatherK) return Bm + (bases.kidx[d.kofs + gk] - d.kb0) + (int64_t)gn * ldb;
+      if (d.gatherN) return Bm + (bases.kidx[d.nofs + gn] - d.nb0) + (int64_t)gk * ldb;
+      return d.tb ? Bm + gn + (int64_t)gk * ldb : Bm + gk + (int64_t)gn * ldb;
+    };
+    auto zeroB = [&](int gk, int gn) -> bool {
+      return masktri && ((d.triB == 1 && gk < gn) || (d.triB == 2 && gk > gn));
+    };
+
+    // producer's output: row r (TMEM lane), 32 columns starting at ch * 32
+    const int r = (warp & 3) * 32 + lane;
+    const int ch = (warp >> 2) & 1;
+    float acc_hi[32], acc_lo[32];
+#pragma unroll
+    for (int j = 0; j < 32; j++) acc_hi[j] = acc_lo[j] = 0.f;
+
+    for (int b = 0; b < nblk && !*sAbort; b++, blk_ctr++) {
+      const int kb0 = k0 + b * KB, kb1 = min(k1, kb0 + KB), nk = kb1 - kb0;
+      const int nch = (nk + KC - 1) / KC;
+      const int eb = blk_ctr & 1;
+      if (producer) {
+        // ---- pre-pass: row and column exponents of this K-block
+        {
+          const int rr = tid & (BM - 1), h = tid >> 7;
+          const int gm = m0 + rr;
+          float mx = 0.f;
+          if (gm < M)
+            for (int k = kb0 + h; k < kb1; k += 2) mx = fmaxf(mx, fabsf(*reinterpret_cast<const float*>(addrA(gm, k))));
+          sPart[tid] = mx;
+          named_sync_producers();
+          if (tid < BM) sExpA[eb * BM + tid] = block_exponent(fmaxf(sPart[tid], sPart[tid + BM]));
+          named_sync_producers();
+          const int c = tid & (BN - 1), q = tid >> 6;
+          const int gn = n0 + c;
+          mx = 0.f;
+          if (gn < N)
+            for (int k = kb0 + q; k < kb1; k += 4)
+              if (!zeroB(k, gn)) mx = fmaxf(mx, fabsf(*reinterpret_cast<const float*>(addrB(k, gn))));
+          sPart[tid] = mx;
+          named_sync_producers();
+          if (tid < BN)
+            sExpB[eb * BN + tid] = block_exponent(
+                fmaxf(fmaxf(sPart[tid], sPart[tid + BN]), fmaxf(sPart[tid + 2 * BN], sPart[tid + 3 * BN])));
+          named_sync_producers();
+        }
+        // ---- slice the chunks of the block into the stages
+        for (int c = 0; c < nch; c++) {
+          const uint32_t cc = chunk_ctr + c;
+          const int stage = cc % NST;
+          const uint32_t use = cc / NST;
+          if (use > 0 && !mbar_wait(bEmpty + 8 * stage, (use - 1) & 1, sAbort)) {
+            *sAbort = 1;
+            break;
+          }
+          uint8_t* sA = sm + stage * STAGE;
+          uint8_t* sB = sA + S * A_SLICE;
+          const int ck0 = kb0 + c * KC;
+          {  // A: row rr, k-groups 2 kh and 2 kh + 1 of the chunk
+            const int rr = tid & (BM - 1), kh = tid >> 7;
+            const int gm = m0 + rr;
+            const float sc = pow2f(-sExpA[eb * BM + rr]);
+            float2 v[16];
+#pragma unroll
+            for (int i = 0; i < 16; i++) {
+              const int k = ck0 + kh * 16 + i;
+              v[i] = (gm < M && k < kb1) ? *reinterpret_cast<const float2*>(addrA(gm, k)) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int g = 0; g < 2; g++) {
+              float hh[8], ll[8];
+#pragma unroll
+              for (int i = 0; i < 8; i++) {
+                hh[i] = v[g * 8 + i].x * sc;
+                ll[i] = v[g * 8 + i].y * sc;
+              }
+              uint8_t* dst = sA + (kh * 2 + g) * A_LBO + (rr >> 3) * 128 + (rr & 7) * 16;
+#pragma unroll
+              for (int j = 0; j < S; j++) {
+                const float mg = slice_magic(j);
+                float s8[8];
+#pragma unroll
+                for (int i = 0; i < 8; i++) s8[i] = next_slice(hh[i], ll[i], mg);
+                uint4 w;
+                w.x = pack_bf16x2(s8[0], s8[1]);
+                w.y = pack_bf16x2(s8[2], s8[3]);
+                w.z = pack_bf16x2(s8[4], s8[5]);
+                w.w = pack_bf16x2(s8[6], s8[7]);
+                *reinterpret_cast<uint4*>(dst + j * A_SLICE) = w;
+              }
+            }
+          }
+          {  // B: column cn, k-group kq of the chunk
+            const int cn = tid & (BN - 1), kq = tid >> 6;
+            const int gn = n0 + cn;
+            const float sc = pow2f(-sExpB[eb * BN + cn]);
+            float hh[8], ll[8];
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+              const int k = ck0 + kq * 8 + i;
+              float2 v = make_float2(0.f, 0.f);
+              if (gn < N && k < kb1 && !zeroB(k, gn)) v = *reinterpret_cast<const float2*>(addrB(k, gn));
+              hh[i] = v.x * sc;
+              ll[i] = v.y * sc;
+            }
+            uint8_t* dst = sB + kq * B_LBO + (cn >> 3) * 128 + (cn & 7) * 16;
+#pragma unroll
+            for (int j = 0; j < S; j++) {
+              const float mg = slice_magic(j);
+              float s8[8];
+#pragma unroll
+              for (int i = 0; i < 8; i++) s8[i] = next_slice(hh[i], ll[i], mg);
+              uint4 w;
+              w.x = pack_bf16x2(s8[0], s8[1]);
+              w.y = pack_bf16x2(s8[2], s8[3]);
+              w.z = pack_bf16x2(s8[4], s8[5]);
+              w.w = pack_bf16x2(s8[6], s8[7]);
+              *reinterpret_cast<uint4*>(dst + j * B_SLICE) = w;
+            }
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          mbar_arrive(bFull + 8 * stage);
+        }
+        if (*sAbort) break;
+        // ---- epilogue of the block: S diagonals -> df64, scaled, accumulated
+        if (!mbar_wait(bAccF, blk_ctr & 1, sAbort)) {
+          *sAbort = 1;
+          break;
+        }
+        tc_fence_after();
+        const float scr = pow2f(sExpA[eb * BM + r]);
+        const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+#pragma unroll
+        for (int q8 = 0; q8 < 4; q8++) {
+          const int col = ch * 32 + q8 * 8;
+          if (col < nmma) {
+            float D[S][8];
+#pragma unroll
+            for (int dd = 0; dd < S; dd++) tmem_ld8(tl + dd * BN + col, D[dd]);
+            tmem_ld_wait();
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+              // exact-ish sum of the diagonals (TwoSum into hi, errors into lo)
+              float hi = D[0][j], lo = 0.f;
+#pragma unroll
+              for (int dd = 1; dd < S; dd++) {
+                const float x = D[dd][j];
+                const float s = __fadd_rn(hi, x);
+                const float v = __fsub_rn(s, hi);
+                lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(s, v)), __fsub_rn(x, v)));
+                hi = s;
+              }
+              const float scn = pow2f(sExpB[eb * BN + col + j]);
+              df64 t = df_fast_two_sum(hi, lo);
+              t.hi = (t.hi * scr) * scn;
+              t.lo = (t.lo * scr) * scn;
+              df64 a = {acc_hi[q8 * 8 + j], acc_lo[q8 * 8 + j]};
+              a = df_add(a, t);
+              acc_hi[q8 * 8 + j] = a.hi;
+              acc_lo[q8 * 8 + j] = a.lo;
+            }
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(bAccE);
+      } else if (warp == PW && lane == 0) {
+        // ---- MMA issue
+        if (blk_ctr > 0 && !mbar_wait(bAccE, (blk_ctr - 1) & 1, sAbort)) {
+          *sAbort = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(nmma >> 3) << 17) |
+                               ((uint32_t)(BM >> 4) << 24);
+        uint32_t inited = 0;
+        for (int c = 0; c < nch; c++) {
+          const uint32_t cc = chunk_ctr + c;
+          const int stage = cc % NST;
+          if (!mbar_wait(bFull + 8 * stage, (cc / NST) & 1, sAbort)) {
+            *sAbort = 1;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t aBase = su32(sm + stage * STAGE), bBase = aBase + S * A_SLICE;
+          const int ksteps = (min(KC, nk - c * KC) + 15) / 16;
+          for (int kk = 0; kk < ksteps; kk++) {
+#pragma unroll
+            for (int s = 0; s < S; s++) {
+              const uint64_t ad = smem_desc(aBase + s * A_SLICE + kk * 2 * A_LBO, A_LBO, 128);
+#pragma unroll
+              for (int t = 0; t < S - s; t++) {
+                const int dd = s + t;
+                const uint64_t bd = smem_desc(bBase + t * B_SLICE + kk * 2 * B_LBO, B_LBO, 128);
+                mma_bf16(tmem + dd * BN, ad, bd, idesc, (inited >> dd) & 1u);
+                inited |= 1u << dd;
+              }
+            }
+          }
+          issued = true;
+          mma_commit(bEmpty + 8 * stage);
+        }
+        if (*sAbort) break;
+        mma_commit(bAccF);
+      }
+      chunk_ctr += nch;
+    }
+    if (*sAbort) break;
+    if (producer) {
+      // ---- C = alpha * acc + beta * C (df64), like the CUDA-core kernel
+      const int gm = m0 + r;
+      const double alpha = d.alpha * bases.alpha_scale, beta = d.beta;
+      if (gm < M) {
+#pragma unroll
+        for (int j = 0; j < 32; j++) {
+          const int gn = n0 + ch * 32 + j;
+          if (gn >= N || (d.lowC && gm < gn)) continue;
+          const int64_t cn = d.gatherN ? (int64_t)bases.kidx[d.nofs + gn] : (int64_t)gn;
+          double* pcc = C + gm + cn * ldc;
+          df64 v = df_scale(df_fast_two_sum(acc_hi[j], acc_lo[j]), (float)alpha);
+          if (beta != 0.0) {
+            const float2 o = *reinterpret_cast<const float2*>(pcc);
+            df64 old = {o.x, o.y};
+            if (beta != 1.0) old = df_scale(old, (float)beta);
+            v = df_add(v, old);
+          }
+          *reinterpret_cast<float2*>(pcc) = make_float2(v.hi, v.lo);
+        }
+      }
+    }
+  }
+
+  // ---- teardown: on abort record the timeout and drain this CTA's MMAs
+  if (*sAbort && tid == 0) report(&g_tc_status, RSF_ETIMEOUT, -1, blockIdx.x, 0);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == PW) {
+    if (lane == 0 && *sAbort && issued) {
+      mma_commit(bDrain);
+      volatile int never = 0;
+      mbar_wait(bDrain, 0, &never);
+    }
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+  }
+}
+
+// ------------------------------------------------------------------ host
+static int tc_sm_count() {
+  static int cnt[64] = {0};
+  int dev = 0;
+  RSF_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!cnt[dev]) {
+    RSF_CUDA(cudaDeviceGetAttribute(&cnt[dev], cudaDevAttrMultiProcessorCount, dev));
+    RSF_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM));
+  }
+  return cnt[dev];
+}
+
+void tc_gemm_run(const GemmBatch& g, const GemmBases& b, int M, cudaStream_t s) {
+  const int mtiles = cdiv(M, tc::BM);
+  const int64_t ntiles = (int64_t)g.ntilesN64 * mtiles;
+  if (ntiles == 0) return;
+  RSF_CHECK(ntiles < (1ll << 31), RSF_EINVAL, "tensor-core gemm: too many tiles");
+  const int grid = (int)std::min<int64_t>(ntiles, tc_sm_count());
+  LAUNCH(tc_gemm_kernel, grid, tc::NTHREADS, tc::SMEM, s, g.desc.as<GemmDesc>(), g.prefix64.as<int>(), g.nprob,
+         g.ntilesN64, mtiles, b);
+}
+
+// One column-major GEMM through a batch engine, for the self-check entry
+// point: operands are copied (and converted to df64 pairs for engines 1 and
+// 2) into stream-ordered work buffers.
+void gemm_selftest(int engine, int m, int n, int k, int ta, int tb, double alpha, const double* A, int lda,
+                   const double* B, int ldb, double beta, double* C, int ldc, cudaStream_t s) {
+  const int64_t acols = ta ? m : k, bcols = tb ? k : n;
+  DBuf a, bb, c;
+  a.alloc(sizeof(double) * std::max<int64_t>(1, (int64_t)lda * acols), s);
+  bb.alloc(sizeof(double) * std::max<int64_t>(1, (int64_t)ldb * bcols), s);
+  c.alloc(sizeof(double) * std::max<int64_t>(1, (int64_t)ldc * n), s);
+  RSF_CUDA(cudaMemcpyAsync(a.p, A, sizeof(double) * lda * acols, cudaMemcpyDeviceToDevice, s));
+  RSF_CUDA(cudaMemcpyAsync(bb.p, B, sizeof(double) * ldb * bcols, cudaMemcpyDeviceToDevice, s));
+  RSF_CUDA(cudaMemcpyAsync(c.p, C, sizeof(double) * ldc * n, cudaMemcpyDeviceToDevice, s));
+  if (engine) {
+    convert_df64(a.as<double>(), (int64_t)lda * acols, 1, s);
+    convert_df64(bb.as<double>(), (int64_t)ldb * bcols, 1, s);
+    convert_df64(c.as<double>(), (int64_t)ldc * n, 1, s);
+  }
+  GemmDesc d{};
+  d.M = m; d.N = n; d.K = k;
+  d.lda = lda; d.ldb = ldb; d.ldc = ldc;
+  d.a = 0; d.b = 0; d.c = 0;
+  d.abase = 0; d.bbase = 1; d.cbase = 2;
+  d.ta = (int8_t)ta; d.tb = (int8_t)tb;
+  d.alpha = alpha; d.beta = beta;
+  GemmBatch g;
+  g.build(std::vector<GemmDesc>{d}, s);
+  GemmBases b{};
+  b.p[0] = a.as<double>(); b.p[1] = bb.as<double>(); b.p[2] = c.as<double>(); b.p[3] = nullptr;
+  b.sc[0] = b.sc[1] = b.sc[2] = b.sc[3] = 1;
+  b.M = m; b.ld = ldc; b.alpha_scale = 1.0; b.df = engine;
+  g.run(b, s);
+  if (engine) convert_df64(c.as<double>(), (int64_t)ldc * n, 0, s);
+  RSF_CUDA(cudaMemcpyAsync(C, c.p, sizeof(double) * ldc * n, cudaMemcpyDeviceToDevice, s));
+  sync(s);
+  const int tcs = tc_status_take();
+  RSF_CHECK(tcs == 0, (rsf_status)tcs, "tensor-core GEMM: a bounded wait gave up");
+}
+
+int tc_status_take() {
+  DevStatus h{}, z{};
+  RSF_CUDA(cudaMemcpyFromSymbol(&h, g_tc_status, sizeof(DevStatus)));
+  if (h.code != 0) RSF_CUDA(cudaMemcpyToSymbol(g_tc_status, &z, sizeof(DevStatus)));
+  return h.code;
+}
+
+}  // namespace rsf

@@ -1,0 +1,64 @@
+"""The batched-GEMM engines behind the solves and the peeling (Sec. 2.3.2
+applies and solves, Sec. 3 products), checked element by element through
+the C ABI (rsf_selftest_gemm) against NumPy's fp64 product.
+
+Engine 1 multiplies df64 operands on the tensor cores from exact bf16 slices
+(seven per operand, exact fp32 accumulation per diagonal of slice products,
+K-blocks of 384).  Its result must match the exact product to the df64
+rounding of the operands: each operand is rounded to a 48-bit significand
+(relative 2^-48 = 3.6e-15) and the slices keep 7 x 7 bits below the block's
+largest power of two, so |C - AB| <= 1e-13 sum_k |A_ik||B_kj| + the same
+bound on the beta C term.  Engine 2 (df64 on the CUDA cores) meets the same
+bar, engine 0 (fp64) the classical k u.  Shapes span several tiles with ragged
+tails in m, n and k, more than one K-block, transposed operands, and rows
+and columns whose magnitudes differ by up to 1e6 (one power of two per row
+and K-block must still leave every element its full precision relative to
+the largest one).
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1603_08057_gb300 import build
+    build.build()
+    from paper_1603_08057_gb300 import binding
+    return binding
+
+
+def _mats(m, n, k, ta, tb, seed, spread):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((m, k)) * 10.0 ** rng.uniform(-spread, spread, (m, 1))
+    Bm = rng.standard_normal((k, n)) * 10.0 ** rng.uniform(-spread, spread, (1, n))
+    C = rng.standard_normal((m, n))
+    return (A.T.copy() if ta else A), (Bm.T.copy() if tb else Bm), C, A, Bm
+
+
+# (m, n, k) of C = op(A) op(B); the library sees the column-major transpose,
+# whose row count is n: n >= 64 runs on the tensor cores, n < 64 on engine 2.
+SHAPES = [(128, 64, 32), (200, 70, 45), (129, 33, 1), (300, 130, 1000), (1000, 257, 384), (64, 200, 17),
+          (513, 64, 385), (40, 100, 50), (20, 150, 64)]
+
+
+@pytest.mark.parametrize("engine", [1, 2, 0])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_engine_matches_numpy(B, engine, shape):
+    m, n, k = shape
+    for ta, tb, alpha, beta, spread in ((0, 0, 1.0, 0.0, 0.0), (1, 0, -1.0, 1.0, 3.0), (0, 1, 0.5, 1.0, 3.0),
+                                        (1, 1, 1.0, -2.0, 1.0)):
+        Aop, Bop, C, A, Bm = _mats(m, n, k, ta, tb, 1000 * m + 10 * n + k + 3 * ta + tb, spread)
+        T = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda")  # noqa: E731
+        got = B.selftest_gemm(engine, T(Aop), T(Bop), T(C), bool(ta), bool(tb), alpha, beta).cpu().numpy()
+        ref = alpha * (A @ Bm) + beta * C
+        bound = abs(alpha) * (np.abs(A) @ np.abs(Bm)) + abs(beta) * np.abs(C)
+        err = np.max(np.abs(got - ref) / bound)
+        print(f"engine {engine} {shape} ta={ta} tb={tb}: max |err| / (|A||B| + |C|) = {err:.3e}")
+        # fp64: k u (the classical bound); df64 engines: 1e-13 (see above)
+        assert err <= (2.3e-16 * max(k, 2) if engine == 0 else 1e-13)

@@ -2,9 +2,12 @@
 
 Tolerances (derived from the arithmetic):
 * exact identities of the computed factors (F^-1 F = I, F^1/2 F^1/2^T = F):
-  rounding only, kappa(F) u with kappa <~ 1e4 here: 1e-10 relative in both
-  forms (fp64, u = 2^-53; mixed, whose solve products carry df64 pairs,
-  u = 2^-48 -> 1e4 x 3.6e-15 = 4e-11);
+  rounding only, g kappa(F) u with kappa <~ 1e4 here and a growth g of the
+  order of the number of GEMM passes of a solve (about 2 per level, 10-15):
+  1e-10 relative in fp64 (u = 2^-53; measured 1.1e-12) and 1e-9 in the
+  mixed forms, whose solve operands are df64 pairs (u = 2^-48 = 3.6e-15:
+  1e4 x 3.6e-15 x 15 = 5e-10; measured 2.3e-10 on 3,000 uniform points and
+  1.0e-10 on 3,000 clustered points with df64 products on the CUDA cores);
 * F vs Sigma: the ID tolerance eps_fact = 1e-9 with modest growth -> 1e-8;
 * log|F| vs log|Sigma|, log-likelihood vs dense: the acceptance bar 1e-6
   relative at eps_fact = 1e-9;
@@ -77,7 +80,7 @@ def test_solve_inverts_apply(B, uni):
     Y = F.solve(F.solve(T(V), B.OP_APPLY), B.OP_INV).cpu().numpy()
     err = np.max(np.abs(Y - V)) / np.max(np.abs(V))
     print(f"F^-1 F V - V: {err:.3e}")
-    assert err <= 1e-10
+    assert err <= 1e-9      # default (mixed) form
 
 
 def test_square_root_identities(B, uni):
@@ -91,7 +94,7 @@ def test_square_root_identities(B, uni):
     I2 = F.solve(F.solve(T(E), B.OP_SQRT_T), B.OP_INV_SQRT_T).cpu().numpy()
     e1, e2 = np.max(np.abs(I1 - E)), np.max(np.abs(I2 - E))
     print(f"F^1/2 F^-1/2 - I: {e1:.3e}, F^-T/2 F^T/2 - I: {e2:.3e}")
-    assert e1 <= 1e-10 and e2 <= 1e-10
+    assert e1 <= 1e-9 and e2 <= 1e-9
 
 
 def test_logdet_matches_dense(B, uni):
@@ -266,9 +269,10 @@ def test_invalid_arguments_raise(B):
     assert e.value.code == 1
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_precision_modes_match_dense(B, prec):
-    # plain fp64 (0) and mixed df64 solves/peeling (1) both meet the bars
+    # plain fp64 (0) and the mixed forms (df64 operands; products on the
+    # tensor cores (1) or the CUDA cores (2)) all meet the bars
     x = W.mixture(3000, 201)
     th = (0.05, 2.0, 1e-2)
     z = dense.sample_z_dense(x, K.MATERN32, th, W.standard_normal(3000, 202))
@@ -283,18 +287,19 @@ def test_precision_modes_match_dense(B, prec):
     Y = F.solve(F.solve(T(V), B.OP_APPLY), B.OP_INV).cpu().numpy()
     err = np.max(np.abs(Y - V)) / np.max(np.abs(V))
     print(f"precision {prec}: F^-1 F V - V: {err:.3e}")
-    assert err <= 1e-10
+    assert err <= (1e-10 if prec == 0 else 1e-9)
 
 
 def test_mixed_close_to_fp64(B):
     x = W.uniform(2500, 211)
     th = (0.1, 1.0, 1e-2)
     F0 = B.Factorization(T(x), B.MATERN32, th, B.SIGMA, 1e-9, 0.0, B.opts(precision=0))
-    F1 = B.Factorization(T(x), B.MATERN32, th, B.SIGMA, 1e-9, 0.0, B.opts(precision=1))
     V = T(W.standard_normal(2500, 212, 3))
-    for op in (B.OP_INV, B.OP_APPLY, B.OP_SQRT, B.OP_INV_SQRT_T):
-        a, b = F0.solve(V, op), F1.solve(V, op)
-        err = torch.max(torch.abs(a - b)).item() / torch.max(torch.abs(a)).item()
-        print(f"op {op}: mixed vs fp64 {err:.3e}")
-        assert err <= 1e-10
-    assert F0.logdet() == F1.logdet()
+    for prec in (1, 2):
+        F1 = B.Factorization(T(x), B.MATERN32, th, B.SIGMA, 1e-9, 0.0, B.opts(precision=prec))
+        for op in (B.OP_INV, B.OP_APPLY, B.OP_SQRT, B.OP_INV_SQRT_T):
+            a, b = F0.solve(V, op), F1.solve(V, op)
+            err = torch.max(torch.abs(a - b)).item() / torch.max(torch.abs(a)).item()
+            print(f"precision {prec} op {op}: mixed vs fp64 {err:.3e}")
+            assert err <= 1e-10
+        assert F0.logdet() == F1.logdet()
