@@ -112,6 +112,14 @@ typedef struct {
                        G = F^-1/2 F_k F^-T/2 and, for Tr(F^-1),
                        F^-1/2 F^-T/2, with F = F^1/2 (F^1/2)^T of Sec. 2.3.2:
                        half the solve passes per test column */
+  int refine;       /* sweeps of iterative refinement of alpha = Sigma^-1 z
+                       in gp_loglik (Algorithm 1, first line): alpha +=
+                       F^-1 (z - Sigma alpha), the residual taken against
+                       the exact kernel matrix by an on-the-fly O(n^2)
+                       matvec (df64 on the fp32 pipes for the Matern
+                       families, fp64 otherwise), so that z^T alpha does
+                       not carry the factorization's eps_fact error.
+                       -1 (default): 1 in the mixed forms, 0 in fp64 */
 } rsf_opts;
 
 enum { RSF_TRACE_SYM = 0, RSF_TRACE_SQRT = 1 };

@@ -203,6 +203,7 @@ static rsf_opts resolve_opts(const rsf_opts* o) {
   if (o) r = *o;
   RSF_CHECK(r.trace_form == RSF_TRACE_SYM || r.trace_form == RSF_TRACE_SQRT, RSF_EINVAL,
             "trace_form must be RSF_TRACE_SYM or RSF_TRACE_SQRT");
+  RSF_CHECK(r.refine >= -1 && r.refine <= 8, RSF_EINVAL, "refine must be in -1 .. 8");
   return r;
 }
 
@@ -247,6 +248,11 @@ static rsf_handle_s* make_handle(std::shared_ptr<rsf_tree_s> tree, const rsf_ker
   return h.release();
 }
 
+int refine_sweeps(const rsf_handle_s* F) {
+  if (!F->spd) return 0;
+  return F->opts.refine >= 0 ? F->opts.refine : (F->opts.precision != RSF_PREC_FP64 ? 1 : 0);
+}
+
 }  // namespace rsf
 
 using namespace rsf;
@@ -284,6 +290,7 @@ void rsf_opts_default(rsf_opts* o) {
   o->seed = 0;
   o->precision = RSF_PREC_MIXED;
   o->trace_form = RSF_TRACE_SYM;
+  o->refine = -1;
 }
 
 const char* rsf_last_error(void) { return g_err.c_str(); }
@@ -390,6 +397,18 @@ static void loglik_sets(rsf_handle_s* F, const double* z, double* alpha_out, DBu
   sc.zero();
   LAUNCH(to_tree_kernel, cdiv(n, 256), 256, 0, s, z, n, 1, perm, n, zt.as<double>());
   solve_rows(F, RSF_OP_INV, zt.as<double>(), at.as<double>(), 1);
+  // iterative refinement against the exact Sigma: alpha += F^-1 (z - Sigma alpha)
+  const int sweeps = refine_sweeps(F);
+  if (sweeps > 0) {
+    DBuf rt, dt;
+    rt.alloc(sizeof(double) * n, s);
+    dt.alloc(sizeof(double) * n, s);
+    for (int k = 0; k < sweeps; k++) {
+      kernel_residual(F, zt.as<double>(), at.as<double>(), rt.as<double>());
+      solve_rows(F, RSF_OP_INV, rt.as<double>(), dt.as<double>(), 1);
+      add_into(at.as<double>(), dt.as<double>(), n, s);
+    }
+  }
   for (int i = 0; i < T.nsets; i++) {
     const int64_t r0 = T.set_off[i], cnt = T.set_off[i + 1] - r0;
     dot_into(zt.as<double>() + r0, at.as<double>() + r0, cnt, sc.as<double>() + (int64_t)i * S_NSLOTS + S_QUAD, s);

@@ -195,6 +195,12 @@ void convert_df64(double* p, int64_t n, int to, cudaStream_t s);
 // d_out[i] may be null) and to h_sets[i * nsets + j] (host, may be null).
 void peel_traces(rsf_handle_s* F, rsf_handle_s* Fk, bool want0, double tol, const rsf_opts& o,
                  double* const d_out[2], int64_t d_stride, double* h_sets);
+// r = z - Sigma x in tree order (exact kernel, on the fly; df64 for the
+// Matern families unless force_fp64), and y += x.
+void kernel_residual(rsf_handle_s* F, const double* zt, const double* x, double* rt, int force_fp64 = 0);
+void add_into(double* y, const double* x, int64_t n, cudaStream_t s);
+// Iterative-refinement sweeps of Sigma^-1 z that gp_loglik runs for handle F.
+int refine_sweeps(const rsf_handle_s* F);
 // device reductions
 double dot_device(const double* a, const double* b, int64_t n, cudaStream_t s);
 // a . b into a device scalar (stream ordered, no synchronisation)
