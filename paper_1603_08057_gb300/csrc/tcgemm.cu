@@ -28,15 +28,17 @@
 //     scales by 2^(E_m + F_n) and accumulates the K-blocks, then applies
 //     alpha and beta like the CUDA-core df64 kernel.
 //
-// Work split of one CTA (persistent over the tiles of the batch):
-//   * warps 0-7 (256 threads): pre-pass, slicing of the A tile (128 x 32 per
-//     stage) and B tile (64 x 32) into shared memory in the canonical
-//     K-major, no-swizzle core-matrix layout, and the epilogue;
-//   * warp 8: allocates the 512 TMEM columns; its lane 0 issues the
-//     tcgen05.mma instructions (M = 128, N = 64 or 32, K = 16, bf16 x bf16 ->
-//     fp32) into the S accumulators (columns d * 64), and commits to the
-//     mbarriers that free a shared-memory stage and that hand a finished
-//     K-block to the epilogue.
+// Work split of one CTA (persistent over the tiles of the batch; 8 warps,
+// two per SM sub-partition, so each thread may hold up to 255 registers):
+//   * all 256 threads: pre-pass, slicing of the A tile (128 x 32 per stage)
+//     and B tile (64 x 32) into shared memory in the canonical K-major,
+//     no-swizzle core-matrix layout (the next chunk's loads in flight while
+//     the current one is sliced), and the epilogue;
+//   * warp 0 allocates the 512 TMEM columns; thread 0 issues, once every
+//     thread has sliced a chunk, its tcgen05.mma instructions (M = 128,
+//     N = 64 or 32, K = 16, bf16 x bf16 -> fp32) into the S accumulators
+//     (columns d * 64), and commits to the mbarriers that free the
+//     shared-memory stage and that hand a finished K-block to the epilogue.
 // Every wait is bounded (a few seconds): on expiry the CTA records
 // RSF_ETIMEOUT, drains its own MMAs, frees its TMEM and returns.
 #include <algorithm>
@@ -50,9 +52,9 @@ namespace rsf {
 
 namespace tc {
 constexpr int BM = 128, BN = 64, KC = 32, KB = 384, S = 7, NST = 2;
-constexpr int PW = 8;                          // producer / epilogue warps
+constexpr int PW = 8;                          // warps: slicing, MMA issue (thread 0), epilogue
 constexpr int NPROD = PW * 32;
-constexpr int NTHREADS = NPROD + 32;           // + the MMA warp
+constexpr int NTHREADS = NPROD;                // 2 warps per SM sub-partition: up to 255 registers
 constexpr int A_SLICE = BM * KC * 2;           // bytes of one bf16 slice of an A stage
 constexpr int B_SLICE = BN * KC * 2;
 constexpr int STAGE = S * (A_SLICE + B_SLICE);
@@ -176,6 +178,24 @@ __device__ __forceinline__ float slice_magic(int j) {
   return 1.5f * pow2f(16 - 7 * j);
 }
 
+// The S slices of 8 consecutive k of one row: slice j as 8 bf16 (16 bytes,
+// one core-matrix row) at dst + j * slice_bytes.
+__device__ __forceinline__ void slice_store(float (&hh)[8], const float (&ll)[8], uint8_t* dst, int slice_bytes) {
+#pragma unroll
+  for (int j = 0; j < tc::S; j++) {
+    const float mg = slice_magic(j);
+    float s8[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) s8[i] = next_slice(hh[i], ll[i], mg);
+    uint4 w;
+    w.x = pack_bf16x2(s8[0], s8[1]);
+    w.y = pack_bf16x2(s8[2], s8[3]);
+    w.z = pack_bf16x2(s8[4], s8[5]);
+    w.w = pack_bf16x2(s8[6], s8[7]);
+    *reinterpret_cast<uint4*>(dst + j * slice_bytes) = w;
+  }
+}
+
 // Base array i of the launch (a select chain keeps the parameter struct in
 // registers instead of indexing it through local memory).
 __device__ __forceinline__ double* base_ptr(const GemmBases& b, int i) {
@@ -200,22 +220,21 @@ __global__ void __launch_bounds__(tc::NTHREADS, 1)
   uint32_t* sTmem = reinterpret_cast<uint32_t*>(bars + 2 * NST + 3);
   volatile int* sAbort = reinterpret_cast<volatile int*>(sTmem + 1);
   const uint32_t bFull = su32(bars), bEmpty = su32(bars + NST), bAccF = su32(bars + 2 * NST),
-                 bAccE = su32(bars + 2 * NST + 1), bDrain = su32(bars + 2 * NST + 2);
+                 bDrain = su32(bars + 2 * NST + 2);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const bool producer = warp < PW;
+  const bool producer = true;
   if (tid == 0) {
     for (int i = 0; i < NST; i++) {
       mbar_init(bFull + 8 * i, NPROD);
       mbar_init(bEmpty + 8 * i, 1);
     }
     mbar_init(bAccF, 1);
-    mbar_init(bAccE, NPROD);
     mbar_init(bDrain, 1);
     *sAbort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == PW) {
+  if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(su32(sTmem)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
@@ -268,32 +287,69 @@ __global__ void __launch_bounds__(tc::NTHREADS, 1)
     // producer's output: row r (TMEM lane), 32 columns starting at ch * 32
     const int r = (warp & 3) * 32 + lane;
     const int ch = (warp >> 2) & 1;
-    float acc_hi[32], acc_lo[32];
+    const double alpha = d.alpha * bases.alpha_scale, beta = d.beta;
+    // loads of one chunk (k from ck0): A row rr, k = ck0 + kh * 16 + i;
+    // B column cn, k = ck0 + kq * 8 + i (zero outside the block and the masks)
+    const int rr = tid & (BM - 1), kh = (tid >> 7) & 1;
+    const int cn = tid & (BN - 1), kq = (tid >> 6) & 3;
+    auto load_chunk = [&](int ck0, int kend, float2 (&va)[16], float2 (&vb)[8]) {
+      const int gm = m0 + rr, gn = n0 + cn;
 #pragma unroll
-    for (int j = 0; j < 32; j++) acc_hi[j] = acc_lo[j] = 0.f;
+      for (int i = 0; i < 16; i++) {
+        const int k = ck0 + kh * 16 + i;
+        va[i] = (gm < M && k < kend) ? *reinterpret_cast<const float2*>(addrA(gm, k)) : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int i = 0; i < 8; i++) {
+        const int k = ck0 + kq * 8 + i;
+        vb[i] = (gn < N && k < kend && !zeroB(k, gn)) ? *reinterpret_cast<const float2*>(addrB(k, gn))
+                                                      : make_float2(0.f, 0.f);
+      }
+    };
 
     for (int b = 0; b < nblk && !*sAbort; b++, blk_ctr++) {
       const int kb0 = k0 + b * KB, kb1 = min(k1, kb0 + KB), nk = kb1 - kb0;
       const int nch = (nk + KC - 1) / KC;
       const int eb = blk_ctr & 1;
       if (producer) {
-        // ---- pre-pass: row and column exponents of this K-block
+        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(nmma >> 3) << 17) |
+                               ((uint32_t)(BM >> 4) << 24);
+        uint32_t inited = 0;   // thread 0: diagonals written in this block
+        // ---- pre-pass: row and column exponents of this K-block (batches of
+        // 16 independent loads per thread keep the memory pipe busy)
         {
-          const int rr = tid & (BM - 1), h = tid >> 7;
+          const int h = tid >> 7;
           const int gm = m0 + rr;
           float mx = 0.f;
           if (gm < M)
-            for (int k = kb0 + h; k < kb1; k += 2) mx = fmaxf(mx, fabsf(*reinterpret_cast<const float*>(addrA(gm, k))));
+            for (int kb = kb0 + h; kb < kb1; kb += 32) {
+              float v[16];
+#pragma unroll
+              for (int i = 0; i < 16; i++) {
+                const int k = kb + 2 * i;
+                v[i] = k < kb1 ? fabsf(*reinterpret_cast<const float*>(addrA(gm, k))) : 0.f;
+              }
+#pragma unroll
+              for (int i = 0; i < 16; i++) mx = fmaxf(mx, v[i]);
+            }
           sPart[tid] = mx;
           named_sync_producers();
           if (tid < BM) sExpA[eb * BM + tid] = block_exponent(fmaxf(sPart[tid], sPart[tid + BM]));
           named_sync_producers();
-          const int c = tid & (BN - 1), q = tid >> 6;
-          const int gn = n0 + c;
+          const int q = tid >> 6;
+          const int gn = n0 + cn;
           mx = 0.f;
           if (gn < N)
-            for (int k = kb0 + q; k < kb1; k += 4)
-              if (!zeroB(k, gn)) mx = fmaxf(mx, fabsf(*reinterpret_cast<const float*>(addrB(k, gn))));
+            for (int kb = kb0 + q; kb < kb1; kb += 64) {
+              float v[16];
+#pragma unroll
+              for (int i = 0; i < 16; i++) {
+                const int k = kb + 4 * i;
+                v[i] = (k < kb1 && !zeroB(k, gn)) ? fabsf(*reinterpret_cast<const float*>(addrB(k, gn))) : 0.f;
+              }
+#pragma unroll
+              for (int i = 0; i < 16; i++) mx = fmaxf(mx, v[i]);
+            }
           sPart[tid] = mx;
           named_sync_producers();
           if (tid < BN)
@@ -301,85 +357,87 @@ __global__ void __launch_bounds__(tc::NTHREADS, 1)
                 fmaxf(fmaxf(sPart[tid], sPart[tid + BN]), fmaxf(sPart[tid + 2 * BN], sPart[tid + 3 * BN])));
           named_sync_producers();
         }
-        // ---- slice the chunks of the block into the stages
+        // ---- slice the chunks of the block into the stages; the loads of
+        // chunk c + 1 are issued before chunk c is sliced
+        float2 va[16], vb[8];
+        load_chunk(kb0, kb1, va, vb);
         for (int c = 0; c < nch; c++) {
           const uint32_t cc = chunk_ctr + c;
           const int stage = cc % NST;
           const uint32_t use = cc / NST;
+          float2 na[16], nb[8];
+          const bool more = c + 1 < nch;
+          if (more) load_chunk(kb0 + (c + 1) * KC, kb1, na, nb);
           if (use > 0 && !mbar_wait(bEmpty + 8 * stage, (use - 1) & 1, sAbort)) {
             *sAbort = 1;
             break;
           }
           uint8_t* sA = sm + stage * STAGE;
           uint8_t* sB = sA + S * A_SLICE;
-          const int ck0 = kb0 + c * KC;
           {  // A: row rr, k-groups 2 kh and 2 kh + 1 of the chunk
-            const int rr = tid & (BM - 1), kh = tid >> 7;
-            const int gm = m0 + rr;
             const float sc = pow2f(-sExpA[eb * BM + rr]);
-            float2 v[16];
-#pragma unroll
-            for (int i = 0; i < 16; i++) {
-              const int k = ck0 + kh * 16 + i;
-              v[i] = (gm < M && k < kb1) ? *reinterpret_cast<const float2*>(addrA(gm, k)) : make_float2(0.f, 0.f);
-            }
 #pragma unroll
             for (int g = 0; g < 2; g++) {
               float hh[8], ll[8];
 #pragma unroll
               for (int i = 0; i < 8; i++) {
-                hh[i] = v[g * 8 + i].x * sc;
-                ll[i] = v[g * 8 + i].y * sc;
+                hh[i] = va[g * 8 + i].x * sc;
+                ll[i] = va[g * 8 + i].y * sc;
               }
               uint8_t* dst = sA + (kh * 2 + g) * A_LBO + (rr >> 3) * 128 + (rr & 7) * 16;
-#pragma unroll
-              for (int j = 0; j < S; j++) {
-                const float mg = slice_magic(j);
-                float s8[8];
-#pragma unroll
-                for (int i = 0; i < 8; i++) s8[i] = next_slice(hh[i], ll[i], mg);
-                uint4 w;
-                w.x = pack_bf16x2(s8[0], s8[1]);
-                w.y = pack_bf16x2(s8[2], s8[3]);
-                w.z = pack_bf16x2(s8[4], s8[5]);
-                w.w = pack_bf16x2(s8[6], s8[7]);
-                *reinterpret_cast<uint4*>(dst + j * A_SLICE) = w;
-              }
+              slice_store(hh, ll, dst, A_SLICE);
             }
           }
           {  // B: column cn, k-group kq of the chunk
-            const int cn = tid & (BN - 1), kq = tid >> 6;
-            const int gn = n0 + cn;
             const float sc = pow2f(-sExpB[eb * BN + cn]);
             float hh[8], ll[8];
 #pragma unroll
             for (int i = 0; i < 8; i++) {
-              const int k = ck0 + kq * 8 + i;
-              float2 v = make_float2(0.f, 0.f);
-              if (gn < N && k < kb1 && !zeroB(k, gn)) v = *reinterpret_cast<const float2*>(addrB(k, gn));
-              hh[i] = v.x * sc;
-              ll[i] = v.y * sc;
+              hh[i] = vb[i].x * sc;
+              ll[i] = vb[i].y * sc;
             }
             uint8_t* dst = sB + kq * B_LBO + (cn >> 3) * 128 + (cn & 7) * 16;
-#pragma unroll
-            for (int j = 0; j < S; j++) {
-              const float mg = slice_magic(j);
-              float s8[8];
-#pragma unroll
-              for (int i = 0; i < 8; i++) s8[i] = next_slice(hh[i], ll[i], mg);
-              uint4 w;
-              w.x = pack_bf16x2(s8[0], s8[1]);
-              w.y = pack_bf16x2(s8[2], s8[3]);
-              w.z = pack_bf16x2(s8[4], s8[5]);
-              w.w = pack_bf16x2(s8[6], s8[7]);
-              *reinterpret_cast<uint4*>(dst + j * B_SLICE) = w;
-            }
+            slice_store(hh, ll, dst, B_SLICE);
           }
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           mbar_arrive(bFull + 8 * stage);
+          if (tid == 0) {
+            // ---- MMA issue for this chunk once every thread has sliced it
+            if (!mbar_wait(bFull + 8 * stage, use & 1, sAbort)) {
+              *sAbort = 1;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t aBase = su32(sA), bBase = su32(sB);
+            const int ksteps = (min(KC, nk - c * KC) + 15) / 16;
+            for (int kk = 0; kk < ksteps; kk++) {
+#pragma unroll
+              for (int s1 = 0; s1 < S; s1++) {
+                const uint64_t ad = smem_desc(aBase + s1 * A_SLICE + kk * 2 * A_LBO, A_LBO, 128);
+#pragma unroll
+                for (int t1 = 0; t1 < S - s1; t1++) {
+                  const int dd = s1 + t1;
+                  const uint64_t bd = smem_desc(bBase + t1 * B_SLICE + kk * 2 * B_LBO, B_LBO, 128);
+                  mma_bf16(tmem + dd * BN, ad, bd, idesc, (inited >> dd) & 1u);
+                  inited |= 1u << dd;
+                }
+              }
+            }
+            issued = true;
+            mma_commit(bEmpty + 8 * stage);
+            if (c == nch - 1) mma_commit(bAccF);
+          }
+          if (more) {
+#pragma unroll
+            for (int i = 0; i < 16; i++) va[i] = na[i];
+#pragma unroll
+            for (int i = 0; i < 8; i++) vb[i] = nb[i];
+          }
         }
         if (*sAbort) break;
-        // ---- epilogue of the block: S diagonals -> df64, scaled, accumulated
+        // ---- epilogue of the block: S diagonals -> df64, scaled by
+        // 2^(E_m + F_n), into C: the first block writes alpha v + beta C, later
+        // blocks add alpha v to what the first wrote
         if (!mbar_wait(bAccF, blk_ctr & 1, sAbort)) {
           *sAbort = 1;
           break;
@@ -387,6 +445,9 @@ __global__ void __launch_bounds__(tc::NTHREADS, 1)
         tc_fence_after();
         const float scr = pow2f(sExpA[eb * BM + r]);
         const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+        const int gm = m0 + r;
+        const bool first = b == 0;
+        const bool rd = !first || beta != 0.0;
 #pragma unroll
         for (int q8 = 0; q8 < 4; q8++) {
           const int col = ch * 32 + q8 * 8;
@@ -395,92 +456,68 @@ __global__ void __launch_bounds__(tc::NTHREADS, 1)
 #pragma unroll
             for (int dd = 0; dd < S; dd++) tmem_ld8(tl + dd * BN + col, D[dd]);
             tmem_ld_wait();
+            double* pcc[8];
+            float2 old[8];
 #pragma unroll
-            for (int j = 0; j < 8; j++) {
+            for (int j2 = 0; j2 < 8; j2++) {
+              const int gn = n0 + col + j2;
+              const bool ok = gm < M && gn < N && !(d.lowC && gm < gn);
+              pcc[j2] = nullptr;
+              old[j2] = make_float2(0.f, 0.f);
+              if (ok) {
+                const int64_t cnn = d.gatherN ? (int64_t)bases.kidx[d.nofs + gn] : (int64_t)gn;
+                pcc[j2] = C + gm + cnn * ldc;
+                if (rd) old[j2] = *reinterpret_cast<const float2*>(pcc[j2]);
+              }
+            }
+#pragma unroll
+            for (int j2 = 0; j2 < 8; j2++) {
               // exact-ish sum of the diagonals (TwoSum into hi, errors into lo)
-              float hi = D[0][j], lo = 0.f;
+              float hi = D[0][j2], lo = 0.f;
 #pragma unroll
               for (int dd = 1; dd < S; dd++) {
-                const float x = D[dd][j];
-                const float s = __fadd_rn(hi, x);
-                const float v = __fsub_rn(s, hi);
-                lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(s, v)), __fsub_rn(x, v)));
-                hi = s;
+                const float x = D[dd][j2];
+                const float sm2 = __fadd_rn(hi, x);
+                const float v = __fsub_rn(sm2, hi);
+                lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(sm2, v)), __fsub_rn(x, v)));
+                hi = sm2;
               }
-              const float scn = pow2f(sExpB[eb * BN + col + j]);
+              const float scn = pow2f(sExpB[eb * BN + col + j2]);
               df64 t = df_fast_two_sum(hi, lo);
               t.hi = (t.hi * scr) * scn;
               t.lo = (t.lo * scr) * scn;
-              df64 a = {acc_hi[q8 * 8 + j], acc_lo[q8 * 8 + j]};
-              a = df_add(a, t);
-              acc_hi[q8 * 8 + j] = a.hi;
-              acc_lo[q8 * 8 + j] = a.lo;
-            }
-          }
-        }
-        tc_fence_before();
-        mbar_arrive(bAccE);
-      } else if (warp == PW && lane == 0) {
-        // ---- MMA issue
-        if (blk_ctr > 0 && !mbar_wait(bAccE, (blk_ctr - 1) & 1, sAbort)) {
-          *sAbort = 1;
-          break;
-        }
-        tc_fence_after();
-        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(nmma >> 3) << 17) |
-                               ((uint32_t)(BM >> 4) << 24);
-        uint32_t inited = 0;
-        for (int c = 0; c < nch; c++) {
-          const uint32_t cc = chunk_ctr + c;
-          const int stage = cc % NST;
-          if (!mbar_wait(bFull + 8 * stage, (cc / NST) & 1, sAbort)) {
-            *sAbort = 1;
-            break;
-          }
-          tc_fence_after();
-          const uint32_t aBase = su32(sm + stage * STAGE), bBase = aBase + S * A_SLICE;
-          const int ksteps = (min(KC, nk - c * KC) + 15) / 16;
-          for (int kk = 0; kk < ksteps; kk++) {
-#pragma unroll
-            for (int s = 0; s < S; s++) {
-              const uint64_t ad = smem_desc(aBase + s * A_SLICE + kk * 2 * A_LBO, A_LBO, 128);
-#pragma unroll
-              for (int t = 0; t < S - s; t++) {
-                const int dd = s + t;
-                const uint64_t bd = smem_desc(bBase + t * B_SLICE + kk * 2 * B_LBO, B_LBO, 128);
-                mma_bf16(tmem + dd * BN, ad, bd, idesc, (inited >> dd) & 1u);
-                inited |= 1u << dd;
+              t = df_scale(t, (float)alpha);
+              if (pcc[j2]) {
+                df64 o = {old[j2].x, old[j2].y};
+                if (first && beta != 1.0) o = df_scale(o, (float)beta);
+                if (rd) t = df_add(t, o);
+                *reinterpret_cast<float2*>(pcc[j2]) = make_float2(t.hi, t.lo);
               }
             }
           }
-          issued = true;
-          mma_commit(bEmpty + 8 * stage);
         }
-        if (*sAbort) break;
-        mma_commit(bAccF);
+        // TMEM reads done before the next block's MMAs (ordered by the
+        // barriers of its pre-pass)
+        tc_fence_before();
       }
       chunk_ctr += nch;
     }
     if (*sAbort) break;
-    if (producer) {
-      // ---- C = alpha * acc + beta * C (df64), like the CUDA-core kernel
+    if (producer && nblk == 0 && beta != 1.0) {
+      // no K terms (empty or masked range): C = beta C
       const int gm = m0 + r;
-      const double alpha = d.alpha * bases.alpha_scale, beta = d.beta;
       if (gm < M) {
-#pragma unroll
-        for (int j = 0; j < 32; j++) {
-          const int gn = n0 + ch * 32 + j;
+        for (int j2 = 0; j2 < 32; j2++) {
+          const int gn = n0 + ch * 32 + j2;
           if (gn >= N || (d.lowC && gm < gn)) continue;
-          const int64_t cn = d.gatherN ? (int64_t)bases.kidx[d.nofs + gn] : (int64_t)gn;
-          double* pcc = C + gm + cn * ldc;
-          df64 v = df_scale(df_fast_two_sum(acc_hi[j], acc_lo[j]), (float)alpha);
+          const int64_t cnn = d.gatherN ? (int64_t)bases.kidx[d.nofs + gn] : (int64_t)gn;
+          float2* pc2 = reinterpret_cast<float2*>(C + gm + cnn * ldc);
+          df64 o = {0.f, 0.f};
           if (beta != 0.0) {
-            const float2 o = *reinterpret_cast<const float2*>(pcc);
-            df64 old = {o.x, o.y};
-            if (beta != 1.0) old = df_scale(old, (float)beta);
-            v = df_add(v, old);
+            const float2 v = *pc2;
+            o = df_scale({v.x, v.y}, (float)beta);
           }
-          *reinterpret_cast<float2*>(pcc) = make_float2(v.hi, v.lo);
+          *pc2 = make_float2(o.hi, o.lo);
         }
       }
     }
@@ -491,7 +528,7 @@ __global__ void __launch_bounds__(tc::NTHREADS, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == PW) {
+  if (warp == 0) {
     if (lane == 0 && *sAbort && issued) {
       mma_commit(bDrain);
       volatile int never = 0;
