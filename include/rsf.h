@@ -61,7 +61,9 @@ typedef enum {
   RSF_MATERN12 = 0,  /* s2 exp(-r/l) */
   RSF_MATERN32 = 1,  /* s2 (1 + a) exp(-a), a = sqrt(3) r / l */
   RSF_MATERN52 = 2,  /* s2 (1 + a + a^2/3) exp(-a), a = sqrt(5) r / l */
-  RSF_MATERN1 = 3,   /* s2 x K_1(x), x = sqrt(2) r / l (not built yet: EINVAL) */
+  RSF_MATERN1 = 3,   /* s2 x K_1(x), x = sqrt(2) r / l (K_0, K_1: ascending
+                        series for x < 1, trapezoid rule on the integral
+                        representation otherwise) */
   RSF_RQ = 4         /* s2 (1 + r^2 / (2 alpha l^2))^-alpha */
 } rsf_family;
 

@@ -210,7 +210,7 @@ static rsf_opts resolve_opts(const rsf_opts* o) {
 static void check_kernel(const rsf_kernel* k, const double* theta) {
   RSF_CHECK(k != nullptr && theta != nullptr, RSF_EINVAL, "kernel and theta must not be NULL");
   RSF_CHECK(k->family == RSF_MATERN12 || k->family == RSF_MATERN32 || k->family == RSF_MATERN52 ||
-                k->family == RSF_RQ,
+                k->family == RSF_MATERN1 || k->family == RSF_RQ,
             RSF_EINVAL, "unsupported kernel family");
   RSF_CHECK(k->family != RSF_RQ || k->alpha > 0.0, RSF_EINVAL, "RQ needs alpha > 0");
   RSF_CHECK(theta[0] > 0.0 && theta[1] > 0.0 && theta[2] >= 0.0, RSF_EINVAL, "theta must satisfy l > 0, s2 > 0, nug >= 0");

@@ -207,13 +207,14 @@ __global__ void __launch_bounds__(GT, GEMM_MIN_BLOCKS) gemm_kernel(const GemmDes
 
 void GemmBatch::build(const std::vector<GemmDesc>& d, cudaStream_t s) {
   nprob = (int)d.size();
-  std::vector<int> pre(nprob + 1, 0), pre64(nprob + 1, 0);
+  std::vector<int> pre(nprob + 1, 0);
+  std::vector<int2> nt32;
   maxM = 0;
   anyLaunchM = false;
   fixedMNK = launchNK = fixedBytes = launchBytesPerM = launchBytes0 = 0;
   for (int i = 0; i < nprob; i++) {
     pre[i + 1] = pre[i] + std::max(0, cdiv(d[i].N, BN));
-    pre64[i + 1] = pre64[i] + std::max(0, cdiv(d[i].N, 64));
+    for (int c = 0; c < d[i].N; c += 32) nt32.push_back(make_int2(i, c));
     if (d[i].M < 0) anyLaunchM = true; else maxM = std::max(maxM, d[i].M);
     // nonzero (k, n) pairs of op(B) and the computed part of C
     double N = d[i].N, K = d[i].K, nk;
@@ -237,10 +238,10 @@ void GemmBatch::build(const std::vector<GemmDesc>& d, cudaStream_t s) {
     }
   }
   ntilesN = pre[nprob];
-  ntilesN64 = pre64[nprob];
+  ntilesN32 = (int)nt32.size();
   upload(desc, d, s);
   upload(prefix, pre, s);
-  upload(prefix64, pre64, s);
+  upload(ntile32, nt32, s);
 }
 
 void GemmBatch::run(const GemmBases& b, cudaStream_t s) const {

@@ -57,10 +57,11 @@ struct GemmBases {
 
 // Device-resident batch of GEMM problems with its tile prefix.
 struct GemmBatch {
-  DBuf desc, prefix, prefix64;
+  DBuf desc, prefix, ntile32;
   int nprob = 0;
   int ntilesN = 0;   // sum over problems of ceil(N / BN)
-  int ntilesN64 = 0; // the same for the 64-column tiles of the tensor-core kernel
+  int ntilesN32 = 0; // the same for the 32-column tiles of the tensor-core kernel,
+                     // whose (problem, first column) pairs ntile32 lists
   int maxM = 0;      // max M over problems with M >= 0
   bool anyLaunchM = false;
   // algorithmic work: flops = 2 (fixedMNK + launchM * launchNK), same for bytes

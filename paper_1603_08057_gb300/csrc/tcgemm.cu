@@ -28,17 +28,21 @@
 //     scales by 2^(E_m + F_n) and accumulates the K-blocks, then applies
 //     alpha and beta like the CUDA-core df64 kernel.
 //
-// Work split of one CTA (persistent over the tiles of the batch; 8 warps,
-// two per SM sub-partition, so each thread may hold up to 255 registers):
-//   * all 256 threads: pre-pass, slicing of the A tile (128 x 32 per stage)
-//     and B tile (64 x 32) into shared memory in the canonical K-major,
-//     no-swizzle core-matrix layout (the next chunk's loads in flight while
-//     the current one is sliced), and the epilogue;
-//   * warp 0 allocates the 512 TMEM columns; thread 0 issues, once every
-//     thread has sliced a chunk, its tcgen05.mma instructions (M = 128,
-//     N = 64 or 32, K = 16, bf16 x bf16 -> fp32) into the S accumulators
-//     (columns d * 64), and commits to the mbarriers that free the
-//     shared-memory stage and that hand a finished K-block to the epilogue.
+// Work split (persistent CTAs over the 128 x 32 output tiles of the batch,
+// two CTAs per SM so that one CTA's memory latency hides behind the other's
+// work; 4 warps each):
+//   * every thread owns one row of the A tile (and the TMEM lane of that
+//     row in the epilogue) and helps slice the B tile; blocks of at most 32
+//     terms are held in registers whole, so their exponents need no second
+//     pass, longer blocks take a pre-pass and keep the next chunk's loads in
+//     flight while the current chunk (16 terms) is sliced into one of three
+//     shared-memory stages (canonical K-major, no-swizzle core-matrix layout);
+//   * warp 0 allocates 256 TMEM columns (the S = 7 accumulators of 32
+//     columns); thread 0 issues, once every thread has sliced a chunk, its
+//     28 tcgen05.mma instructions (M = 128, N = 32, K = 16, bf16 x bf16 ->
+//     fp32) and commits to the mbarriers that free the stage and that hand a
+//     finished K-block to the epilogue, which loads the C values it updates
+//     while the last MMAs run.
 // Every wait is bounded (a few seconds): on expiry the CTA records
 // RSF_ETIMEOUT, drains its own MMAs, frees its TMEM and returns.
 #include <algorithm>
@@ -51,20 +55,20 @@
 namespace rsf {
 
 namespace tc {
-constexpr int BM = 128, BN = 64, KC = 32, KB = 384, S = 7, NST = 2;
-constexpr int PW = 8;                          // warps: slicing, MMA issue (thread 0), epilogue
-constexpr int NPROD = PW * 32;
-constexpr int NTHREADS = NPROD;                // 2 warps per SM sub-partition: up to 255 registers
+constexpr int BM = 128, BN = 32, KC = 16, KB = 384, S = 7, NST = 3;
+constexpr int NTHREADS = 128;                  // 4 warps; two CTAs per SM
 constexpr int A_SLICE = BM * KC * 2;           // bytes of one bf16 slice of an A stage
 constexpr int B_SLICE = BN * KC * 2;
 constexpr int STAGE = S * (A_SLICE + B_SLICE);
 constexpr int A_LBO = (BM / 8) * 128;          // bytes between k-groups of 8 (core matrices)
 constexpr int B_LBO = (BN / 8) * 128;
-constexpr int AUX = 4096;
-constexpr int SMEM = NST * STAGE + AUX + 1024; // + alignment slack
+constexpr int TMEM_COLS = 256;                 // S * BN accumulator columns, rounded to a power of two
+constexpr int AUX = 2048;
+constexpr int SMEM = NST * STAGE + AUX + 1024; // + alignment slack; two CTAs fit an SM
 constexpr unsigned long long WAIT_NS = 4000000000ull;
-static_assert(S * BN <= 512, "the S accumulators must fit the 512 TMEM columns");
+static_assert(S * BN <= TMEM_COLS, "the S accumulators must fit the allocated TMEM columns");
 static_assert(KB % KC == 0, "K-blocks hold whole chunks");
+static_assert(2 * (SMEM + 1024) <= 232448, "two CTAs per SM");
 }  // namespace tc
 
 __device__ DevStatus g_tc_status;
@@ -107,9 +111,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
   }
 }
 
-__device__ __forceinline__ void named_sync_producers() {
-  asm volatile("bar.sync 1, %0;" ::"n"(tc::NPROD) : "memory");
-}
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -205,28 +206,26 @@ __device__ __forceinline__ int64_t base_scale(const GemmBases& b, int i) {
   return i == 0 ? b.sc[0] : i == 1 ? b.sc[1] : i == 2 ? b.sc[2] : b.sc[3];
 }
 
-__global__ void __launch_bounds__(tc::NTHREADS, 1)
-    tc_gemm_kernel(const GemmDesc* __restrict__ descs, const int* __restrict__ prefix, int nprob, int ntilesN,
-                   int mtiles, GemmBases bases) {
+__global__ void __launch_bounds__(tc::NTHREADS, 2)
+    tc_gemm_kernel(const GemmDesc* __restrict__ descs, const int2* __restrict__ ntile, int ntilesN, int mtiles,
+                   GemmBases bases) {
   using namespace tc;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* aux = sm + NST * STAGE;
-  int* sExpA = reinterpret_cast<int*>(aux);                 // [2][BM]
-  int* sExpB = sExpA + 2 * BM;                              // [2][BN]
-  float* sPart = reinterpret_cast<float*>(sExpB + 2 * BN);  // [NPROD]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sPart + NPROD);
-  // bars: full[NST], empty[NST], accf, acce, drain
-  uint32_t* sTmem = reinterpret_cast<uint32_t*>(bars + 2 * NST + 3);
+  int* sExpB = reinterpret_cast<int*>(aux);                 // [2][BN] (by K-block parity)
+  float* sPart = reinterpret_cast<float*>(sExpB + 2 * BN);  // [NTHREADS]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sPart + NTHREADS);
+  // bars: full[NST], empty[NST], accf, drain
+  uint32_t* sTmem = reinterpret_cast<uint32_t*>(bars + 2 * NST + 2);
   volatile int* sAbort = reinterpret_cast<volatile int*>(sTmem + 1);
   const uint32_t bFull = su32(bars), bEmpty = su32(bars + NST), bAccF = su32(bars + 2 * NST),
-                 bDrain = su32(bars + 2 * NST + 2);
+                 bDrain = su32(bars + 2 * NST + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const bool producer = true;
   if (tid == 0) {
     for (int i = 0; i < NST; i++) {
-      mbar_init(bFull + 8 * i, NPROD);
+      mbar_init(bFull + 8 * i, NTHREADS);
       mbar_init(bEmpty + 8 * i, 1);
     }
     mbar_init(bAccF, 1);
@@ -235,24 +234,31 @@ __global__ void __launch_bounds__(tc::NTHREADS, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(su32(sTmem)));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(sTmem)),
+                 "n"(TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *sTmem;
+  const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);   // this warp's TMEM lanes
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                         ((uint32_t)(BM >> 4) << 24);
+  // thread roles: A row r (and TMEM lane r); B column cb with k-group qb
+  const int r = tid;
+  const int cb = tid & (BN - 1), qb = tid >> 5;
 
   uint32_t chunk_ctr = 0, blk_ctr = 0;
-  bool issued = false;   // the MMA thread issued MMAs (drained on abort)
+  bool issued = false;   // thread 0 issued MMAs (drained on abort)
   const int ntiles = ntilesN * mtiles;
   for (int tile = blockIdx.x; tile < ntiles && !*sAbort; tile += gridDim.x) {
     const int tn = tile / mtiles, tm = tile - tn * mtiles;
-    const int p = find_prob(prefix, nprob, tn);
-    const GemmDesc d = descs[p];
+    const int2 pn = ntile[tn];
+    const GemmDesc d = descs[pn.x];
     const int M = d.M >= 0 ? d.M : bases.M;
     const int N = d.N, K = d.K;
-    const int n0 = (tn - prefix[p]) * BN;
+    const int n0 = pn.y;
     const int m0 = tm * BM;
     if (m0 >= M || n0 >= N) continue;
     if (d.lowC && n0 > m0 + BM - 1) continue;
@@ -267,11 +273,13 @@ __global__ void __launch_bounds__(tc::NTHREADS, 1)
     if (d.triB == 2) k1 = min(K, n0 + BN);
     const int nblk = k1 > k0 ? (k1 - k0 + KB - 1) / KB : 0;
     const int nvalid = min(BN, N - n0);
-    const int nmma = nvalid <= 32 ? 32 : 64;
     const bool masktri = d.triB != 0 && !d.gatherK && !d.gatherN;
+    const double alpha = d.alpha * bases.alpha_scale, beta = d.beta;
+    const int gm = m0 + r;
+    const bool rowok = gm < M;
 
     // element (m, k) of op(A) and (k, n) of op(B) as df64 {hi, lo}
-    auto addrA = [&](int gm, int gk) -> const double* {
+    auto addrA = [&](int gk) -> const double* {
       if (d.gatherK) return A + gm + (int64_t)bases.kidx[d.kofs + gk] * lda;
       return d.ta ? A + gk + (int64_t)gm * lda : A + gm + (int64_t)gk * lda;
     };
@@ -283,27 +291,22 @@ __global__ void __launch_bounds__(tc::NTHREADS, 1)
     auto zeroB = [&](int gk, int gn) -> bool {
       return masktri && ((d.triB == 1 && gk < gn) || (d.triB == 2 && gk > gn));
     };
-
-    // producer's output: row r (TMEM lane), 32 columns starting at ch * 32
-    const int r = (warp & 3) * 32 + lane;
-    const int ch = (warp >> 2) & 1;
-    const double alpha = d.alpha * bases.alpha_scale, beta = d.beta;
-    // loads of one chunk (k from ck0): A row rr, k = ck0 + kh * 16 + i;
-    // B column cn, k = ck0 + kq * 8 + i (zero outside the block and the masks)
-    const int rr = tid & (BM - 1), kh = (tid >> 7) & 1;
-    const int cn = tid & (BN - 1), kq = (tid >> 6) & 3;
-    auto load_chunk = [&](int ck0, int kend, float2 (&va)[16], float2 (&vb)[8]) {
-      const int gm = m0 + rr, gn = n0 + cn;
+    // 16 A values of row r from k0a, and the 8 B values of column cb, k-group
+    // starting at k0b (zero outside [.., kend) and the masks)
+    auto loadA16 = [&](int k0a, int kend, float2 (&v)[16]) {
 #pragma unroll
       for (int i = 0; i < 16; i++) {
-        const int k = ck0 + kh * 16 + i;
-        va[i] = (gm < M && k < kend) ? *reinterpret_cast<const float2*>(addrA(gm, k)) : make_float2(0.f, 0.f);
+        const int k = k0a + i;
+        v[i] = (rowok && k < kend) ? *reinterpret_cast<const float2*>(addrA(k)) : make_float2(0.f, 0.f);
       }
+    };
+    auto loadB8 = [&](int k0b, int kend, float2 (&v)[8]) {
+      const int gn = n0 + cb;
 #pragma unroll
       for (int i = 0; i < 8; i++) {
-        const int k = ck0 + kq * 8 + i;
-        vb[i] = (gn < N && k < kend && !zeroB(k, gn)) ? *reinterpret_cast<const float2*>(addrB(k, gn))
-                                                      : make_float2(0.f, 0.f);
+        const int k = k0b + i;
+        v[i] = (gn < N && k < kend && !zeroB(k, gn)) ? *reinterpret_cast<const float2*>(addrB(k, gn))
+                                                     : make_float2(0.f, 0.f);
       }
     };
 
@@ -311,214 +314,207 @@ __global__ void __launch_bounds__(tc::NTHREADS, 1)
       const int kb0 = k0 + b * KB, kb1 = min(k1, kb0 + KB), nk = kb1 - kb0;
       const int nch = (nk + KC - 1) / KC;
       const int eb = blk_ctr & 1;
-      if (producer) {
-        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(nmma >> 3) << 17) |
-                               ((uint32_t)(BM >> 4) << 24);
-        uint32_t inited = 0;   // thread 0: diagonals written in this block
-        // ---- pre-pass: row and column exponents of this K-block (batches of
-        // 16 independent loads per thread keep the memory pipe busy)
-        {
-          const int h = tid >> 7;
-          const int gm = m0 + rr;
-          float mx = 0.f;
-          if (gm < M)
-            for (int kb = kb0 + h; kb < kb1; kb += 32) {
-              float v[16];
+      const bool small = nk <= 2 * KC;
+      float2 ra[16], rb[8], xa[16], xb[8];
+      float mxA = 0.f, mxB = 0.f;
+      if (small) {
+        // the whole block (<= 32 terms) in registers: row r's A values and
+        // column cb's k-group qb; exponents straight from them
+        loadA16(kb0, kb1, ra);
+        loadA16(kb0 + KC, kb1, xa);
+        loadB8(kb0 + qb * 8, kb1, rb);
 #pragma unroll
-              for (int i = 0; i < 16; i++) {
-                const int k = kb + 2 * i;
-                v[i] = k < kb1 ? fabsf(*reinterpret_cast<const float*>(addrA(gm, k))) : 0.f;
-              }
+        for (int i = 0; i < 16; i++) mxA = fmaxf(mxA, fmaxf(fabsf(ra[i].x), fabsf(xa[i].x)));
 #pragma unroll
-              for (int i = 0; i < 16; i++) mx = fmaxf(mx, v[i]);
+        for (int i = 0; i < 8; i++) mxB = fmaxf(mxB, fabsf(rb[i].x));
+      } else {
+        // pre-pass over the block: batches of 16 independent loads
+        if (rowok)
+          for (int kb = kb0; kb < kb1; kb += 16) {
+            float v[16];
+#pragma unroll
+            for (int i = 0; i < 16; i++)
+              v[i] = kb + i < kb1 ? fabsf(*reinterpret_cast<const float*>(addrA(kb + i))) : 0.f;
+#pragma unroll
+            for (int i = 0; i < 16; i++) mxA = fmaxf(mxA, v[i]);
+          }
+        const int gn = n0 + cb;
+        if (gn < N)
+          for (int kb = kb0 + qb; kb < kb1; kb += 64) {
+            float v[16];
+#pragma unroll
+            for (int i = 0; i < 16; i++) {
+              const int k = kb + 4 * i;
+              v[i] = (k < kb1 && !zeroB(k, gn)) ? fabsf(*reinterpret_cast<const float*>(addrB(k, gn))) : 0.f;
             }
-          sPart[tid] = mx;
-          named_sync_producers();
-          if (tid < BM) sExpA[eb * BM + tid] = block_exponent(fmaxf(sPart[tid], sPart[tid + BM]));
-          named_sync_producers();
-          const int q = tid >> 6;
-          const int gn = n0 + cn;
-          mx = 0.f;
-          if (gn < N)
-            for (int kb = kb0 + q; kb < kb1; kb += 64) {
-              float v[16];
 #pragma unroll
-              for (int i = 0; i < 16; i++) {
-                const int k = kb + 4 * i;
-                v[i] = (k < kb1 && !zeroB(k, gn)) ? fabsf(*reinterpret_cast<const float*>(addrB(k, gn))) : 0.f;
-              }
-#pragma unroll
-              for (int i = 0; i < 16; i++) mx = fmaxf(mx, v[i]);
-            }
-          sPart[tid] = mx;
-          named_sync_producers();
-          if (tid < BN)
-            sExpB[eb * BN + tid] = block_exponent(
-                fmaxf(fmaxf(sPart[tid], sPart[tid + BN]), fmaxf(sPart[tid + 2 * BN], sPart[tid + 3 * BN])));
-          named_sync_producers();
+            for (int i = 0; i < 16; i++) mxB = fmaxf(mxB, v[i]);
+          }
+        loadA16(kb0, kb1, ra);
+        if (qb < 2) loadB8(kb0 + qb * 8, kb1, rb);
+      }
+      const int eA = block_exponent(mxA);
+      sPart[tid] = mxB;
+      __syncthreads();
+      if (tid < BN)
+        sExpB[eb * BN + tid] = block_exponent(
+            fmaxf(fmaxf(sPart[tid], sPart[tid + BN]), fmaxf(sPart[tid + 2 * BN], sPart[tid + 3 * BN])));
+      __syncthreads();
+      const float scA = pow2f(-eA);
+      const float scB = pow2f(-sExpB[eb * BN + cb]);
+
+      uint32_t inited = 0;   // thread 0: diagonals written in this block
+      for (int c = 0; c < nch; c++) {
+        const uint32_t cc = chunk_ctr + c;
+        const int stage = cc % NST;
+        const uint32_t use = cc / NST;
+        const bool more = c + 1 < nch;
+        if (!small && more) {
+          loadA16(kb0 + (c + 1) * KC, kb1, xa);
+          if (qb < 2) loadB8(kb0 + (c + 1) * KC + qb * 8, kb1, xb);
         }
-        // ---- slice the chunks of the block into the stages; the loads of
-        // chunk c + 1 are issued before chunk c is sliced
-        float2 va[16], vb[8];
-        load_chunk(kb0, kb1, va, vb);
-        for (int c = 0; c < nch; c++) {
-          const uint32_t cc = chunk_ctr + c;
-          const int stage = cc % NST;
-          const uint32_t use = cc / NST;
-          float2 na[16], nb[8];
-          const bool more = c + 1 < nch;
-          if (more) load_chunk(kb0 + (c + 1) * KC, kb1, na, nb);
-          if (use > 0 && !mbar_wait(bEmpty + 8 * stage, (use - 1) & 1, sAbort)) {
-            *sAbort = 1;
-            break;
-          }
-          uint8_t* sA = sm + stage * STAGE;
-          uint8_t* sB = sA + S * A_SLICE;
-          {  // A: row rr, k-groups 2 kh and 2 kh + 1 of the chunk
-            const float sc = pow2f(-sExpA[eb * BM + rr]);
-#pragma unroll
-            for (int g = 0; g < 2; g++) {
-              float hh[8], ll[8];
-#pragma unroll
-              for (int i = 0; i < 8; i++) {
-                hh[i] = va[g * 8 + i].x * sc;
-                ll[i] = va[g * 8 + i].y * sc;
-              }
-              uint8_t* dst = sA + (kh * 2 + g) * A_LBO + (rr >> 3) * 128 + (rr & 7) * 16;
-              slice_store(hh, ll, dst, A_SLICE);
-            }
-          }
-          {  // B: column cn, k-group kq of the chunk
-            const float sc = pow2f(-sExpB[eb * BN + cn]);
-            float hh[8], ll[8];
-#pragma unroll
-            for (int i = 0; i < 8; i++) {
-              hh[i] = vb[i].x * sc;
-              ll[i] = vb[i].y * sc;
-            }
-            uint8_t* dst = sB + kq * B_LBO + (cn >> 3) * 128 + (cn & 7) * 16;
-            slice_store(hh, ll, dst, B_SLICE);
-          }
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          mbar_arrive(bFull + 8 * stage);
-          if (tid == 0) {
-            // ---- MMA issue for this chunk once every thread has sliced it
-            if (!mbar_wait(bFull + 8 * stage, use & 1, sAbort)) {
-              *sAbort = 1;
-              break;
-            }
-            tc_fence_after();
-            const uint32_t aBase = su32(sA), bBase = su32(sB);
-            const int ksteps = (min(KC, nk - c * KC) + 15) / 16;
-            for (int kk = 0; kk < ksteps; kk++) {
-#pragma unroll
-              for (int s1 = 0; s1 < S; s1++) {
-                const uint64_t ad = smem_desc(aBase + s1 * A_SLICE + kk * 2 * A_LBO, A_LBO, 128);
-#pragma unroll
-                for (int t1 = 0; t1 < S - s1; t1++) {
-                  const int dd = s1 + t1;
-                  const uint64_t bd = smem_desc(bBase + t1 * B_SLICE + kk * 2 * B_LBO, B_LBO, 128);
-                  mma_bf16(tmem + dd * BN, ad, bd, idesc, (inited >> dd) & 1u);
-                  inited |= 1u << dd;
-                }
-              }
-            }
-            issued = true;
-            mma_commit(bEmpty + 8 * stage);
-            if (c == nch - 1) mma_commit(bAccF);
-          }
-          if (more) {
-#pragma unroll
-            for (int i = 0; i < 16; i++) va[i] = na[i];
-#pragma unroll
-            for (int i = 0; i < 8; i++) vb[i] = nb[i];
-          }
-        }
-        if (*sAbort) break;
-        // ---- epilogue of the block: S diagonals -> df64, scaled by
-        // 2^(E_m + F_n), into C: the first block writes alpha v + beta C, later
-        // blocks add alpha v to what the first wrote
-        if (!mbar_wait(bAccF, blk_ctr & 1, sAbort)) {
+        if (use > 0 && !mbar_wait(bEmpty + 8 * stage, (use - 1) & 1, sAbort)) {
           *sAbort = 1;
           break;
         }
-        tc_fence_after();
-        const float scr = pow2f(sExpA[eb * BM + r]);
-        const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-        const int gm = m0 + r;
-        const bool first = b == 0;
-        const bool rd = !first || beta != 0.0;
+        uint8_t* sA = sm + stage * STAGE;
+        uint8_t* sB = sA + S * A_SLICE;
+        {  // A: row r, both k-groups of the chunk
+          const float2* va = (small && c == 1) ? xa : ra;
 #pragma unroll
-        for (int q8 = 0; q8 < 4; q8++) {
-          const int col = ch * 32 + q8 * 8;
-          if (col < nmma) {
-            float D[S][8];
+          for (int g = 0; g < 2; g++) {
+            float hh[8], ll[8];
 #pragma unroll
-            for (int dd = 0; dd < S; dd++) tmem_ld8(tl + dd * BN + col, D[dd]);
-            tmem_ld_wait();
-            double* pcc[8];
-            float2 old[8];
-#pragma unroll
-            for (int j2 = 0; j2 < 8; j2++) {
-              const int gn = n0 + col + j2;
-              const bool ok = gm < M && gn < N && !(d.lowC && gm < gn);
-              pcc[j2] = nullptr;
-              old[j2] = make_float2(0.f, 0.f);
-              if (ok) {
-                const int64_t cnn = d.gatherN ? (int64_t)bases.kidx[d.nofs + gn] : (int64_t)gn;
-                pcc[j2] = C + gm + cnn * ldc;
-                if (rd) old[j2] = *reinterpret_cast<const float2*>(pcc[j2]);
-              }
+            for (int i = 0; i < 8; i++) {
+              hh[i] = va[g * 8 + i].x * scA;
+              ll[i] = va[g * 8 + i].y * scA;
             }
-#pragma unroll
-            for (int j2 = 0; j2 < 8; j2++) {
-              // exact-ish sum of the diagonals (TwoSum into hi, errors into lo)
-              float hi = D[0][j2], lo = 0.f;
-#pragma unroll
-              for (int dd = 1; dd < S; dd++) {
-                const float x = D[dd][j2];
-                const float sm2 = __fadd_rn(hi, x);
-                const float v = __fsub_rn(sm2, hi);
-                lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(sm2, v)), __fsub_rn(x, v)));
-                hi = sm2;
-              }
-              const float scn = pow2f(sExpB[eb * BN + col + j2]);
-              df64 t = df_fast_two_sum(hi, lo);
-              t.hi = (t.hi * scr) * scn;
-              t.lo = (t.lo * scr) * scn;
-              t = df_scale(t, (float)alpha);
-              if (pcc[j2]) {
-                df64 o = {old[j2].x, old[j2].y};
-                if (first && beta != 1.0) o = df_scale(o, (float)beta);
-                if (rd) t = df_add(t, o);
-                *reinterpret_cast<float2*>(pcc[j2]) = make_float2(t.hi, t.lo);
-              }
-            }
+            slice_store(hh, ll, sA + g * A_LBO + (r >> 3) * 128 + (r & 7) * 16, A_SLICE);
           }
         }
-        // TMEM reads done before the next block's MMAs (ordered by the
-        // barriers of its pre-pass)
-        tc_fence_before();
+        // B: the threads holding this chunk's k-groups of column cb
+        const int gB = small ? qb - 2 * c : qb;
+        if (gB == 0 || gB == 1) {
+          float hh[8], ll[8];
+#pragma unroll
+          for (int i = 0; i < 8; i++) {
+            hh[i] = rb[i].x * scB;
+            ll[i] = rb[i].y * scB;
+          }
+          slice_store(hh, ll, sB + gB * B_LBO + (cb >> 3) * 128 + (cb & 7) * 16, B_SLICE);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(bFull + 8 * stage);
+        if (tid == 0) {
+          // MMA issue once every thread has sliced the chunk: all S (S+1)/2
+          // slice products with s + t < S, K = 16 each
+          if (!mbar_wait(bFull + 8 * stage, use & 1, sAbort)) {
+            *sAbort = 1;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t aBase = su32(sA), bBase = su32(sB);
+#pragma unroll
+          for (int s1 = 0; s1 < S; s1++) {
+            const uint64_t ad = smem_desc(aBase + s1 * A_SLICE, A_LBO, 128);
+#pragma unroll
+            for (int t1 = 0; t1 < S - s1; t1++) {
+              const int dd = s1 + t1;
+              const uint64_t bd = smem_desc(bBase + t1 * B_SLICE, B_LBO, 128);
+              mma_bf16(tmem + dd * BN, ad, bd, idesc, (inited >> dd) & 1u);
+              inited |= 1u << dd;
+            }
+          }
+          issued = true;
+          mma_commit(bEmpty + 8 * stage);
+          if (c == nch - 1) mma_commit(bAccF);
+        }
+        if (!small && more) {
+#pragma unroll
+          for (int i = 0; i < 16; i++) ra[i] = xa[i];
+#pragma unroll
+          for (int i = 0; i < 8; i++) rb[i] = xb[i];
+        } else if (small) {
+          // the small path's k-groups 2 and 3 were loaded into rb by threads qb = 2, 3
+        }
       }
       chunk_ctr += nch;
+      if (*sAbort) break;
+
+      // ---- epilogue: the C values this block updates are loaded while the
+      // last MMAs finish; the first block writes alpha v + beta C, later
+      // blocks add alpha v
+      const bool first = b == 0;
+      const bool rd = !first || beta != 0.0;
+      float2 oldc[BN];
+#pragma unroll
+      for (int j = 0; j < BN; j++) {
+        oldc[j] = make_float2(0.f, 0.f);
+        const int gn = n0 + j;
+        if (rd && rowok && gn < N && !(d.lowC && gm < gn)) {
+          const int64_t cnn = d.gatherN ? (int64_t)bases.kidx[d.nofs + gn] : (int64_t)gn;
+          oldc[j] = *reinterpret_cast<const float2*>(C + gm + cnn * ldc);
+        }
+      }
+      if (!mbar_wait(bAccF, blk_ctr & 1, sAbort)) {
+        *sAbort = 1;
+        break;
+      }
+      tc_fence_after();
+      const float scr = pow2f(eA);
+#pragma unroll
+      for (int q8 = 0; q8 < BN / 8; q8++) {
+        const int col = q8 * 8;
+        if (col < nvalid) {
+          float D[S][8];
+#pragma unroll
+          for (int dd = 0; dd < S; dd++) tmem_ld8(tl + dd * BN + col, D[dd]);
+          tmem_ld_wait();
+#pragma unroll
+          for (int j2 = 0; j2 < 8; j2++) {
+            const int gn = n0 + col + j2;
+            if (!rowok || gn >= N || (d.lowC && gm < gn)) continue;
+            // exact-ish sum of the diagonals (TwoSum into hi, errors into lo)
+            float hi = D[0][j2], lo = 0.f;
+#pragma unroll
+            for (int dd = 1; dd < S; dd++) {
+              const float x = D[dd][j2];
+              const float sm2 = __fadd_rn(hi, x);
+              const float v = __fsub_rn(sm2, hi);
+              lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(sm2, v)), __fsub_rn(x, v)));
+              hi = sm2;
+            }
+            const float scn = pow2f(sExpB[eb * BN + col + j2]);
+            df64 t = df_fast_two_sum(hi, lo);
+            t.hi = (t.hi * scr) * scn;
+            t.lo = (t.lo * scr) * scn;
+            t = df_scale(t, (float)alpha);
+            df64 o = {oldc[col + j2].x, oldc[col + j2].y};
+            if (first && beta != 1.0) o = df_scale(o, (float)beta);
+            if (rd) t = df_add(t, o);
+            const int64_t cnn = d.gatherN ? (int64_t)bases.kidx[d.nofs + gn] : (int64_t)gn;
+            *reinterpret_cast<float2*>(C + gm + cnn * ldc) = make_float2(t.hi, t.lo);
+          }
+        }
+      }
+      // TMEM reads complete before the next block's MMAs (which follow the
+      // barriers of its exponent step)
+      tc_fence_before();
     }
     if (*sAbort) break;
-    if (producer && nblk == 0 && beta != 1.0) {
+    if (nblk == 0 && beta != 1.0 && rowok) {
       // no K terms (empty or masked range): C = beta C
-      const int gm = m0 + r;
-      if (gm < M) {
-        for (int j2 = 0; j2 < 32; j2++) {
-          const int gn = n0 + ch * 32 + j2;
-          if (gn >= N || (d.lowC && gm < gn)) continue;
-          const int64_t cnn = d.gatherN ? (int64_t)bases.kidx[d.nofs + gn] : (int64_t)gn;
-          float2* pc2 = reinterpret_cast<float2*>(C + gm + cnn * ldc);
-          df64 o = {0.f, 0.f};
-          if (beta != 0.0) {
-            const float2 v = *pc2;
-            o = df_scale({v.x, v.y}, (float)beta);
-          }
-          *pc2 = make_float2(o.hi, o.lo);
+      for (int j2 = 0; j2 < BN; j2++) {
+        const int gn = n0 + j2;
+        if (gn >= N || (d.lowC && gm < gn)) continue;
+        const int64_t cnn = d.gatherN ? (int64_t)bases.kidx[d.nofs + gn] : (int64_t)gn;
+        float2* pc2 = reinterpret_cast<float2*>(C + gm + cnn * ldc);
+        df64 o = {0.f, 0.f};
+        if (beta != 0.0) {
+          const float2 v = *pc2;
+          o = df_scale({v.x, v.y}, (float)beta);
         }
+        *pc2 = make_float2(o.hi, o.lo);
       }
     }
   }
@@ -535,7 +531,7 @@ __global__ void __launch_bounds__(tc::NTHREADS, 1)
       mbar_wait(bDrain, 0, &never);
     }
     __syncwarp();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TMEM_COLS));
   }
 }
 
@@ -554,12 +550,13 @@ static int tc_sm_count() {
 
 void tc_gemm_run(const GemmBatch& g, const GemmBases& b, int M, cudaStream_t s) {
   const int mtiles = cdiv(M, tc::BM);
-  const int64_t ntiles = (int64_t)g.ntilesN64 * mtiles;
+  const int64_t ntiles = (int64_t)g.ntilesN32 * mtiles;
   if (ntiles == 0) return;
   RSF_CHECK(ntiles < (1ll << 31), RSF_EINVAL, "tensor-core gemm: too many tiles");
-  const int grid = (int)std::min<int64_t>(ntiles, tc_sm_count());
-  LAUNCH(tc_gemm_kernel, grid, tc::NTHREADS, tc::SMEM, s, g.desc.as<GemmDesc>(), g.prefix64.as<int>(), g.nprob,
-         g.ntilesN64, mtiles, b);
+  // persistent: two CTAs per SM (shared memory and TMEM columns allow two)
+  const int grid = (int)std::min<int64_t>(ntiles, 2 * (int64_t)tc_sm_count());
+  LAUNCH(tc_gemm_kernel, grid, tc::NTHREADS, tc::SMEM, s, g.desc.as<GemmDesc>(), g.ntile32.as<int2>(), g.ntilesN32,
+         mtiles, b);
 }
 
 // One column-major GEMM through a batch engine, for the self-check entry

@@ -172,7 +172,7 @@ def test_sqrt_trace_form_nugget_identity(B):
     assert abs(tn - exact) <= 1e-6 * abs(exact)
 
 
-@pytest.mark.parametrize("fam", [K.MATERN12, K.MATERN52])
+@pytest.mark.parametrize("fam", [K.MATERN12, K.MATERN52, K.MATERN1])
 def test_loglik_other_matern(B, fam):
     x = W.uniform(1500, 131)
     th = (0.08, 1.5, 5e-3)

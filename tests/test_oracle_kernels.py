@@ -73,3 +73,25 @@ def test_nugget_on_index_diagonal_not_on_location():
     x = np.array([[0.2, 0.2], [0.2, 0.2], [0.5, 0.1]])
     S = K.kernel_block(x, x, K.MATERN32, (0.1, 1.0, 0.5), K.SIGMA, 0.0, np.arange(3), np.arange(3))
     assert S[0, 0] == 1.5 and S[0, 1] == 1.0 and S[1, 1] == 1.5
+
+
+def _bessel_k_integral(nu, x, h=0.02):
+    """K_nu(x) = int_0^inf exp(-x cosh t) cosh(nu t) dt (DLMF 10.32.9) by the
+    trapezoid rule, exponentially convergent for this integrand: a pin of the
+    oracle's nu = 1 Matern kernel that shares nothing with its Bessel
+    routines."""
+    t = np.arange(0.0, np.arccosh(1.0 + 60.0 / x) + h, h)
+    f = np.exp(-x * np.cosh(t)) * np.cosh(nu * t)
+    return h * (f.sum() - 0.5 * f[0])
+
+
+def test_matern_nu1_against_the_bessel_integral():
+    # Matern nu = 1 (Eq. (matern)): k(r) = x K_1(x), d k / d l = x^2 K_0(x) / l
+    # with x = sqrt(2) r / l
+    l = 0.07
+    for r in (1e-4, 3e-3, 0.02, 0.07, 0.3, 1.1):
+        x = np.sqrt(2.0) * r / l
+        k_ref = x * _bessel_k_integral(1.0, x)
+        dk_ref = x * x * _bessel_k_integral(0.0, x) / l
+        assert K.correlation(np.array([r]), K.MATERN1, l)[0] == pytest.approx(k_ref, rel=1e-13)
+        assert K.dcorrelation_dl(np.array([r]), K.MATERN1, l)[0] == pytest.approx(dk_ref, rel=1e-13)
