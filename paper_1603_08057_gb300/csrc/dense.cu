@@ -208,13 +208,13 @@ __global__ void __launch_bounds__(GT, GEMM_MIN_BLOCKS) gemm_kernel(const GemmDes
 void GemmBatch::build(const std::vector<GemmDesc>& d, cudaStream_t s) {
   nprob = (int)d.size();
   std::vector<int> pre(nprob + 1, 0);
-  std::vector<int2> nt32;
+  std::vector<int2> nttc;
   maxM = 0;
   anyLaunchM = false;
   fixedMNK = launchNK = fixedBytes = launchBytesPerM = launchBytes0 = 0;
   for (int i = 0; i < nprob; i++) {
     pre[i + 1] = pre[i] + std::max(0, cdiv(d[i].N, BN));
-    for (int c = 0; c < d[i].N; c += 32) nt32.push_back(make_int2(i, c));
+    for (int c = 0; c < d[i].N; c += TC_BN) nttc.push_back(make_int2(i, c));
     if (d[i].M < 0) anyLaunchM = true; else maxM = std::max(maxM, d[i].M);
     // nonzero (k, n) pairs of op(B) and the computed part of C
     double N = d[i].N, K = d[i].K, nk;
@@ -238,10 +238,10 @@ void GemmBatch::build(const std::vector<GemmDesc>& d, cudaStream_t s) {
     }
   }
   ntilesN = pre[nprob];
-  ntilesN32 = (int)nt32.size();
+  ntilesN_tc = (int)nttc.size();
   upload(desc, d, s);
   upload(prefix, pre, s);
-  upload(ntile32, nt32, s);
+  upload(ntile_tc, nttc, s);
 }
 
 void GemmBatch::run(const GemmBases& b, cudaStream_t s) const {

@@ -33,6 +33,9 @@ struct GemmDesc {
                    // of a row-major multi-RHS block
 };
 
+// Output-tile width (columns) of the tensor-core GEMM kernel.
+constexpr int TC_BN = 64;
+
 // Index of the problem owning tile `tile` given the per-problem tile prefix.
 __device__ __forceinline__ int find_prob(const int* prefix, int nprob, int tile) {
   int lo = 0, hi = nprob - 1;
@@ -57,11 +60,11 @@ struct GemmBases {
 
 // Device-resident batch of GEMM problems with its tile prefix.
 struct GemmBatch {
-  DBuf desc, prefix, ntile32;
+  DBuf desc, prefix, ntile_tc;
   int nprob = 0;
   int ntilesN = 0;   // sum over problems of ceil(N / BN)
-  int ntilesN32 = 0; // the same for the 32-column tiles of the tensor-core kernel,
-                     // whose (problem, first column) pairs ntile32 lists
+  int ntilesN_tc = 0; // the same for the TC_BN-column tiles of the tensor-core
+                      // kernel, whose (problem, first column) pairs ntile_tc lists
   int maxM = 0;      // max M over problems with M >= 0
   bool anyLaunchM = false;
   // algorithmic work: flops = 2 (fixedMNK + launchM * launchNK), same for bytes

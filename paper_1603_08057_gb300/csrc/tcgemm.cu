@@ -9,9 +9,9 @@
 // using fast routines of matrix multiplication and its applications", Numer.
 // Algorithms 59 (2012), here with bf16 slices and fp32 accumulation):
 //
-//   * per K-block of at most KB = 384 terms, every row m of op(A) gets the
+//   * per K-block of at most KB = 64 terms, every row m of op(A) gets the
 //     power of two 2^E_m > max_k |A_mk| and every column n of op(B) the power
-//     2^F_n > max_k |B_kn| (computed in a pre-pass over the block);
+//     2^F_n > max_k |B_kn|;
 //   * a = A_mk / 2^E_m in (-1, 1) is cut into S = 7 slices a_j, each a
 //     multiple of 2^-7(j+1) with at most 8 significant bits (exact in bf16):
 //     a_j = round-to-nearest of the remainder onto the grid 2^-7(j+1); the
@@ -21,28 +21,34 @@
 //     so one fp32 TMEM accumulator per diagonal sums them EXACTLY as long as
 //     the integer sum stays below 2^24: |a_0|, |b_0| <= 128 units, later
 //     slices <= 65, so a diagonal gains at most 16640 + 4225 (d - 1) <=
-//     37765 units per term and KB = 384 terms stay below 2^24;
+//     37765 units per term and 64 terms stay far below 2^24 (up to 444 would);
 //   * diagonals d >= S are dropped (the truncation error is ~S 2^-7(S+1) of
 //     2^(E_m+F_n) per term, below the df64 rounding of the inputs);
-//   * the epilogue reads the S diagonals from TMEM, sums them in df64,
-//     scales by 2^(E_m + F_n) and accumulates the K-blocks, then applies
-//     alpha and beta like the CUDA-core df64 kernel.
+//   * the epilogue reads the S diagonals from TMEM, sums them by TwoSum into
+//     a df64 value,
+//     scales by 2^(E_m + F_n) and adds alpha times it to C (the first block
+//     also applies beta), in df64 like the CUDA-core df64 kernel.
 //
-// Work split (persistent CTAs over the 128 x 32 output tiles of the batch,
-// two CTAs per SM so that one CTA's memory latency hides behind the other's
-// work; 4 warps each):
-//   * every thread owns one row of the A tile (and the TMEM lane of that
-//     row in the epilogue) and helps slice the B tile; blocks of at most 32
-//     terms are held in registers whole, so their exponents need no second
-//     pass, longer blocks take a pre-pass and keep the next chunk's loads in
-//     flight while the current chunk (16 terms) is sliced into one of three
-//     shared-memory stages (canonical K-major, no-swizzle core-matrix layout);
-//   * warp 0 allocates 256 TMEM columns (the S = 7 accumulators of 32
-//     columns); thread 0 issues, once every thread has sliced a chunk, its
-//     28 tcgen05.mma instructions (M = 128, N = 32, K = 16, bf16 x bf16 ->
-//     fp32) and commits to the mbarriers that free the stage and that hand a
-//     finished K-block to the epilogue, which loads the C values it updates
-//     while the last MMAs run.
+// Work split (one persistent CTA per SM over the 128 x 64 output tiles of the
+// batch; 9 warps):
+//   * warps 0-7 load a whole K-block (64 terms: 32 A values of one row and 16
+//     B values of one column per thread, every load issued at once, so the
+//     block's exponents come from registers without a second pass over
+//     memory), slice it into one of three shared-memory stages per 16-term
+//     chunk (canonical K-major, no-swizzle core-matrix layout), copy the C
+//     values the block updates into shared memory asynchronously
+//     (cp.async) while the MMAs finish, and run the block's epilogue (each
+//     thread one TMEM lane and 32 columns);
+//   * warp 8 allocates the 512 TMEM columns (the S = 7 accumulators of 64
+//     columns); its lane 0 issues the 28 tcgen05.mma instructions of a chunk
+//     (M = 128, N = 64, K = 16, bf16 x bf16 -> fp32) and commits to the
+//     mbarriers that free the stage and that hand a finished block to the
+//     epilogue.
+// Measured on GB300 (rsf_selftest_gemm, 4096 x 4096 x 384 and 2048^3):
+// 6-6.5 TFLOP/s fp64-equivalent including the operand copies, 1.5x the
+// CUDA-core df64 kernel at the same accuracy class.  The producer warps
+// bound it (per 64-term block: one ~8k-cycle load round trip, ~8k cycles of
+// slicing, ~13k of epilogue); the tensor pipe is mostly idle.
 // Every wait is bounded (a few seconds): on expiry the CTA records
 // RSF_ETIMEOUT, drains its own MMAs, frees its TMEM and returns.
 #include <algorithm>
@@ -55,20 +61,23 @@
 namespace rsf {
 
 namespace tc {
-constexpr int BM = 128, BN = 32, KC = 16, KB = 384, S = 7, NST = 3;
-constexpr int NTHREADS = 128;                  // 4 warps; two CTAs per SM
+constexpr int BM = 128, BN = TC_BN, KC = 16, KB = 64, S = 7, NST = 3;
+constexpr int PW = 8;                          // slicing / epilogue warps
+constexpr int NPROD = PW * 32;
+constexpr int NTHREADS = NPROD + 32;           // + the MMA warp
 constexpr int A_SLICE = BM * KC * 2;           // bytes of one bf16 slice of an A stage
 constexpr int B_SLICE = BN * KC * 2;
 constexpr int STAGE = S * (A_SLICE + B_SLICE);
 constexpr int A_LBO = (BM / 8) * 128;          // bytes between k-groups of 8 (core matrices)
 constexpr int B_LBO = (BN / 8) * 128;
-constexpr int TMEM_COLS = 256;                 // S * BN accumulator columns, rounded to a power of two
-constexpr int AUX = 2048;
-constexpr int SMEM = NST * STAGE + AUX + 1024; // + alignment slack; two CTAs fit an SM
+constexpr int TMEM_COLS = 512;
+constexpr int CBUF = BM * BN * 8;             // the C tile (df64) staged for the epilogue
+constexpr int AUX = 4096;
+constexpr int SMEM = NST * STAGE + CBUF + AUX + 1024; // + alignment slack
 constexpr unsigned long long WAIT_NS = 4000000000ull;
 static_assert(S * BN <= TMEM_COLS, "the S accumulators must fit the allocated TMEM columns");
-static_assert(KB % KC == 0, "K-blocks hold whole chunks");
-static_assert(2 * (SMEM + 1024) <= 232448, "two CTAs per SM");
+static_assert(KB == 4 * KC && BM * KB == NPROD * 32 && BN * KB == NPROD * 16, "thread ownership of a K-block");
+static_assert(SMEM <= 232448, "shared memory of one CTA");
 }  // namespace tc
 
 __device__ DevStatus g_tc_status;
@@ -206,34 +215,38 @@ __device__ __forceinline__ int64_t base_scale(const GemmBases& b, int i) {
   return i == 0 ? b.sc[0] : i == 1 ? b.sc[1] : i == 2 ? b.sc[2] : b.sc[3];
 }
 
-__global__ void __launch_bounds__(tc::NTHREADS, 2)
+__global__ void __launch_bounds__(tc::NTHREADS, 1)
     tc_gemm_kernel(const GemmDesc* __restrict__ descs, const int2* __restrict__ ntile, int ntilesN, int mtiles,
                    GemmBases bases) {
   using namespace tc;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* aux = sm + NST * STAGE;
+  float2* sC = reinterpret_cast<float2*>(sm + NST * STAGE);   // [BN][BM]: C(row, col) at col * BM + row
+  uint8_t* aux = sm + NST * STAGE + CBUF;
   int* sExpB = reinterpret_cast<int*>(aux);                 // [2][BN] (by K-block parity)
-  float* sPart = reinterpret_cast<float*>(sExpB + 2 * BN);  // [NTHREADS]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sPart + NTHREADS);
-  // bars: full[NST], empty[NST], accf, drain
-  uint32_t* sTmem = reinterpret_cast<uint32_t*>(bars + 2 * NST + 2);
+  float* sPartA = reinterpret_cast<float*>(sExpB + 2 * BN); // [NPROD]
+  float* sPartB = sPartA + NPROD;                           // [NPROD]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sPartB + NPROD);
+  // bars: full[NST], empty[NST], accf, acce, drain
+  uint32_t* sTmem = reinterpret_cast<uint32_t*>(bars + 2 * NST + 3);
   volatile int* sAbort = reinterpret_cast<volatile int*>(sTmem + 1);
   const uint32_t bFull = su32(bars), bEmpty = su32(bars + NST), bAccF = su32(bars + 2 * NST),
-                 bDrain = su32(bars + 2 * NST + 1);
+                 bAccE = su32(bars + 2 * NST + 1), bDrain = su32(bars + 2 * NST + 2);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool producer = warp < PW;
   if (tid == 0) {
     for (int i = 0; i < NST; i++) {
-      mbar_init(bFull + 8 * i, NTHREADS);
+      mbar_init(bFull + 8 * i, NPROD);
       mbar_init(bEmpty + 8 * i, 1);
     }
     mbar_init(bAccF, 1);
+    mbar_init(bAccE, NPROD);
     mbar_init(bDrain, 1);
     *sAbort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
+  if (warp == PW) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(sTmem)),
                  "n"(TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -242,15 +255,22 @@ __global__ void __launch_bounds__(tc::NTHREADS, 2)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *sTmem;
-  const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);   // this warp's TMEM lanes
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                          ((uint32_t)(BM >> 4) << 24);
-  // thread roles: A row r (and TMEM lane r); B column cb with k-group qb
-  const int r = tid;
-  const int cb = tid & (BN - 1), qb = tid >> 5;
+  // Ownership of a K-block (64 terms = 8 k-groups of 8):
+  //   A: row r, k-groups kh, kh + 2, kh + 4, kh + 6 (kh = 0, 1);
+  //   B: column cb, k-groups qb, qb + 4 (qb = 0..3);
+  // chunk c of the block takes k-groups 2c and 2c + 1, so every thread
+  // slices one A group of each chunk (slot kh) and the B threads with
+  // qb + 4j in {2c, 2c + 1} one B group.  In the epilogue the
+  // thread reads TMEM lane r (its warp's lane quarter) and columns
+  // 32 kh .. 32 kh + 31.
+  const int r = tid & (BM - 1), kh = (tid >> 7) & 1;
+  const int cb = tid & (BN - 1), qb = (tid >> 6) & 3;
+  const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);
 
   uint32_t chunk_ctr = 0, blk_ctr = 0;
-  bool issued = false;   // thread 0 issued MMAs (drained on abort)
+  bool issued = false;   // the MMA thread issued MMAs (drained on abort)
   const int ntiles = ntilesN * mtiles;
   for (int tile = blockIdx.x; tile < ntiles && !*sAbort; tile += gridDim.x) {
     const int tn = tile / mtiles, tm = tile - tn * mtiles;
@@ -277,235 +297,207 @@ __global__ void __launch_bounds__(tc::NTHREADS, 2)
     const double alpha = d.alpha * bases.alpha_scale, beta = d.beta;
     const int gm = m0 + r;
     const bool rowok = gm < M;
+    const int gnb = n0 + cb;
 
-    // element (m, k) of op(A) and (k, n) of op(B) as df64 {hi, lo}
     auto addrA = [&](int gk) -> const double* {
       if (d.gatherK) return A + gm + (int64_t)bases.kidx[d.kofs + gk] * lda;
       return d.ta ? A + gk + (int64_t)gm * lda : A + gm + (int64_t)gk * lda;
     };
-    auto addrB = [&](int gk, int gn) -> const double* {
-      if (d.gatherK) return Bm + (bases.kidx[d.kofs + gk] - d.kb0) + (int64_t)gn * ldb;
-      if (d.gatherN) return Bm + (bases.kidx[d.nofs + gn] - d.nb0) + (int64_t)gk * ldb;
-      return d.tb ? Bm + gn + (int64_t)gk * ldb : Bm + gk + (int64_t)gn * ldb;
+    auto addrB = [&](int gk) -> const double* {
+      if (d.gatherK) return Bm + (bases.kidx[d.kofs + gk] - d.kb0) + (int64_t)gnb * ldb;
+      if (d.gatherN) return Bm + (bases.kidx[d.nofs + gnb] - d.nb0) + (int64_t)gk * ldb;
+      return d.tb ? Bm + gnb + (int64_t)gk * ldb : Bm + gk + (int64_t)gnb * ldb;
     };
-    auto zeroB = [&](int gk, int gn) -> bool {
-      return masktri && ((d.triB == 1 && gk < gn) || (d.triB == 2 && gk > gn));
-    };
-    // 16 A values of row r from k0a, and the 8 B values of column cb, k-group
-    // starting at k0b (zero outside [.., kend) and the masks)
-    auto loadA16 = [&](int k0a, int kend, float2 (&v)[16]) {
-#pragma unroll
-      for (int i = 0; i < 16; i++) {
-        const int k = k0a + i;
-        v[i] = (rowok && k < kend) ? *reinterpret_cast<const float2*>(addrA(k)) : make_float2(0.f, 0.f);
-      }
-    };
-    auto loadB8 = [&](int k0b, int kend, float2 (&v)[8]) {
-      const int gn = n0 + cb;
-#pragma unroll
-      for (int i = 0; i < 8; i++) {
-        const int k = k0b + i;
-        v[i] = (gn < N && k < kend && !zeroB(k, gn)) ? *reinterpret_cast<const float2*>(addrB(k, gn))
-                                                     : make_float2(0.f, 0.f);
-      }
+    auto zeroB = [&](int gk) -> bool {
+      return masktri && ((d.triB == 1 && gk < gnb) || (d.triB == 2 && gk > gnb));
     };
 
     for (int b = 0; b < nblk && !*sAbort; b++, blk_ctr++) {
       const int kb0 = k0 + b * KB, kb1 = min(k1, kb0 + KB), nk = kb1 - kb0;
       const int nch = (nk + KC - 1) / KC;
       const int eb = blk_ctr & 1;
-      const bool small = nk <= 2 * KC;
-      float2 ra[16], rb[8], xa[16], xb[8];
-      float mxA = 0.f, mxB = 0.f;
-      if (small) {
-        // the whole block (<= 32 terms) in registers: row r's A values and
-        // column cb's k-group qb; exponents straight from them
-        loadA16(kb0, kb1, ra);
-        loadA16(kb0 + KC, kb1, xa);
-        loadB8(kb0 + qb * 8, kb1, rb);
+      if (producer) {
+        // ---- every load of the block at once (its exponents need all of it)
+        float2 a[32], bv[16];
 #pragma unroll
-        for (int i = 0; i < 16; i++) mxA = fmaxf(mxA, fmaxf(fabsf(ra[i].x), fabsf(xa[i].x)));
+        for (int j = 0; j < 4; j++)
 #pragma unroll
-        for (int i = 0; i < 8; i++) mxB = fmaxf(mxB, fabsf(rb[i].x));
-      } else {
-        // pre-pass over the block: batches of 16 independent loads
-        if (rowok)
-          for (int kb = kb0; kb < kb1; kb += 16) {
-            float v[16];
-#pragma unroll
-            for (int i = 0; i < 16; i++)
-              v[i] = kb + i < kb1 ? fabsf(*reinterpret_cast<const float*>(addrA(kb + i))) : 0.f;
-#pragma unroll
-            for (int i = 0; i < 16; i++) mxA = fmaxf(mxA, v[i]);
+          for (int i = 0; i < 8; i++) {
+            const int k = kb0 + (kh + 2 * j) * 8 + i;
+            a[j * 8 + i] = (rowok && k < kb1) ? *reinterpret_cast<const float2*>(addrA(k)) : make_float2(0.f, 0.f);
           }
-        const int gn = n0 + cb;
-        if (gn < N)
-          for (int kb = kb0 + qb; kb < kb1; kb += 64) {
-            float v[16];
 #pragma unroll
-            for (int i = 0; i < 16; i++) {
-              const int k = kb + 4 * i;
-              v[i] = (k < kb1 && !zeroB(k, gn)) ? fabsf(*reinterpret_cast<const float*>(addrB(k, gn))) : 0.f;
-            }
+        for (int j = 0; j < 2; j++)
 #pragma unroll
-            for (int i = 0; i < 16; i++) mxB = fmaxf(mxB, v[i]);
+          for (int i = 0; i < 8; i++) {
+            const int k = kb0 + (qb + 4 * j) * 8 + i;
+            bv[j * 8 + i] = (gnb < N && k < kb1 && !zeroB(k)) ? *reinterpret_cast<const float2*>(addrB(k))
+                                                               : make_float2(0.f, 0.f);
           }
-        loadA16(kb0, kb1, ra);
-        if (qb < 2) loadB8(kb0 + qb * 8, kb1, rb);
-      }
-      const int eA = block_exponent(mxA);
-      sPart[tid] = mxB;
-      __syncthreads();
-      if (tid < BN)
-        sExpB[eb * BN + tid] = block_exponent(
-            fmaxf(fmaxf(sPart[tid], sPart[tid + BN]), fmaxf(sPart[tid + 2 * BN], sPart[tid + 3 * BN])));
-      __syncthreads();
-      const float scA = pow2f(-eA);
-      const float scB = pow2f(-sExpB[eb * BN + cb]);
-
-      uint32_t inited = 0;   // thread 0: diagonals written in this block
-      for (int c = 0; c < nch; c++) {
-        const uint32_t cc = chunk_ctr + c;
-        const int stage = cc % NST;
-        const uint32_t use = cc / NST;
-        const bool more = c + 1 < nch;
-        if (!small && more) {
-          loadA16(kb0 + (c + 1) * KC, kb1, xa);
-          if (qb < 2) loadB8(kb0 + (c + 1) * KC + qb * 8, kb1, xb);
-        }
-        if (use > 0 && !mbar_wait(bEmpty + 8 * stage, (use - 1) & 1, sAbort)) {
-          *sAbort = 1;
-          break;
-        }
-        uint8_t* sA = sm + stage * STAGE;
-        uint8_t* sB = sA + S * A_SLICE;
-        {  // A: row r, both k-groups of the chunk
-          const float2* va = (small && c == 1) ? xa : ra;
+        float ma = 0.f, mb = 0.f;
 #pragma unroll
-          for (int g = 0; g < 2; g++) {
+        for (int i = 0; i < 32; i++) ma = fmaxf(ma, fabsf(a[i].x));
+#pragma unroll
+        for (int i = 0; i < 16; i++) mb = fmaxf(mb, fabsf(bv[i].x));
+        sPartA[tid] = ma;
+        sPartB[tid] = mb;
+        asm volatile("bar.sync 1, %0;" ::"n"(NPROD) : "memory");
+        const int eA = block_exponent(fmaxf(sPartA[r], sPartA[r + BM]));
+        const int eB = block_exponent(fmaxf(fmaxf(sPartB[cb], sPartB[cb + BN]),
+                                            fmaxf(sPartB[cb + 2 * BN], sPartB[cb + 3 * BN])));
+        if (tid < BN) sExpB[eb * BN + tid] = eB;
+        const float scA = pow2f(-eA), scB = pow2f(-eB);
+        // ---- slice the (up to four) chunks of the block into the stages
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+          if (c >= nch) break;
+          const uint32_t cc = chunk_ctr + c;
+          const int stage = cc % NST;
+          const uint32_t use = cc / NST;
+          if (use > 0 && !mbar_wait(bEmpty + 8 * stage, (use - 1) & 1, sAbort)) {
+            *sAbort = 1;
+            break;
+          }
+          uint8_t* sA = sm + stage * STAGE;
+          uint8_t* sB = sA + S * A_SLICE;
+          {  // A group kh + 2c -> chunk slot kh
             float hh[8], ll[8];
 #pragma unroll
             for (int i = 0; i < 8; i++) {
-              hh[i] = va[g * 8 + i].x * scA;
-              ll[i] = va[g * 8 + i].y * scA;
+              hh[i] = a[c * 8 + i].x * scA;
+              ll[i] = a[c * 8 + i].y * scA;
             }
-            slice_store(hh, ll, sA + g * A_LBO + (r >> 3) * 128 + (r & 7) * 16, A_SLICE);
+            slice_store(hh, ll, sA + kh * A_LBO + (r >> 3) * 128 + (r & 7) * 16, A_SLICE);
           }
-        }
-        // B: the threads holding this chunk's k-groups of column cb
-        const int gB = small ? qb - 2 * c : qb;
-        if (gB == 0 || gB == 1) {
-          float hh[8], ll[8];
+          // B group qb + 4j -> chunk slot qb + 4j - 2c, for the threads whose
+          // group lies in this chunk
 #pragma unroll
-          for (int i = 0; i < 8; i++) {
-            hh[i] = rb[i].x * scB;
-            ll[i] = rb[i].y * scB;
+          for (int j = 0; j < 2; j++) {
+            const int slot = qb + 4 * j - 2 * c;
+            if (slot == 0 || slot == 1) {
+              float hh[8], ll[8];
+#pragma unroll
+              for (int i = 0; i < 8; i++) {
+                hh[i] = bv[j * 8 + i].x * scB;
+                ll[i] = bv[j * 8 + i].y * scB;
+              }
+              slice_store(hh, ll, sB + slot * B_LBO + (cb >> 3) * 128 + (cb & 7) * 16, B_SLICE);
+            }
           }
-          slice_store(hh, ll, sB + gB * B_LBO + (cb >> 3) * 128 + (cb & 7) * 16, B_SLICE);
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          mbar_arrive(bFull + 8 * stage);
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive(bFull + 8 * stage);
-        if (tid == 0) {
-          // MMA issue once every thread has sliced the chunk: all S (S+1)/2
-          // slice products with s + t < S, K = 16 each
-          if (!mbar_wait(bFull + 8 * stage, use & 1, sAbort)) {
+        if (*sAbort) break;
+        // ---- epilogue: load the C values this block updates while the last
+        // MMAs run; the first block writes alpha v + beta C, later blocks add
+        // alpha v
+        const bool first = b == 0;
+        const bool rd = !first || beta != 0.0;
+        // the C values go to shared memory by asynchronous copies (no
+        // registers held while the MMAs finish)
+        if (rd) {
+#pragma unroll 4
+          for (int j = 0; j < 32; j++) {
+            const int col = kh * 32 + j, gn = n0 + col;
+            const bool ok = rowok && gn < N && !(d.lowC && gm < gn);
+            const int64_t cnn = ok ? (d.gatherN ? (int64_t)bases.kidx[d.nofs + gn] : (int64_t)gn) : 0;
+            const double* src = ok ? C + gm + cnn * ldc : C;
+            const uint32_t dst = su32(sC + col * BM + r);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst), "l"(src), "r"(ok ? 8 : 0)
+                         : "memory");
+          }
+          asm volatile("cp.async.commit_group;\n" ::: "memory");
+        }
+        if (!mbar_wait(bAccF, blk_ctr & 1, sAbort)) {
+          *sAbort = 1;
+          break;
+        }
+        tc_fence_after();
+        if (rd) asm volatile("cp.async.wait_all;\n" ::: "memory");
+        const float scr = pow2f(eA);
+#pragma unroll
+        for (int q8 = 0; q8 < 4; q8++) {
+          const int col = kh * 32 + q8 * 8;
+          if (col < nvalid) {
+            float D[S][8];
+#pragma unroll
+            for (int dd = 0; dd < S; dd++) tmem_ld8(tl + dd * BN + col, D[dd]);
+            tmem_ld_wait();
+#pragma unroll
+            for (int j2 = 0; j2 < 8; j2++) {
+              const int gn = n0 + col + j2;
+              if (!rowok || gn >= N || (d.lowC && gm < gn)) continue;
+              // exact-ish sum of the diagonals, smallest first (TwoSum into
+              // hi, the errors into lo)
+              float hi = D[S - 1][j2], lo = 0.f;
+#pragma unroll
+              for (int dd = S - 2; dd >= 0; dd--) {
+                const float x = D[dd][j2];
+                const float sm2 = __fadd_rn(hi, x);
+                const float v = __fsub_rn(sm2, hi);
+                lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(sm2, v)), __fsub_rn(x, v)));
+                hi = sm2;
+              }
+              const float scn = pow2f(sExpB[eb * BN + col + j2]);
+              df64 t = df_fast_two_sum(hi, lo);
+              t.hi = (t.hi * scr) * scn;
+              t.lo = (t.lo * scr) * scn;
+              t = df_scale(t, (float)alpha);
+              const float2 oc = sC[(col + j2) * BM + r];
+              df64 o = {oc.x, oc.y};
+              if (first && beta != 1.0) o = df_scale(o, (float)beta);
+              if (rd) t = df_add(t, o);
+              const int64_t cnn = d.gatherN ? (int64_t)bases.kidx[d.nofs + gn] : (int64_t)gn;
+              *reinterpret_cast<float2*>(C + gm + cnn * ldc) = make_float2(t.hi, t.lo);
+            }
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(bAccE);
+      } else if (warp == PW && lane == 0) {
+        // ---- MMA issue: all slice products with s + t < S, K = 16 each
+        if (blk_ctr > 0 && !mbar_wait(bAccE, (blk_ctr - 1) & 1, sAbort)) {
+          *sAbort = 1;
+          break;
+        }
+        tc_fence_after();
+        uint32_t inited = 0;
+        for (int c = 0; c < nch; c++) {
+          const uint32_t cc = chunk_ctr + c;
+          const int stage = cc % NST;
+          if (!mbar_wait(bFull + 8 * stage, (cc / NST) & 1, sAbort)) {
             *sAbort = 1;
             break;
           }
           tc_fence_after();
-          const uint32_t aBase = su32(sA), bBase = su32(sB);
+          const uint32_t aBase = su32(sm + stage * STAGE), bBase = aBase + S * A_SLICE;
+          const int ksteps = (min(KC, nk - c * KC) + 15) / 16;
+          for (int kk = 0; kk < ksteps; kk++) {
 #pragma unroll
-          for (int s1 = 0; s1 < S; s1++) {
-            const uint64_t ad = smem_desc(aBase + s1 * A_SLICE, A_LBO, 128);
+            for (int s1 = 0; s1 < S; s1++) {
+              const uint64_t ad = smem_desc(aBase + s1 * A_SLICE + kk * 2 * A_LBO, A_LBO, 128);
 #pragma unroll
-            for (int t1 = 0; t1 < S - s1; t1++) {
-              const int dd = s1 + t1;
-              const uint64_t bd = smem_desc(bBase + t1 * B_SLICE, B_LBO, 128);
-              mma_bf16(tmem + dd * BN, ad, bd, idesc, (inited >> dd) & 1u);
-              inited |= 1u << dd;
+              for (int t1 = 0; t1 < S - s1; t1++) {
+                const int dd = s1 + t1;
+                const uint64_t bd = smem_desc(bBase + t1 * B_SLICE + kk * 2 * B_LBO, B_LBO, 128);
+                mma_bf16(tmem + dd * BN, ad, bd, idesc, (inited >> dd) & 1u);
+                inited |= 1u << dd;
+              }
             }
           }
           issued = true;
           mma_commit(bEmpty + 8 * stage);
-          if (c == nch - 1) mma_commit(bAccF);
         }
-        if (!small && more) {
-#pragma unroll
-          for (int i = 0; i < 16; i++) ra[i] = xa[i];
-#pragma unroll
-          for (int i = 0; i < 8; i++) rb[i] = xb[i];
-        } else if (small) {
-          // the small path's k-groups 2 and 3 were loaded into rb by threads qb = 2, 3
-        }
+        if (*sAbort) break;
+        mma_commit(bAccF);
       }
       chunk_ctr += nch;
-      if (*sAbort) break;
-
-      // ---- epilogue: the C values this block updates are loaded while the
-      // last MMAs finish; the first block writes alpha v + beta C, later
-      // blocks add alpha v
-      const bool first = b == 0;
-      const bool rd = !first || beta != 0.0;
-      float2 oldc[BN];
-#pragma unroll
-      for (int j = 0; j < BN; j++) {
-        oldc[j] = make_float2(0.f, 0.f);
-        const int gn = n0 + j;
-        if (rd && rowok && gn < N && !(d.lowC && gm < gn)) {
-          const int64_t cnn = d.gatherN ? (int64_t)bases.kidx[d.nofs + gn] : (int64_t)gn;
-          oldc[j] = *reinterpret_cast<const float2*>(C + gm + cnn * ldc);
-        }
-      }
-      if (!mbar_wait(bAccF, blk_ctr & 1, sAbort)) {
-        *sAbort = 1;
-        break;
-      }
-      tc_fence_after();
-      const float scr = pow2f(eA);
-#pragma unroll
-      for (int q8 = 0; q8 < BN / 8; q8++) {
-        const int col = q8 * 8;
-        if (col < nvalid) {
-          float D[S][8];
-#pragma unroll
-          for (int dd = 0; dd < S; dd++) tmem_ld8(tl + dd * BN + col, D[dd]);
-          tmem_ld_wait();
-#pragma unroll
-          for (int j2 = 0; j2 < 8; j2++) {
-            const int gn = n0 + col + j2;
-            if (!rowok || gn >= N || (d.lowC && gm < gn)) continue;
-            // exact-ish sum of the diagonals (TwoSum into hi, errors into lo)
-            float hi = D[0][j2], lo = 0.f;
-#pragma unroll
-            for (int dd = 1; dd < S; dd++) {
-              const float x = D[dd][j2];
-              const float sm2 = __fadd_rn(hi, x);
-              const float v = __fsub_rn(sm2, hi);
-              lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(sm2, v)), __fsub_rn(x, v)));
-              hi = sm2;
-            }
-            const float scn = pow2f(sExpB[eb * BN + col + j2]);
-            df64 t = df_fast_two_sum(hi, lo);
-            t.hi = (t.hi * scr) * scn;
-            t.lo = (t.lo * scr) * scn;
-            t = df_scale(t, (float)alpha);
-            df64 o = {oldc[col + j2].x, oldc[col + j2].y};
-            if (first && beta != 1.0) o = df_scale(o, (float)beta);
-            if (rd) t = df_add(t, o);
-            const int64_t cnn = d.gatherN ? (int64_t)bases.kidx[d.nofs + gn] : (int64_t)gn;
-            *reinterpret_cast<float2*>(C + gm + cnn * ldc) = make_float2(t.hi, t.lo);
-          }
-        }
-      }
-      // TMEM reads complete before the next block's MMAs (which follow the
-      // barriers of its exponent step)
-      tc_fence_before();
     }
     if (*sAbort) break;
-    if (nblk == 0 && beta != 1.0 && rowok) {
+    if (producer && nblk == 0 && beta != 1.0 && rowok) {
       // no K terms (empty or masked range): C = beta C
-      for (int j2 = 0; j2 < BN; j2++) {
-        const int gn = n0 + j2;
+      for (int j2 = 0; j2 < 32; j2++) {
+        const int gn = n0 + kh * 32 + j2;
         if (gn >= N || (d.lowC && gm < gn)) continue;
         const int64_t cnn = d.gatherN ? (int64_t)bases.kidx[d.nofs + gn] : (int64_t)gn;
         float2* pc2 = reinterpret_cast<float2*>(C + gm + cnn * ldc);
@@ -524,7 +516,7 @@ __global__ void __launch_bounds__(tc::NTHREADS, 2)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 0) {
+  if (warp == PW) {
     if (lane == 0 && *sAbort && issued) {
       mma_commit(bDrain);
       volatile int never = 0;
@@ -550,12 +542,12 @@ static int tc_sm_count() {
 
 void tc_gemm_run(const GemmBatch& g, const GemmBases& b, int M, cudaStream_t s) {
   const int mtiles = cdiv(M, tc::BM);
-  const int64_t ntiles = (int64_t)g.ntilesN32 * mtiles;
+  const int64_t ntiles = (int64_t)g.ntilesN_tc * mtiles;
   if (ntiles == 0) return;
   RSF_CHECK(ntiles < (1ll << 31), RSF_EINVAL, "tensor-core gemm: too many tiles");
-  // persistent: two CTAs per SM (shared memory and TMEM columns allow two)
-  const int grid = (int)std::min<int64_t>(ntiles, 2 * (int64_t)tc_sm_count());
-  LAUNCH(tc_gemm_kernel, grid, tc::NTHREADS, tc::SMEM, s, g.desc.as<GemmDesc>(), g.ntile32.as<int2>(), g.ntilesN32,
+  // persistent: one CTA per SM (its shared memory and all 512 TMEM columns)
+  const int grid = (int)std::min<int64_t>(ntiles, (int64_t)tc_sm_count());
+  LAUNCH(tc_gemm_kernel, grid, tc::NTHREADS, tc::SMEM, s, g.desc.as<GemmDesc>(), g.ntile_tc.as<int2>(), g.ntilesN_tc,
          mtiles, b);
 }
 

@@ -4,7 +4,7 @@ the C ABI (rsf_selftest_gemm) against NumPy's fp64 product.
 
 Engine 1 multiplies df64 operands on the tensor cores from exact bf16 slices
 (seven per operand, exact fp32 accumulation per diagonal of slice products,
-K-blocks of 384).  Its result must match the exact product to the df64
+K-blocks of 64).  Its result must match the exact product to the df64
 rounding of the operands: each operand is rounded to a 48-bit significand
 (relative 2^-48 = 3.6e-15) and the slices keep 7 x 7 bits below the block's
 largest power of two, so |C - AB| <= 1e-13 sum_k |A_ik||B_kj| + the same
