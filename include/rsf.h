@@ -119,9 +119,11 @@ typedef struct {
                        F^-1 (z - Sigma alpha), the residual taken against
                        the exact kernel matrix by an on-the-fly O(n^2)
                        matvec (df64 on the fp32 pipes for the Matern
-                       families, fp64 otherwise), so that z^T alpha does
-                       not carry the factorization's eps_fact error.
-                       -1 (default): 1 in the mixed forms, 0 in fp64 */
+                       1/2, 3/2, 5/2 kernels and the rational quadratic
+                       with integer alpha <= 8, fp64 otherwise), so that
+                       z^T alpha does not carry the factorization's
+                       eps_fact error.  -1 (default): 1 in the mixed forms
+                       where the matvec runs in df64, else 0 */
 } rsf_opts;
 
 enum { RSF_TRACE_SYM = 0, RSF_TRACE_SQRT = 1 };

@@ -250,7 +250,10 @@ static rsf_handle_s* make_handle(std::shared_ptr<rsf_tree_s> tree, const rsf_ker
 
 int refine_sweeps(const rsf_handle_s* F) {
   if (!F->spd) return 0;
-  return F->opts.refine >= 0 ? F->opts.refine : (F->opts.precision != RSF_PREC_FP64 ? 1 : 0);
+  // default: one sweep in the mixed forms where the residual runs in df64
+  // (Matern 1/2, 3/2, 5/2; rational quadratic with integer alpha)
+  if (F->opts.refine >= 0) return F->opts.refine;
+  return F->opts.precision != RSF_PREC_FP64 && residual_uses_df64(F->kp) ? 1 : 0;
 }
 
 }  // namespace rsf

@@ -15,8 +15,12 @@
 //     four squarings ("scaling and squaring", J.-M. Muller, Elementary
 //     Functions, ch. 11); the square root is one Newton step in df64 from the
 //     fp32 root;
-//   * every other family (rational quadratic): fp64 with the library's fp64
-//     kernel evaluation.
+//   * rational quadratic with an integer shape alpha = 1..8: df64 as well,
+//     (1 + r^2 / (2 alpha l^2))^-alpha from a df64 reciprocal (one Newton
+//     step from the fp32 one) raised by repeated multiplication;
+//   * every other kernel (Matern nu = 1, rational quadratic with other
+//     alpha): fp64 with the library's fp64 kernel evaluation (O(n^2) fp64
+//     work: slow at large n, so not run by default, see refine_sweeps).
 // Both accumulate each row's sum in df64 (error-free products and sums), so
 // the residual carries ~1e-14 relative rounding of sum_j |K_ij alpha_j|.
 //
@@ -90,10 +94,29 @@ __device__ __forceinline__ df64 d_exp_neg(df64 a) {
 // a = sqrt5 r/l (Sec. 1 Eq. (matern) at half-integer nu).
 struct MaternDF {
   int family;
-  df64 c;       // a = c r
+  df64 c;       // a = c r (Matern); 1 / (2 alpha l^2) (rational quadratic)
   df64 s2;
   df64 third;   // 1/3
+  int alpha;    // rational quadratic: integer shape
 };
+
+__device__ __forceinline__ df64 d_recip(df64 u) {
+  const float y = __fdiv_rn(1.f, u.hi);
+  // t = 1 - u y, evaluated with the exact product u.hi y
+  const float p = __fmul_rn(u.hi, y);
+  const float pe = __fmaf_rn(u.hi, y, -p);
+  const float t = __fsub_rn(__fsub_rn(__fsub_rn(1.f, p), pe), __fmul_rn(u.lo, y));
+  return df_fast_two_sum(y, __fmul_rn(y, t));
+}
+
+// s2 (1 + r^2 c)^-alpha for the rational quadratic with integer alpha
+__device__ __forceinline__ df64 rq_df(const MaternDF& m, df64 r2) {
+  const df64 u = df_add({1.f, 0.f}, d_mul(r2, m.c));
+  const df64 inv = d_recip(u);
+  df64 p = inv;
+  for (int i = 1; i < m.alpha; i++) p = d_mul(p, inv);
+  return d_mul(m.s2, p);
+}
 
 __device__ __forceinline__ df64 matern_df(const MaternDF& m, df64 r) {
   const df64 a = d_mul(m.c, r);
@@ -175,7 +198,8 @@ __global__ void __launch_bounds__(RT) residual_kernel(const double* __restrict__
           } else {
             const df64 dx = d_sub(xid, dx_s[jj]);
             const df64 dy = d_sub(yid, dy_s[jj]);
-            v = matern_df(md, d_sqrt(df_add(d_mul(dx, dx), d_mul(dy, dy))));
+            const df64 r2 = df_add(d_mul(dx, dx), d_mul(dy, dy));
+            v = md.family == RSF_RQ ? rq_df(md, r2) : matern_df(md, d_sqrt(r2));
           }
           df_mac(acc, v, dv_s[jj]);
         } else {
@@ -233,6 +257,7 @@ df64 host_df(double v) {
 }  // namespace
 
 bool residual_uses_df64(const KernelParams& kp) {
+  if (kp.family == RSF_RQ) return kp.alpha >= 1.0 && kp.alpha <= 8.0 && kp.alpha == std::floor(kp.alpha);
   return kp.family == RSF_MATERN12 || kp.family == RSF_MATERN32 || kp.family == RSF_MATERN52;
 }
 
@@ -245,7 +270,8 @@ void kernel_residual(rsf_handle_s* F, const double* zt, const double* xt_vec, do
   MaternDF md{};
   md.family = kp.family;
   const double c = kp.family == RSF_MATERN32 ? std::sqrt(3.0) : kp.family == RSF_MATERN52 ? std::sqrt(5.0) : 1.0;
-  md.c = host_df(c / kp.l);
+  md.c = host_df(kp.family == RSF_RQ ? 1.0 / (2.0 * kp.alpha * kp.l * kp.l) : c / kp.l);
+  md.alpha = kp.family == RSF_RQ ? (int)kp.alpha : 0;
   md.s2 = host_df(kp.s2);
   md.third = host_df(1.0 / 3.0);
   const bool df = residual_uses_df64(kp) && !force_fp64;

@@ -4,11 +4,15 @@ alpha = 2, l = 0.02, s2 = 1, nugget 1e-2, eps_fact 1e-9.
 z is F^1/2 w of the plain fp64 GPU factorization at eps_fact = 1e-12
 (Sec. 2.3.2), w ~ N(0, I) (seed 8).  Checked:
 
-* the mixed form (df64 solves) against the plain fp64 form on the same
-  points, theta and z: log|F| identical (both forms factor in fp64),
-  z^T F^-1 z and the log-likelihood within 1e-10 relative (the df64 solve's
-  rounding, ~1e-14 per product, times the conditioning; measured values are
-  printed);
+* the mixed form (df64 operands, tensor-core products) against the plain
+  fp64 form on the same points, theta and z, both without refinement:
+  log|F| identical (both forms factor in fp64), z^T F^-1 z and the
+  log-likelihood within 1e-10 relative (the products' rounding, ~1e-14,
+  times the conditioning; measured 2.1e-15 and 3.6e-15 with the CUDA-core
+  df64 products);
+* the refined quadratic form (one sweep against the exact Sigma, df64
+  residual) differs from the unrefined one by at most 1e-6 relative (the
+  factorization's error; measured 7e-9 against the fp64 form);
 * both forms against the dense oracle on a 16,384-point subsample (seed 9)
   of the same points: log-likelihood 1e-6 relative, score 1e-3 relative and
   1e-5 of the term scale;
@@ -55,23 +59,28 @@ def test_1m_mixed_vs_fp64_and_sampled_rows(B, pts):
     z = F12.solve(T(W.standard_normal(n, WL["seed_z"])), B.OP_SQRT)
     del F12
     out = {}
-    for prec in (0, 1):
-        F = B.Factorization(P, B.RQ, th, B.SIGMA, WL["tol_fact"], a, B.opts(precision=prec))
+    for prec, refine in ((0, 0), (1, 0), (1, 1)):
+        F = B.Factorization(P, B.RQ, th, B.SIGMA, WL["tol_fact"], a, B.opts(precision=prec, refine=refine))
         ll, quad, _ = F.loglik(z)
-        out[prec] = (ll, quad, F.logdet())
-        if prec == 1:
+        out[(prec, refine)] = (ll, quad, F.logdet())
+        if prec == 1 and refine == 0:
             x = W.standard_normal(n, 10)
             y = F.solve(T(x), B.OP_APPLY).cpu().numpy()
             rows = np.random.default_rng(11).choice(n, 32, replace=False)
             Kr = K.kernel_block(pts[rows], pts, K.RQ, th, K.SIGMA, a, ia=rows, ib=np.arange(n))
             assert np.all(np.abs(y[rows] - Kr @ x) <= 1e-8 * (np.abs(Kr) @ np.abs(x)))
         del F
-    (ll0, q0, ld0), (ll1, q1, ld1) = out[0], out[1]
-    print(f"n=1048576 RQ: loglik fp64 {ll0!r} mixed {ll1!r}; rel diff loglik {abs(ll1 - ll0) / abs(ll0):.3e}, "
-          f"quad {abs(q1 - q0) / abs(q0):.3e}, logdet {abs(ld1 - ld0) / abs(ld0):.3e}")
-    assert ld0 == ld1
+    (ll0, q0, ld0), (ll1, q1, ld1), (ll2, q2, ld2) = out[(0, 0)], out[(1, 0)], out[(1, 1)]
+    print(f"n=1048576 RQ: loglik fp64 {ll0!r} mixed {ll1!r} mixed+refinement {ll2!r}; mixed vs fp64: loglik "
+          f"{abs(ll1 - ll0) / abs(ll0):.3e}, quad {abs(q1 - q0) / abs(q0):.3e}, logdet {abs(ld1 - ld0) / abs(ld0):.3e}; "
+          f"refinement moved quad by {abs(q2 - q1) / abs(q1):.3e}")
+    # the same factorization and solve in both forms: df64 rounding only
+    assert ld0 == ld1 == ld2
     assert abs(q1 - q0) <= 1e-10 * abs(q0)
     assert abs(ll1 - ll0) <= 1e-10 * abs(ll0)
+    # the refinement corrects z^T F^-1 z toward z^T Sigma^-1 z by about the
+    # factorization's error (eps_fact = 1e-9 amplified by the conditioning)
+    assert abs(q2 - q1) <= 1e-6 * abs(q1)
 
 
 @pytest.mark.parametrize("prec", [0, 1])

@@ -5,8 +5,9 @@ Without refinement the quadratic form z^T F^-1 z carries the factorization's
 error (eps_fact = 1e-9, measured ~3e-10 relative against dense on 16,384
 clustered points).  One sweep alpha += F^-1 (z - Sigma alpha), with the
 residual from an on-the-fly matvec of the exact kernel (df64 with a
-project-written exp for the Matern families, fp64 for the rational
-quadratic), must bring z^T alpha to the dense Cholesky value within 1e-11
+project-written exp for Matern 1/2, 3/2, 5/2 and a df64 reciprocal for the
+rational quadratic with integer alpha; fp64 for Matern 1 and other alpha),
+must bring z^T alpha to the dense Cholesky value within 1e-11
 relative: the residual's rounding (~1e-14 of sum_j |K_ij alpha_j|) times the
 conditioning seen by z, plus eps_fact^2-sized terms.  The log-likelihood then
 differs from dense only by the log-determinant's error.
@@ -42,10 +43,12 @@ CASES = [  # family, alpha, theta, points, n
     (K.MATERN12, 0.0, (0.08, 1.5, 5e-3), "uniform", 2000),
     (K.MATERN52, 0.0, (0.08, 1.5, 5e-3), "uniform", 2000),
     (K.RQ, 1.0, (0.05, 1.0, 1e-3), "mixture", 3000),
+    (K.RQ, 2.5, (0.05, 1.0, 1e-3), "mixture", 2000),
+    (K.MATERN1, 0.0, (0.08, 1.5, 5e-3), "uniform", 1500),
 ]
 
 
-@pytest.mark.parametrize("case", CASES, ids=["matern32", "matern12", "matern52", "rq"])
+@pytest.mark.parametrize("case", CASES, ids=["matern32", "matern12", "matern52", "rq1", "rq2.5", "matern1"])
 def test_refinement_reaches_dense_quadratic_form(B, case):
     fam, alpha, th, kind, n = case
     x = W.make_points(kind, n, 501)
