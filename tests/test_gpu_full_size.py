@@ -117,19 +117,18 @@ def test_full_size_score_traces_match_logdet_derivatives(B, pts):
 
 def test_full_size_score_vs_loglik_differences(B, pts):
     # Eq. (gradient): g_k = d loglik / d theta_k.  Reference: central
-    # differences (h = 1e-3 theta_k) of the RSF log-likelihood at
-    # eps_fact = 1e-12 in plain fp64 (log-determinant and quadratic form
-    # accurate to ~1e-11 relative; the differences carry ~1e-6 relative
-    # error, the O(h^2) truncation).  The score under test is the benchmark's
-    # configuration (mixed precision, eps_fact 1e-9, eps_peel 1e-6) at theta
-    # of one benchmark step (l * 1.005); z = F^1/2 w drawn at the workload's
-    # theta.  Here g_l and g_s2 are only 2e-4 and 1.6e-4 of their term scale
-    # (|quad_k| + |trace_k|) / 2, and the measured errors, 3.1e-7 and 1.7e-7
-    # of that scale, do not shrink when eps_peel goes from 1e-6 to 1e-7 (they
-    # come from the eps_fact = 1e-9 factorizations): the plain 1e-3 relative
-    # bar is met by the well-conditioned component (|g_k| >= 1e-3 of its
-    # scale: g_nug, measured 2.2e-4) and every component meets 1e-6 of its
-    # term scale (g_l, g_s2 are at 1.6e-3 and 1.1e-3 relative).
+    # differences of the RSF log-likelihood at eps_fact = 1e-12 in plain fp64,
+    # Richardson-extrapolated from the steps h = 1e-3 theta_k and h / 2 (the
+    # O(h^2) term of a single difference is not small here: the score
+    # components are small differences of terms of size ~n, and so is the
+    # third derivative, which put a plain h = 1e-3 difference ~0.4 off g_l).
+    # The extrapolated reference carries the log-likelihood's rounding and
+    # rank-decision noise (~1e-6 absolute at eps_fact = 1e-12) divided by the
+    # step, ~0.02.  The score under test is the benchmark's configuration
+    # (mixed precision, eps_fact 1e-9, eps_peel 1e-6) at theta of one
+    # benchmark step (l * 1.005); z = F^1/2 w drawn at the workload's theta.
+    # Bars: 1e-3 relative per component, and 1e-6 of the term scale
+    # (|quad_k| + |trace_k|) / 2.
     n = WL["n"]
     th0 = WL["theta"]
     P = T(pts)
@@ -147,17 +146,17 @@ def test_full_size_score_vs_loglik_differences(B, pts):
         del Fh
         return v
 
+    def central(k, h):
+        up, dn = list(th), list(th)
+        up[k] += h * th[k]
+        dn[k] -= h * th[k]
+        return (loglik_at(tuple(up)) - loglik_at(tuple(dn))) / (2.0 * h * th[k])
+
     fd = np.zeros(3)
     for k in range(3):
-        step = 1e-3 * th[k]
-        up, dn = list(th), list(th)
-        up[k] += step
-        dn[k] -= step
-        fd[k] = (loglik_at(tuple(up)) - loglik_at(tuple(dn))) / (2.0 * step)
+        fd[k] = (4.0 * central(k, 5e-4) - central(k, 1e-3)) / 3.0
     scale = 0.5 * np.abs(t[:3]) + 0.5 * np.abs(t[3:])
     print(f"full size score {g} vs loglik differences {fd}: rel {np.abs(g - fd) / np.abs(fd)}, "
           f"term scale {np.abs(g - fd) / scale}")
     assert np.all(np.abs(g - fd) <= 1e-6 * scale)
-    well = np.abs(fd) >= 1e-3 * scale
-    assert well.any()
-    assert np.all(np.abs(g - fd)[well] <= 1e-3 * np.abs(fd)[well])
+    assert np.all(np.abs(g - fd) <= 1e-3 * np.abs(fd))
