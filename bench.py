@@ -72,6 +72,11 @@ def parse():
     p.add_argument("--workload", default=WORKLOAD, choices=sorted(WL.WORKLOADS))
     p.add_argument("--n", type=int, default=None, help="override the point count (testing)")
     p.add_argument("--tol-peel", type=float, default=None, help="override the workload's eps_peel")
+    p.add_argument("--mle", action="store_true",
+                   help="instead of the benchmark: the full-MLE workload's L-BFGS fit (Matern nu=1, mixture points, "
+                        "data drawn at theta (0.05, 1, 1e-2), started from (0.2, 0.5, 0.1)) at --n points "
+                        "(default 65,536) for --mle-iters iterations")
+    p.add_argument("--mle-iters", type=int, default=30)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-other-form", action="store_true",
@@ -462,8 +467,36 @@ def run_gpu(args):
     return 0
 
 
+def run_mle(args):
+    """The MLE loop of the full-MLE workload on one GPU: one JSON line with the
+    wall time per L-BFGS iteration and the error of the fitted theta."""
+    import torch
+    from paper_1603_08057_gb300 import build
+    build.build()
+    from paper_1603_08057_gb300 import binding as B
+    from paper_1603_08057_gb300 import mle
+    n = args.n or 65536
+    th_true, th0 = (0.05, 1.0, 1e-2), (0.2, 0.5, 0.1)
+    pts = torch.tensor(WL.mixture(n, 9), dtype=torch.float64, device="cuda")
+    F = B.Factorization(pts, B.MATERN1, th_true, B.SIGMA, 1e-12, 0.0, B.opts(precision=B.PREC_FP64))
+    z = F.solve(torch.tensor(WL.standard_normal(n, 10), dtype=torch.float64, device="cuda"), B.OP_SQRT)
+    del F
+    torch.cuda.synchronize()
+    th, info = mle.fit(pts, z, B.MATERN1, th0, max_iter=args.mle_iters)
+    iters = len({tuple(t[0]) for t in info["trace"]})
+    line = {"mode": "mle", "workload": f"matern nu=1 mixture n={n}", "n": n, "theta_true": list(th_true),
+            "theta0": list(th0), "theta_hat": th, "theta_rel_err": [abs(a - b) / b for a, b in zip(th, th_true)],
+            "lbfgs_max_iter": args.mle_iters, "evaluations": info["evals"], "seconds": info["seconds"],
+            "s_per_evaluation": info["seconds"] / max(1, info["evals"]), "distinct_thetas": iters,
+            "final_loglik": info["loglik"], "final_score": info["trace"][-1][2] if info["trace"] else None}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.mle:
+        return run_mle(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -113,7 +113,13 @@ typedef struct {
                        itself for Tr(F^-1).  RSF_TRACE_SQRT (1):
                        G = F^-1/2 F_k F^-T/2 and, for Tr(F^-1),
                        F^-1/2 F^-T/2, with F = F^1/2 (F^1/2)^T of Sec. 2.3.2:
-                       half the solve passes per test column */
+                       half the solve passes per test column.
+                       RSF_TRACE_HUTCH (2): no peeling -- Hutchinson's
+                       estimator (Sec. 3, Eq. (hutch)), the mean of
+                       u^T F^-1 u and (F^-1 u)^T F_k u over `probes`
+                       Rademacher vectors (Philox stream 1, key seed): a
+                       cheap trace with statistical error
+                       ~ sqrt(2 / probes) ||G||_F; tol_peel is ignored */
   int refine;       /* sweeps of iterative refinement of alpha = Sigma^-1 z
                        in gp_loglik (Algorithm 1, first line): alpha +=
                        F^-1 (z - Sigma alpha), the residual taken against
@@ -124,9 +130,10 @@ typedef struct {
                        z^T alpha does not carry the factorization's
                        eps_fact error.  -1 (default): 1 in the mixed forms
                        where the matvec runs in df64, else 0 */
+  int probes;       /* Hutchinson probes for RSF_TRACE_HUTCH (64) */
 } rsf_opts;
 
-enum { RSF_TRACE_SYM = 0, RSF_TRACE_SQRT = 1 };
+enum { RSF_TRACE_SYM = 0, RSF_TRACE_SQRT = 1, RSF_TRACE_HUTCH = 2 };
 
 enum { RSF_PREC_FP64 = 0, RSF_PREC_MIXED = 1, RSF_PREC_MIXED_DF64 = 2 };
 

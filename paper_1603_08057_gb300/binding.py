@@ -39,11 +39,11 @@ class RsfOpts(C.Structure):
     _fields_ = [("n_occ", C.c_int), ("n_prox", C.c_int), ("n_rings", C.c_int),
                 ("r_near", C.c_double), ("r_in", C.c_double), ("r_out", C.c_double),
                 ("oversample", C.c_int), ("q0", C.c_int), ("seed", C.c_uint64),
-                ("precision", C.c_int), ("trace_form", C.c_int), ("refine", C.c_int)]
+                ("precision", C.c_int), ("trace_form", C.c_int), ("refine", C.c_int), ("probes", C.c_int)]
 
 
 PREC_FP64, PREC_MIXED, PREC_MIXED_DF64 = 0, 1, 2
-TRACE_SYM, TRACE_SQRT = 0, 1
+TRACE_SYM, TRACE_SQRT, TRACE_HUTCH = 0, 1, 2
 
 
 class RsfInfo(C.Structure):

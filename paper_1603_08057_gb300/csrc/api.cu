@@ -201,8 +201,10 @@ static rsf_opts resolve_opts(const rsf_opts* o) {
   rsf_opts r;
   rsf_opts_default(&r);
   if (o) r = *o;
-  RSF_CHECK(r.trace_form == RSF_TRACE_SYM || r.trace_form == RSF_TRACE_SQRT, RSF_EINVAL,
-            "trace_form must be RSF_TRACE_SYM or RSF_TRACE_SQRT");
+  RSF_CHECK(r.trace_form == RSF_TRACE_SYM || r.trace_form == RSF_TRACE_SQRT || r.trace_form == RSF_TRACE_HUTCH,
+            RSF_EINVAL, "trace_form must be RSF_TRACE_SYM, RSF_TRACE_SQRT or RSF_TRACE_HUTCH");
+  RSF_CHECK(r.trace_form != RSF_TRACE_HUTCH || (r.probes >= 1 && r.probes <= 65536), RSF_EINVAL,
+            "probes must be in 1 .. 65536");
   RSF_CHECK(r.refine >= -1 && r.refine <= 8, RSF_EINVAL, "refine must be in -1 .. 8");
   return r;
 }
@@ -294,6 +296,7 @@ void rsf_opts_default(rsf_opts* o) {
   o->precision = RSF_PREC_MIXED;
   o->trace_form = RSF_TRACE_SYM;
   o->refine = -1;
+  o->probes = 64;
 }
 
 const char* rsf_last_error(void) { return g_err.c_str(); }

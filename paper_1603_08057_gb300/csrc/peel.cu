@@ -413,8 +413,63 @@ static inline uint64_t sketch_hash(uint64_t seed, uint64_t pos, int lev, int op,
 // Both share every test matrix and sketch, and F^-1 W -- one of the four
 // multi-RHS applications G_1 W needs -- is G_0 W, so peeling both costs the
 // applications of G_1 alone.
+// Rademacher probes for Hutchinson's estimator (Sec. 3, Eq. (hutch)): the
+// sign of Philox stream 1's normal draw at (tree position, probe), scaled by
+// 1/sqrt(m) so that sums of u^T G u over the m probes are the mean.
+__global__ void hutch_probe_kernel(int64_t n, int m, unsigned long long seed, double scale, double* __restrict__ U) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n * m) return;
+  const int64_t p = g / m;
+  const int j = (int)(g % m);
+  const double v = philox_normal((unsigned)p, (unsigned)j, 0u, 1u, seed);
+  U[g] = v >= 0.0 ? scale : -scale;
+}
+
+// Hutchinson's estimator of Tr(F^-1) and Tr(F^-1 F_k) with m probes u:
+// mean of u^T F^-1 u and of (F^-1 u)^T (F_k u) (F symmetric), per point set
+// (the probes restricted to a set's rows).  One solve and one apply with m
+// right-hand sides instead of the peeling's level sweep; its error is
+// statistical (standard error ~ sqrt(2/m) ||G||_F).
+static void hutch_traces(rsf_handle_s* F, rsf_handle_s* Fk, bool want0, const rsf_opts& o,
+                         double* const d_out[2], int64_t d_stride, double* h_sets) {
+  cudaStream_t s = F->stream;
+  TreeData& T = F->tree_raw->t;
+  const int64_t n = T.n;
+  const int m = std::max(1, o.probes);
+  DBuf U, V, W, res;
+  U.alloc(sizeof(double) * n * m, s);
+  V.alloc(sizeof(double) * n * m, s);
+  LAUNCH(hutch_probe_kernel, cdiv(n * m, 256), 256, 0, s, n, m, (unsigned long long)o.seed, 1.0 / std::sqrt((double)m),
+         U.as<double>());
+  solve_rows(F, RSF_OP_INV, U.as<double>(), V.as<double>(), m, 0);
+  if (Fk) {
+    W.alloc(sizeof(double) * n * m, s);
+    solve_rows(Fk, RSF_OP_APPLY, U.as<double>(), W.as<double>(), m, 0);
+  }
+  res.alloc(sizeof(double) * 2 * T.nsets, s);
+  res.zero();
+  for (int j = 0; j < T.nsets; j++) {
+    const int64_t r0 = T.set_off[j], cnt = T.set_off[j + 1] - r0;
+    if (want0 || !Fk) dot_into(U.as<double>() + r0 * m, V.as<double>() + r0 * m, cnt * m, res.as<double>() + j, s);
+    if (Fk) dot_into(V.as<double>() + r0 * m, W.as<double>() + r0 * m, cnt * m, res.as<double>() + T.nsets + j, s);
+  }
+  for (int i = 0; i < 2; i++)
+    if (d_out[i])
+      for (int j = 0; j < T.nsets; j++)
+        RSF_CUDA(cudaMemcpyAsync(d_out[i] + (int64_t)j * d_stride, res.as<double>() + i * T.nsets + j, sizeof(double),
+                                 cudaMemcpyDeviceToDevice, s));
+  if (h_sets) {
+    d2h(h_sets, res.as<double>(), 2 * T.nsets, s);
+    sync(s);
+  }
+}
+
 void peel_traces(rsf_handle_s* F, rsf_handle_s* Fk, bool want0, double tol, const rsf_opts& o,
                  double* const d_out[2], int64_t d_stride, double* h_sets) {
+  if (o.trace_form == RSF_TRACE_HUTCH) {
+    hutch_traces(F, Fk, want0, o, d_out, d_stride, h_sets);
+    return;
+  }
   cudaStream_t s = F->stream;
   TreeData& T = F->tree_raw->t;
   const int64_t n = T.n;

@@ -38,7 +38,7 @@ def test_library_builds_loads_and_exports_every_symbol():
     lib.rsf_opts_default(ctypes.byref(o))
     assert (o.n_occ, o.n_prox, o.n_rings, o.oversample, o.q0, o.seed) == (64, 256, 8, 10, 64, 0)
     assert (o.r_near, o.r_in, o.r_out) == (1.0, 1.0, 2.0)
-    assert (o.precision, o.trace_form, o.refine) == (binding.PREC_MIXED, binding.TRACE_SYM, -1)
+    assert (o.precision, o.trace_form, o.refine, o.probes) == (binding.PREC_MIXED, binding.TRACE_SYM, -1, 64)
     # sizes of the C structs (x86-64 and aarch64 alike): the field lists match rsf.h
     assert ctypes.sizeof(o) == 72 and ctypes.sizeof(binding.RsfInfo) == 80
     # the hook setter rejects a half-set pair without touching the GPU
