@@ -320,6 +320,67 @@ rsf_status gp_loglik_and_score_batched(int nsets, const int64_t* offsets,
                                        const rsf_opts* opts, void* stream,
                                        double* loglik, double* score, double* terms);
 
+/* Profile log-likelihood (Sec. 5.5, Eq. (prof)) for z ~ N(mu 1, s Sigma(theta))
+ * with the mean level mu and the variance level s profiled out, as printed
+ * with A = Sigma + 1 1^T:
+ *   lt   = -1/2 log|Sigma| - n/2 log(z^T A^-1 z) + n/2 (log n - 1 - log 2 pi)
+ *   gt_k = -1/2 Tr(Sigma^-1 Sigma_k) + n/2 gamma^T Sigma_k gamma / z^T gamma,
+ *          gamma = A^-1 z,
+ * (the printed constant "log n - 1 - 2 pi" read as log n - 1 - log 2 pi, the
+ * value at the maximizing s = z^T A^-1 z / n).  gamma comes from alpha =
+ * F^-1 z and beta = F^-1 1 (one two-column solve, refined as in gp_loglik)
+ * by Sherman-Morrison; the traces are peeled exactly as in gp_score.  The
+ * paper's model has unit variance in Sigma (theta = (l, 1, nug)); any s2 is
+ * accepted and gt_s2 is the derivative in it.  points, z device; loglik (1),
+ * score (3, or NULL for lt alone) and terms (10, or NULL) host: terms =
+ * (gamma^T Sigma_k gamma for k = l, s2, nug; Tr(Sigma^-1 Sigma_k) for the
+ * same k (zero when score is NULL); z^T gamma; log|F|; 1^T Sigma^-1 z;
+ * 1^T Sigma^-1 1).  Synchronises. */
+rsf_status gp_profile_loglik_and_score(const double* points, const double* z, int64_t n,
+                                       const rsf_kernel* kernel, const double* theta,
+                                       double tol_fact, double tol_peel,
+                                       const rsf_opts* opts, void* stream,
+                                       double* loglik, double* score, double* terms);
+
+/* gp_profile_loglik_and_score for nsets independent datasets in one forest
+ * (points, offsets and z as in gp_loglik_and_score_batched): per set i,
+ * loglik[i], score[3 i ..] and terms[10 i ..]; each set has its own mean and
+ * variance level. */
+rsf_status gp_profile_loglik_and_score_batched(int nsets, const int64_t* offsets,
+                                               const double* points, const double* z,
+                                               const rsf_kernel* kernel, const double* theta,
+                                               double tol_fact, double tol_peel,
+                                               const rsf_opts* opts, void* stream,
+                                               double* loglik, double* score, double* terms);
+
+/* How gp_conditional applies the cross covariance Sigma_12. */
+typedef enum {
+  RSF_COND_RSF = 0,    /* the remark's route: F of the joint matrix of
+                          [new points; points], Sigma_12 v = (F [0; v])(0:m) */
+  RSF_COND_DIRECT = 1  /* Sigma_12 v summed on the fly from the kernel (fp64,
+                          O(m n) work, exact Sigma_12; mean only) */
+} rsf_cond_method;
+
+/* Conditional distribution of z' at m new points given z at n points
+ * (Remark conditional, Sec. 4): z' | z ~ N(Sigma_12 Sigma_22^-1 z,
+ * Sigma_11 - Sigma_12 Sigma_22^-1 Sigma_12^T) under the same kernel, the
+ * nugget on equal indices only (Sigma_12 holds none).  Sigma_22^-1 z comes
+ * from F_22 (refined as in gp_loglik).  Samples follow the remark:
+ * y = F^1/2 w with F the joint factorization, sample = mean + y(0:m) -
+ * Sigma_12 F_22^-1 y(m:m+n), so their covariance is the conditional one up to
+ * the factorizations' tolerance.  points (n x 2), z (n), new_points (m x 2),
+ * mean (m) device; w (device, (m + n) x q column-major, leading dimension
+ * m + n, joint order: new points first) and samples (device, m x q,
+ * leading dimension m) only when q > 0, which needs RSF_COND_RSF.  The
+ * caller draws w (e.g. N(0, I)).  tol is the factorizations' ID tolerance.
+ * RSF_EINVAL for n or m < 1, q < 0, an unknown method, or samples asked of
+ * RSF_COND_DIRECT.  Synchronises. */
+rsf_status gp_conditional(const double* points, int64_t n, const double* z,
+                          const double* new_points, int64_t m,
+                          const rsf_kernel* kernel, const double* theta, double tol,
+                          const rsf_opts* opts, void* stream, int method,
+                          double* mean, const double* w, int q, double* samples);
+
 /* Factorization summary (host struct). */
 rsf_status rsf_get_info(rsf_handle h, rsf_info_t* info);
 

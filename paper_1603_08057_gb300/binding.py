@@ -28,7 +28,8 @@ EXPORTS = ["rsf_opts_default", "rsf_last_error", "rsf_tree_build", "rsf_tree_des
            "gp_loglik", "gp_score", "gp_loglik_and_score", "rsf_get_info",
            "rsf_launch_count", "rsf_profile_enable", "rsf_profile_read", "rsf_destroy",
            "rsf_solve_noalloc", "rsf_set_allocator", "rsf_build_batched", "rsf_logdet_sets",
-           "gp_loglik_and_score_batched", "rsf_selftest_wait_limit", "rsf_selftest_gemm"]
+           "gp_loglik_and_score_batched", "rsf_selftest_wait_limit", "rsf_selftest_gemm",
+           "gp_profile_loglik_and_score", "gp_profile_loglik_and_score_batched", "gp_conditional"]
 
 
 class RsfKernel(C.Structure):
@@ -44,6 +45,7 @@ class RsfOpts(C.Structure):
 
 PREC_FP64, PREC_MIXED, PREC_MIXED_DF64 = 0, 1, 2
 TRACE_SYM, TRACE_SQRT, TRACE_HUTCH = 0, 1, 2
+COND_RSF, COND_DIRECT = 0, 1
 
 
 class RsfInfo(C.Structure):
@@ -98,6 +100,10 @@ def lib():
         L.rsf_selftest_gemm.argtypes = [ip, ip, ip, ip, ip, ip, C.c_double, vp, ip, vp, ip, C.c_double, vp, ip, vp]
         L.gp_loglik_and_score_batched.argtypes = [ip, C.POINTER(C.c_int64), vp, vp, C.POINTER(RsfKernel), dp,
                                                   C.c_double, C.c_double, C.POINTER(RsfOpts), vp, dp, dp, dp]
+        L.gp_profile_loglik_and_score.argtypes = L.gp_loglik_and_score.argtypes
+        L.gp_profile_loglik_and_score_batched.argtypes = L.gp_loglik_and_score_batched.argtypes
+        L.gp_conditional.argtypes = [vp, i64, vp, vp, i64, C.POINTER(RsfKernel), dp, C.c_double,
+                                     C.POINTER(RsfOpts), vp, ip, vp, vp, ip, vp]
         L.rsf_profile_enable.argtypes = [ip]
         L.rsf_profile_enable.restype = None
         L.rsf_profile_read.argtypes = [ip, ip, C.POINTER(C.c_int64), dp, dp, dp]
@@ -386,6 +392,72 @@ def loglik_and_score_batched(points, offsets, z, family, theta, tol_fact=1e-9, t
     if not want_score:
         return np.array(list(ll)), None, None
     return np.array(list(ll)), np.array(list(g)).reshape(k, 3), np.array(list(t)).reshape(k, 6)
+
+
+def profile_loglik_and_score(points, z, family, theta, tol_fact=1e-9, tol_peel=1e-6, alpha=0.0,
+                             o: RsfOpts | None = None, want_score=True):
+    """gp_profile_loglik_and_score: the profile log-likelihood of Sec. 5.5
+    (mean and variance level profiled out).  Returns (lt, score, terms):
+    score (3,) or None, terms (10,) as documented in the header."""
+    pts = _dev(points)
+    n = pts.shape[0]
+    zz = _dev(z, (n,))
+    k = RsfKernel(family, alpha)
+    ll = C.c_double()
+    g = (C.c_double * 3)()
+    t = (C.c_double * 10)()
+    _check(lib().gp_profile_loglik_and_score(pts.data_ptr(), zz.data_ptr(), n, C.byref(k), _theta(theta),
+                                             tol_fact, tol_peel, C.byref(o) if o else None, _stream(),
+                                             C.byref(ll), g if want_score else None, t))
+    terms = torch.tensor(list(t), dtype=torch.float64)
+    return ll.value, (torch.tensor(list(g), dtype=torch.float64) if want_score else None), terms
+
+
+def profile_loglik_and_score_batched(points, offsets, z, family, theta, tol_fact=1e-9, tol_peel=1e-6, alpha=0.0,
+                                     o: RsfOpts | None = None, want_score=True):
+    """gp_profile_loglik_and_score_batched: per-set profile log-likelihoods.
+    Returns numpy arrays (nsets,), (nsets, 3) or None, (nsets, 10)."""
+    pts = _dev(points)
+    n = pts.shape[0]
+    zz = _dev(z, (n,))
+    off = _offsets(offsets, n)
+    k = len(off) - 1
+    kern = RsfKernel(family, alpha)
+    ll = (C.c_double * k)()
+    g = (C.c_double * (3 * k))()
+    t = (C.c_double * (10 * k))()
+    _check(lib().gp_profile_loglik_and_score_batched(k, off, pts.data_ptr(), zz.data_ptr(), C.byref(kern),
+                                                     _theta(theta), tol_fact, tol_peel, C.byref(o) if o else None,
+                                                     _stream(), ll, g if want_score else None, t))
+    g = np.array(list(g)).reshape(k, 3) if want_score else None
+    return np.array(list(ll)), g, np.array(list(t)).reshape(k, 10)
+
+
+def conditional(points, z, new_points, family, theta, tol=1e-9, alpha=0.0, o: RsfOpts | None = None,
+                method=COND_RSF, w=None):
+    """gp_conditional: mean (m,) of z' at new_points given z, and, when w
+    ((m + n) x q, new points first) is given, the samples (m, q)."""
+    pts = _dev(points)
+    n = pts.shape[0]
+    zz = _dev(z, (n,))
+    xs = _dev(new_points)
+    m = xs.shape[0]
+    kern = RsfKernel(family, alpha)
+    mean = torch.empty(m, dtype=torch.float64, device=pts.device)
+    q, wp, sp, S, wt = 0, None, None, None, None
+    if w is not None:
+        ww = _dev(w)
+        if ww.dim() == 1:
+            ww = ww.reshape(-1, 1)
+        if ww.shape[0] != m + n:
+            raise ValueError("w must have m + n rows")
+        q = ww.shape[1]
+        wt = ww.t().contiguous()  # column-major (m + n) x q
+        S = torch.empty(q, m, dtype=torch.float64, device=pts.device)
+        wp, sp = wt.data_ptr(), S.data_ptr()
+    _check(lib().gp_conditional(pts.data_ptr(), n, zz.data_ptr(), xs.data_ptr(), m, C.byref(kern), _theta(theta),
+                                tol, C.byref(o) if o else None, _stream(), method, mean.data_ptr(), wp, q, sp))
+    return mean, (S.t() if S is not None else None)
 
 
 class GPLogLikelihood(torch.autograd.Function):

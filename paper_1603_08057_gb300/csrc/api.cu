@@ -130,7 +130,7 @@ __global__ void from_tree_kernel(const double* __restrict__ X, int64_t n, int q,
 
 // Scalars slots
 enum { S_QUAD = 0, S_LOGDET, S_LOGLIK, S_AA, S_QL, S_QF, S_TNUG, S_TL, S_G0, S_G1, S_G2,
-       S_T0, S_T1, S_T2, S_T3, S_T4, S_T5, S_NSLOTS };
+       S_T0, S_T1, S_T2, S_T3, S_T4, S_T5, S_ONEA, S_ONEB, S_PQ, S_NSLOTS };
 
 // Every point set (one for a plain quadtree, several for batched datasets)
 // has its own block of S_NSLOTS scalars.
@@ -160,6 +160,54 @@ __global__ void score_kernel(double* sc, const int64_t* __restrict__ set_off, in
   c[S_G0] = 0.5 * ql - 0.5 * tl;
   c[S_G1] = 0.5 * qs - 0.5 * ts;
   c[S_G2] = 0.5 * qn - 0.5 * tn;
+}
+
+// Profile likelihood, Sec. 5.5 Eq. (prof), with A = Sigma + 1 1^T per set.
+// gamma = A^-1 z = alpha - beta (1^T alpha) / (1 + 1^T beta) (Sherman-Morrison)
+// from alpha = Sigma^-1 z and beta = Sigma^-1 1 of the row's set.
+__global__ void profile_gamma_kernel(const double* __restrict__ a, const double* __restrict__ b, int64_t n,
+                                     const int64_t* __restrict__ set_off, int nsets, const double* __restrict__ sc,
+                                     double* __restrict__ g) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int lo = 0, hi = nsets - 1;  // the set holding row i: last k with set_off[k] <= i
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (set_off[mid] <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  const double* c = sc + (int64_t)lo * S_NSLOTS;
+  g[i] = a[i] - b[i] * (c[S_ONEA] / (1.0 + c[S_ONEB]));
+}
+
+// Eq. (prof) per set with the constant read as n/2 (log n - 1 - log 2 pi):
+//   lt   = -log|F|/2 - n/2 log(z^T gamma) + n/2 (log n - 1 - log 2 pi)
+//   gt_k = -Tr(Sigma^-1 Sigma_k)/2 + n/2 (gamma^T Sigma_k gamma) / (z^T gamma)
+// with gamma's quadratic terms and the traces in S_T0 .. S_T5 (score_kernel).
+__global__ void profile_kernel(double* sc, const int64_t* __restrict__ set_off, int nsets, int with_score) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nsets) return;
+  double* c = sc + (int64_t)i * S_NSLOTS;
+  const double n = (double)(set_off[i + 1] - set_off[i]);
+  const double qt = c[S_PQ];
+  c[S_LOGLIK] = -0.5 * c[S_LOGDET] - 0.5 * n * log(qt) + 0.5 * n * (log(n) - 1.0 - log(2.0 * 3.141592653589793));
+  if (with_score)
+    for (int k = 0; k < 3; k++) c[S_G0 + k] = -0.5 * c[S_T3 + k] + 0.5 * n * c[S_T0 + k] / qt;
+}
+
+__global__ void fill_kernel(double* __restrict__ p, int64_t n, double v) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+// Conditional samples (Remark conditional): S(:, j) = mean + Y(0:m, j) - P(0:m, j)
+__global__ void cond_combine_kernel(const double* __restrict__ mean, const double* __restrict__ Y, int64_t ldy,
+                                    const double* __restrict__ P, int64_t ldp, int64_t m, int q,
+                                    double* __restrict__ S, int64_t lds) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m * q) return;
+  const int64_t i = t % m, j = t / m;
+  S[i + j * lds] = mean[i] + Y[i + j * ldy] - P[i + j * ldp];
 }
 
 // log|F| of every set = sum of its boxes' parts (fixed order; one block per
@@ -427,8 +475,9 @@ static void loglik_sets(rsf_handle_s* F, const double* z, double* alpha_out, DBu
 
 // Score scalars of every set into sc (filled by loglik_sets or zeroed):
 // a^T a, a^T F_l a, a^T F a per set, the peeled traces per set, the score.
+// alpha_in_tree: alpha is already in tree order (else the caller's order).
 static void score_sets(rsf_handle_s* F, const double* alpha, double tol_fact, double tol_peel, const rsf_opts& o,
-                       DBuf& sc) {
+                       DBuf& sc, bool alpha_in_tree = false) {
   cudaStream_t s = F->stream;
   const TreeData& T = F->tree_raw->t;
   const int64_t n = T.n;
@@ -440,7 +489,8 @@ static void score_sets(rsf_handle_s* F, const double* alpha, double tol_fact, do
   at.alloc(sizeof(double) * n, s);
   fl.alloc(sizeof(double) * n, s);
   ff.alloc(sizeof(double) * n, s);
-  LAUNCH(to_tree_kernel, cdiv(n, 256), 256, 0, s, alpha, n, 1, perm, n, at.as<double>());
+  if (alpha_in_tree) RSF_CUDA(cudaMemcpyAsync(at.as<double>(), alpha, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  else LAUNCH(to_tree_kernel, cdiv(n, 256), 256, 0, s, alpha, n, 1, perm, n, at.as<double>());
   solve_rows(Fl.get(), RSF_OP_APPLY, at.as<double>(), fl.as<double>(), 1);
   solve_rows(F, RSF_OP_APPLY, at.as<double>(), ff.as<double>(), 1);
   for (int i = 0; i < T.nsets; i++) {
@@ -456,6 +506,67 @@ static void score_sets(rsf_handle_s* F, const double* alpha, double tol_fact, do
   LAUNCH(score_kernel, cdiv(T.nsets, 32), 32, 0, s, sc.as<double>(), T.set_off_d.as<int64_t>(), T.nsets,
          F->kp.s2, F->kp.nug);
   check_status(Fl.get());
+}
+
+// Profile-likelihood scalars of every set into sc (Sec. 5.5): alpha = F^-1 z
+// and beta = F^-1 1 in one two-column solve (refined like gp_loglik),
+// 1^T alpha, 1^T beta, gamma = (Sigma + 1 1^T)^-1 z (tree order, into gt),
+// z^T gamma and log|F|; profile_kernel then forms the profile log-likelihood.
+static void profile_sets(rsf_handle_s* F, const double* z, DBuf& gt, DBuf& sc) {
+  cudaStream_t s = F->stream;
+  const TreeData& T = F->tree_raw->t;
+  const int64_t n = T.n;
+  const int* perm = T.perm.as<int>();
+  DBuf X, Y;
+  X.alloc(sizeof(double) * 2 * n, s);
+  Y.alloc(sizeof(double) * 2 * n, s);
+  gt.alloc(sizeof(double) * n, s);
+  sc.alloc(sizeof(double) * S_NSLOTS * T.nsets, s);
+  sc.zero();
+  double* x = X.as<double>();
+  double* y = Y.as<double>();
+  LAUNCH(to_tree_kernel, cdiv(n, 256), 256, 0, s, z, n, 1, perm, n, x);
+  LAUNCH(fill_kernel, cdiv(n, 256), 256, 0, s, x + n, n, 1.0);
+  solve_rows(F, RSF_OP_INV, x, y, 2);
+  const int sweeps = refine_sweeps(F);
+  if (sweeps > 0) {
+    DBuf R, D;
+    R.alloc(sizeof(double) * 2 * n, s);
+    D.alloc(sizeof(double) * 2 * n, s);
+    for (int k = 0; k < sweeps; k++) {
+      for (int c = 0; c < 2; c++) kernel_residual(F, x + c * n, y + c * n, R.as<double>() + c * n);
+      solve_rows(F, RSF_OP_INV, R.as<double>(), D.as<double>(), 2);
+      add_into(y, D.as<double>(), 2 * n, s);
+    }
+  }
+  for (int i = 0; i < T.nsets; i++) {
+    const int64_t r0 = T.set_off[i], cnt = T.set_off[i + 1] - r0;
+    double* c = sc.as<double>() + (int64_t)i * S_NSLOTS;
+    dot_into(x + n + r0, y + r0, cnt, c + S_ONEA, s);
+    dot_into(x + n + r0, y + n + r0, cnt, c + S_ONEB, s);
+    dot_into(x + r0, y + r0, cnt, c + S_QUAD, s);
+  }
+  LAUNCH(profile_gamma_kernel, cdiv(n, 256), 256, 0, s, y, y + n, n, T.set_off_d.as<int64_t>(), T.nsets,
+         sc.as<double>(), gt.as<double>());
+  for (int i = 0; i < T.nsets; i++) {
+    const int64_t r0 = T.set_off[i], cnt = T.set_off[i + 1] - r0;
+    dot_into(x + r0, gt.as<double>() + r0, cnt, sc.as<double>() + (int64_t)i * S_NSLOTS + S_PQ, s);
+  }
+  LAUNCH(sum_logdet_kernel, T.nsets, 256, 0, s, F->logdet_parts.as<double>(), T.box_set_d.as<int>(),
+         (int)F->nboxes_total, sc.as<double>() + S_LOGDET, (int64_t)S_NSLOTS);
+}
+
+// In-place operator on caller-order columns B (n x nrhs, leading dimension ldb).
+static void solve_caller(rsf_handle_s* h, int op, double* B, int64_t ldb, int nrhs) {
+  cudaStream_t s = h->stream;
+  const int64_t n = h->tree_raw->t.n;
+  const int* perm = h->tree_raw->t.perm.as<int>();
+  DBuf X, Y;
+  X.alloc(sizeof(double) * n * nrhs, s);
+  Y.alloc(sizeof(double) * n * nrhs, s);
+  LAUNCH(to_tree_kernel, cdiv(n * nrhs, 256), 256, 0, s, B, ldb, nrhs, perm, n, X.as<double>());
+  solve_rows(h, op, X.as<double>(), Y.as<double>(), nrhs);
+  LAUNCH(from_tree_kernel, cdiv(n * nrhs, 256), 256, 0, s, Y.as<double>(), n, nrhs, perm, B, ldb);
 }
 
 rsf_status rsf_logdet(rsf_handle h, double* out) {
@@ -485,14 +596,7 @@ rsf_status rsf_solve(rsf_handle h, double* B, int64_t ldb, int nrhs, int op) {
   RSF_CHECK(nrhs >= 1 && ldb >= n, RSF_EINVAL, "need nrhs >= 1 and ldb >= n");
   RSF_CHECK(op >= RSF_OP_INV && op <= RSF_OP_INV_SQRT_T, RSF_EINVAL, "unknown op");
   RSF_CHECK(h->spd || op == RSF_OP_APPLY, RSF_EINVAL, "only APPLY is defined for a derivative factorization");
-  cudaStream_t s = h->stream;
-  const int* perm = h->tree_raw->t.perm.as<int>();
-  DBuf X, Y;
-  X.alloc(sizeof(double) * n * nrhs, s);
-  Y.alloc(sizeof(double) * n * nrhs, s);
-  LAUNCH(to_tree_kernel, cdiv(n * nrhs, 256), 256, 0, s, B, ldb, nrhs, perm, n, X.as<double>());
-  solve_rows(h, op, X.as<double>(), Y.as<double>(), nrhs);
-  LAUNCH(from_tree_kernel, cdiv(n * nrhs, 256), 256, 0, s, Y.as<double>(), n, nrhs, perm, B, ldb);
+  solve_caller(h, op, B, ldb, nrhs);
   API_END
 }
 
@@ -637,6 +741,126 @@ rsf_status gp_loglik_and_score_batched(int nsets, const int64_t* offsets, const 
   check_kernel(kernel, theta);
   auto t = build_forest(points, set_offsets(nsets, offsets), o, (cudaStream_t)stream);
   loglik_and_score_forest(t, z, kernel, theta, tol_fact, tol_peel, o, loglik, score, terms);
+  API_END
+}
+
+// Profile likelihood (Sec. 5.5) on a forest: per-set lt and (score != NULL)
+// its gradient; terms per set (10): gamma^T Sigma_k gamma (3), the traces (3),
+// z^T gamma, log|F|, 1^T Sigma^-1 z, 1^T Sigma^-1 1.
+static void profile_forest(std::shared_ptr<rsf_tree_s> t, const double* z, const rsf_kernel* kernel,
+                           const double* theta, double tol_fact, double tol_peel, const rsf_opts& o, double* loglik,
+                           double* score, double* terms) {
+  const TreeData& T = t->t;
+  cudaStream_t s = T.stream;
+  std::unique_ptr<rsf_handle_s> F(make_handle(t, kernel, theta, RSF_SIGMA, tol_fact, o));
+  DBuf gt, sc;
+  profile_sets(F.get(), z, gt, sc);
+  if (score) score_sets(F.get(), gt.as<double>(), tol_fact, tol_peel, o, sc, true);
+  LAUNCH(profile_kernel, cdiv(T.nsets, 32), 32, 0, s, sc.as<double>(), T.set_off_d.as<int64_t>(), T.nsets,
+         score ? 1 : 0);
+  std::vector<double> h((size_t)S_NSLOTS * T.nsets);
+  d2h(h.data(), sc.as<double>(), h.size(), s);
+  check_status(F.get());
+  for (int i = 0; i < T.nsets; i++) {
+    const double* c = h.data() + (size_t)i * S_NSLOTS;
+    loglik[i] = c[S_LOGLIK];
+    if (score)
+      for (int j = 0; j < 3; j++) score[3 * i + j] = c[S_G0 + j];
+    if (terms) {
+      double* tr = terms + 10 * i;
+      for (int j = 0; j < 6; j++) tr[j] = score ? c[S_T0 + j] : 0.0;
+      tr[6] = c[S_PQ];
+      tr[7] = c[S_LOGDET];
+      tr[8] = c[S_ONEA];
+      tr[9] = c[S_ONEB];
+    }
+  }
+}
+
+rsf_status gp_profile_loglik_and_score(const double* points, const double* z, int64_t n, const rsf_kernel* kernel,
+                                       const double* theta, double tol_fact, double tol_peel, const rsf_opts* opts,
+                                       void* stream, double* loglik, double* score, double* terms) {
+  API_BEGIN
+  RSF_CHECK(points && z && loglik, RSF_EINVAL, "points, z and loglik must not be NULL");
+  RSF_CHECK(tol_peel > 0.0 && tol_peel < 1.0, RSF_EINVAL, "tol_peel must be in (0, 1)");
+  rsf_opts o = resolve_opts(opts);
+  check_kernel(kernel, theta);
+  auto t = build_tree(points, n, o, (cudaStream_t)stream);
+  profile_forest(t, z, kernel, theta, tol_fact, tol_peel, o, loglik, score, terms);
+  API_END
+}
+
+rsf_status gp_profile_loglik_and_score_batched(int nsets, const int64_t* offsets, const double* points,
+                                               const double* z, const rsf_kernel* kernel, const double* theta,
+                                               double tol_fact, double tol_peel, const rsf_opts* opts, void* stream,
+                                               double* loglik, double* score, double* terms) {
+  API_BEGIN
+  RSF_CHECK(points && z && loglik, RSF_EINVAL, "points, z and loglik must not be NULL");
+  RSF_CHECK(tol_peel > 0.0 && tol_peel < 1.0, RSF_EINVAL, "tol_peel must be in (0, 1)");
+  rsf_opts o = resolve_opts(opts);
+  check_kernel(kernel, theta);
+  auto t = build_forest(points, set_offsets(nsets, offsets), o, (cudaStream_t)stream);
+  profile_forest(t, z, kernel, theta, tol_fact, tol_peel, o, loglik, score, terms);
+  API_END
+}
+
+rsf_status gp_conditional(const double* points, int64_t n, const double* z, const double* new_points, int64_t m,
+                          const rsf_kernel* kernel, const double* theta, double tol, const rsf_opts* opts,
+                          void* stream, int method, double* mean, const double* w, int q, double* samples) {
+  API_BEGIN
+  RSF_CHECK(points && z && new_points && mean, RSF_EINVAL, "points, z, new_points and mean must not be NULL");
+  RSF_CHECK(n >= 1 && m >= 1, RSF_EINVAL, "need n >= 1 observed and m >= 1 new points");
+  RSF_CHECK(method == RSF_COND_RSF || method == RSF_COND_DIRECT, RSF_EINVAL, "unknown method");
+  RSF_CHECK(q >= 0, RSF_EINVAL, "q must be >= 0");
+  RSF_CHECK(q == 0 || (w && samples && method == RSF_COND_RSF), RSF_EINVAL,
+            "samples need w, samples and method RSF_COND_RSF");
+  rsf_opts o = resolve_opts(opts);
+  check_kernel(kernel, theta);
+  cudaStream_t s = (cudaStream_t)stream;
+  auto t2 = build_tree(points, n, o, s);
+  std::unique_ptr<rsf_handle_s> F2(make_handle(t2, kernel, theta, RSF_SIGMA, tol, o));
+  // alpha = Sigma_22^-1 z (caller order), refined like gp_loglik
+  DBuf a, sc;
+  a.alloc(sizeof(double) * n, s);
+  loglik_sets(F2.get(), z, a.as<double>(), sc);
+  if (method == RSF_COND_DIRECT) {
+    cross_matvec(F2->kp, points, a.as<double>(), n, new_points, m, mean, s);
+  } else {
+    // the joint matrix of [new points; points]; Sigma_12 v = (F [0; v])(0:m)
+    const int64_t nj = n + m;
+    DBuf J;
+    J.alloc(sizeof(double) * 2 * nj, s);
+    RSF_CUDA(cudaMemcpyAsync(J.as<double>(), new_points, sizeof(double) * 2 * m, cudaMemcpyDeviceToDevice, s));
+    RSF_CUDA(cudaMemcpyAsync(J.as<double>() + 2 * m, points, sizeof(double) * 2 * n, cudaMemcpyDeviceToDevice, s));
+    auto tj = build_tree(J.as<double>(), nj, o, s);
+    std::unique_ptr<rsf_handle_s> FJ(make_handle(tj, kernel, theta, RSF_SIGMA, tol, o));
+    DBuf V;
+    V.alloc(sizeof(double) * nj, s);
+    RSF_CUDA(cudaMemsetAsync(V.as<double>(), 0, sizeof(double) * m, s));
+    RSF_CUDA(cudaMemcpyAsync(V.as<double>() + m, a.as<double>(), sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    solve_caller(FJ.get(), RSF_OP_APPLY, V.as<double>(), nj, 1);
+    RSF_CUDA(cudaMemcpyAsync(mean, V.as<double>(), sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+    if (q > 0) {
+      // y = F^1/2 w; samples = mean + y_1 - Sigma_12 Sigma_22^-1 y_2
+      DBuf Y, Z, P;
+      Y.alloc(sizeof(double) * nj * q, s);
+      Z.alloc(sizeof(double) * n * q, s);
+      P.alloc(sizeof(double) * nj * q, s);
+      RSF_CUDA(cudaMemcpyAsync(Y.as<double>(), w, sizeof(double) * nj * q, cudaMemcpyDeviceToDevice, s));
+      solve_caller(FJ.get(), RSF_OP_SQRT, Y.as<double>(), nj, q);
+      RSF_CUDA(cudaMemcpy2DAsync(Z.as<double>(), sizeof(double) * n, Y.as<double>() + m, sizeof(double) * nj,
+                                 sizeof(double) * n, q, cudaMemcpyDeviceToDevice, s));
+      solve_caller(F2.get(), RSF_OP_INV, Z.as<double>(), n, q);
+      RSF_CUDA(cudaMemsetAsync(P.as<double>(), 0, sizeof(double) * nj * q, s));
+      RSF_CUDA(cudaMemcpy2DAsync(P.as<double>() + m, sizeof(double) * nj, Z.as<double>(), sizeof(double) * n,
+                                 sizeof(double) * n, q, cudaMemcpyDeviceToDevice, s));
+      solve_caller(FJ.get(), RSF_OP_APPLY, P.as<double>(), nj, q);
+      LAUNCH(cond_combine_kernel, cdiv(m * q, 256), 256, 0, s, mean, Y.as<double>(), nj, P.as<double>(), nj, m, q,
+             samples, m);
+    }
+    check_status(FJ.get());
+  }
+  check_status(F2.get());
   API_END
 }
 

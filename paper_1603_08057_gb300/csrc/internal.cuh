@@ -262,6 +262,11 @@ void peel_traces(rsf_handle_s* F, rsf_handle_s* Fk, bool want0, double tol, cons
 // Matern families unless force_fp64), and y += x.
 void kernel_residual(rsf_handle_s* F, const double* zt, const double* x, double* rt, int force_fp64 = 0);
 void add_into(double* y, const double* x, int64_t n, cudaStream_t s);
+// y = K(xs, x) v (kernel kp, no nugget): m new points xs against n points x,
+// both device row-major m x 2 / n x 2, v and y device (the conditional
+// mean's matvec).
+void cross_matvec(KernelParams kp, const double* x, const double* v, int64_t n, const double* xs, int64_t m,
+                  double* y, cudaStream_t s);
 // Whether kernel_residual runs in df64 for these kernel parameters.
 bool residual_uses_df64(const KernelParams& kp);
 // Iterative-refinement sweeps of Sigma^-1 z that gp_loglik runs for handle F.

@@ -216,6 +216,40 @@ __global__ void __launch_bounds__(RT) residual_kernel(const double* __restrict__
   if (i < n) r[i] = z[i] - (DF ? df_to_double(df_of_acc(acc)) : acc64);
 }
 
+// y_i = sum_j K(xs_i, x_j) v_j for m new points xs against n points x (both
+// row-major, 2 doubles per point): the cross-covariance matvec of the
+// conditional mean (no nugget: different observations), fp64 with a
+// Kahan-compensated sum.
+__global__ void __launch_bounds__(RT) cross_matvec_kernel(const double* __restrict__ xt, const double* __restrict__ v,
+                                                          int64_t n, const double* __restrict__ xs, int64_t m,
+                                                          KernelParams kp, double* __restrict__ y) {
+  __shared__ double sx[RT], sy[RT], sv[RT];
+  const int t = threadIdx.x;
+  const int64_t i = (int64_t)blockIdx.x * RT + t;
+  const double xi = i < m ? xs[2 * i] : 0.0, yi = i < m ? xs[2 * i + 1] : 0.0;
+  double acc = 0.0, comp = 0.0;
+  for (int64_t jt = 0; jt < n; jt += RT) {
+    const int64_t j = jt + t;
+    if (j < n) {
+      sx[t] = xt[2 * j];
+      sy[t] = xt[2 * j + 1];
+      sv[t] = v[j];
+    }
+    __syncthreads();
+    const int jn = n - jt < RT ? (int)(n - jt) : RT;
+    if (i < m)
+      for (int jj = 0; jj < jn; jj++) {
+        const double k = kernel_offdiag(kp, sqrt(dist2(xi, yi, sx[jj], sy[jj])));
+        const double yk = fma(k, sv[jj], -comp);
+        const double tsum = acc + yk;
+        comp = (tsum - acc) - yk;
+        acc = tsum;
+      }
+    __syncthreads();
+  }
+  if (i < m) y[i] = acc;
+}
+
 __global__ void axpy_kernel(double* __restrict__ y, const double* __restrict__ x, int64_t n) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g < n) y[g] += x[g];
@@ -282,6 +316,12 @@ void kernel_residual(rsf_handle_s* F, const double* zt, const double* xt_vec, do
   else
     LAUNCH(residual_kernel<false>, cdiv(n, RT), RT, 0, s, T.xt.as<double>(), zt, xt_vec, T.set_off_d.as<int64_t>(),
            T.nsets, n, kp, md, rt);
+}
+
+void cross_matvec(KernelParams kp, const double* x, const double* v, int64_t n, const double* xs, int64_t m,
+                  double* y, cudaStream_t s) {
+  kp.which = 0;
+  if (m > 0) LAUNCH(cross_matvec_kernel, cdiv(m, RT), RT, 0, s, x, v, n, xs, m, kp, y);
 }
 
 void add_into(double* y, const double* x, int64_t n, cudaStream_t s) {
