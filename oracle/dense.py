@@ -34,8 +34,14 @@ def loglik_dense(x, z, family, theta, alpha=0.0):
     return ell, quad, logdet
 
 
+def params(theta):
+    """Matrix selectors of the score's components: (l, s2, nug), then l2
+    for the anisotropic theta of Sec. 5.1."""
+    return (K.D_L, K.D_S2, K.D_NUG) + ((K.D_L2,) if len(theta) == 4 else ())
+
+
 def score_dense(x, z, family, theta, alpha=0.0):
-    """Exact score g (3,) plus its terms.
+    """Exact score g (3,), or (4,) for an anisotropic theta, plus its terms.
 
     Returns dict with g, quadk (z^T S^-1 S_k S^-1 z), trace (Tr(S^-1 S_k)),
     ell, quad, logdet.
@@ -48,10 +54,11 @@ def score_dense(x, z, family, theta, alpha=0.0):
     quad = float(z @ a)
     logdet = 2.0 * float(np.sum(np.log(np.diag(c[0]))))
     ell = -0.5 * quad - 0.5 * logdet - 0.5 * n * np.log(2.0 * np.pi)
-    g = np.zeros(3)
-    quadk = np.zeros(3)
-    trace = np.zeros(3)
-    for k, which in enumerate((K.D_L, K.D_S2, K.D_NUG)):
+    p = len(params(theta))
+    g = np.zeros(p)
+    quadk = np.zeros(p)
+    trace = np.zeros(p)
+    for k, which in enumerate(params(theta)):
         Sk = cov_matrix(x, family, theta, which, alpha)
         quadk[k] = float(a @ (Sk @ a))
         trace[k] = float(np.sum(Sinv * Sk))  # Tr(S^-1 S_k), both symmetric

@@ -18,6 +18,12 @@ variance on the index diagonal, delta_ij).  Families:
 ``which`` selects the matrix: 0 -> Sigma, 1 -> dSigma/dl, 2 -> dSigma/ds2,
 3 -> dSigma/dnug.  The nugget lives on equal *indices* (delta_ij), so two
 coincident points remain distinct observations.
+
+Anisotropic form (Sec. 5.1): with theta = (l1, s2, nug, l2) (four entries)
+the family's unit-length correlation is taken at the scaled distance
+||x - y||_theta = sqrt((x1 - y1)^2 / l1^2 + (x2 - y2)^2 / l2^2), so
+Eqs. (specmatern) and (specrq) are Matern 3/2 and RQ alpha = 1/2 with
+s2 = 1; which = 1 is then d/dl1 and which = 4 (D_L2) is d/dl2.
 """
 from __future__ import annotations
 
@@ -25,7 +31,7 @@ import numpy as np
 from scipy import special
 
 MATERN12, MATERN32, MATERN52, MATERN1, RQ = 0, 1, 2, 3, 4
-SIGMA, D_L, D_S2, D_NUG = 0, 1, 2, 3
+SIGMA, D_L, D_S2, D_NUG, D_L2 = 0, 1, 2, 3, 4
 
 SQRT3 = np.sqrt(3.0)
 SQRT5 = np.sqrt(5.0)
@@ -89,7 +95,8 @@ def dcorrelation_dl(r, family, l, alpha=0.0):
 
 
 def kernel_offdiag(r, family, theta, which, alpha=0.0):
-    """Entry of Sigma (which=0) or dSigma/dtheta_k for two distinct indices."""
+    """Entry of Sigma (which=0) or dSigma/dtheta_k for two distinct indices
+    (isotropic theta = (l, s2, nug))."""
     l, s2, nug = theta
     if which == SIGMA:
         return s2 * correlation(r, family, l, alpha)
@@ -102,12 +109,39 @@ def kernel_offdiag(r, family, theta, which, alpha=0.0):
     raise ValueError(f"unknown matrix selector {which}")
 
 
+def aniso_offdiag(dx, dy, family, theta, which, alpha=0.0):
+    """Off-diagonal entries for the anisotropic theta = (l1, s2, nug, l2) of
+    Sec. 5.1 at coordinate differences dx, dy.  The correlation depends on
+    r = ||x - y||_theta only; its theta_k-derivative is k'(r) dr/dtheta_k with
+    dr/dl1 = -(dx/l1)^2 / (l1 r) and dr/dl2 = -(dy/l2)^2 / (l2 r), and k'(r)
+    follows from the unit-length l-derivative of k(r/l): d/dl k(r/l) at l = 1
+    is -r k'(r)."""
+    l1, s2, nug, l2 = theta
+    u = np.asarray(dx, dtype=np.float64) / l1
+    v = np.asarray(dy, dtype=np.float64) / l2
+    r = np.sqrt(u * u + v * v)
+    if which == SIGMA:
+        return s2 * correlation(r, family, 1.0, alpha)
+    if which == D_S2:
+        return correlation(r, family, 1.0, alpha)
+    if which == D_NUG:
+        return np.zeros_like(r)
+    if which in (D_L, D_L2):
+        w = u * u / l1 if which == D_L else v * v / l2
+        out = np.zeros_like(r)
+        nz = r > 0
+        kprime = -dcorrelation_dl(r[nz], family, 1.0, alpha) / r[nz]
+        out[nz] = s2 * kprime * (-w[nz] / r[nz])
+        return out
+    raise ValueError(f"unknown matrix selector {which}")
+
+
 def diag_value(family, theta, which, alpha=0.0):
     """Diagonal entry (r = 0, same index) of Sigma or dSigma/dtheta_k."""
-    l, s2, nug = theta
+    l, s2, nug = theta[:3]
     if which == SIGMA:
         return s2 + nug
-    if which == D_L:
+    if which in (D_L, D_L2):
         return 0.0
     if which == D_S2:
         return 1.0
@@ -130,8 +164,12 @@ def kernel_block(xa, xb, family, theta, which, alpha=0.0, ia=None, ib=None):
     equal indices get the diagonal value (nugget on delta_ij).  Without
     indices all entries are treated as off-diagonal (distinct observations).
     """
-    r = pairwise_dist(xa, xb)
-    out = kernel_offdiag(r, family, theta, which, alpha)
+    if len(theta) == 4:
+        dx = xa[:, 0:1] - xb[None, :, 0]
+        dy = xa[:, 1:2] - xb[None, :, 1]
+        out = aniso_offdiag(dx, dy, family, theta, which, alpha)
+    else:
+        out = kernel_offdiag(pairwise_dist(xa, xb), family, theta, which, alpha)
     if ia is not None and ib is not None:
         same = np.asarray(ia)[:, None] == np.asarray(ib)[None, :]
         if np.any(same):

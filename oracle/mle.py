@@ -2,7 +2,9 @@
 
 ORACLE -- test infrastructure only (tests, smoke check, benchmark CPU leg).
 
-theta = (l, s2, nug) for K = s2 k(r/l) + nug delta_ij.  Readings:
+theta = (l, s2, nug) for K = s2 k(r/l) + nug delta_ij, or the anisotropic
+(l1, s2, nug, l2) of Sec. 5.1 (a fourth score component, d/dl2, from its own
+factorization and peeled trace).  Readings:
 
 * the constant is -(n/2) log 2 pi as in Eq. (loglikelihood) (the algorithm box
   prints -1/2 log 2 pi, read as a typo);
@@ -38,7 +40,7 @@ def loglik_and_score(x, z, family, theta, tol_fact=1e-9, tol_peel=1e-6,
     out = dict(ell=ell, quad=quad, logdet=logdet, tree=tree, F=F)
     if not want_score:
         return out
-    l, s2, nug = theta
+    l, s2, nug = theta[:3]
     Fl = Factorization(x, family, theta, K.D_L, tol_fact, alpha, o, tree)
     t_nug, info_nug = peel_trace(F.solve, tree, tol_peel, seed=seed)
     t_l, info_l = peel_trace(lambda X: 0.5 * (F.solve(Fl.apply(X)) + Fl.apply(F.solve(X))),
@@ -47,8 +49,18 @@ def loglik_and_score(x, z, family, theta, tol_fact=1e-9, tol_peel=1e-6,
     q_l = float(a @ Fl.apply(a))
     q_s2 = (quad - nug * aa) / s2
     t_s2 = (n - nug * t_nug) / s2
-    quadk = np.array([q_l, q_s2, aa])
-    trace = np.array([t_l, t_s2, t_nug])
+    quadk = [q_l, q_s2, aa]
+    trace = [t_l, t_s2, t_nug]
+    if len(theta) == 4:
+        # anisotropic theta (Sec. 5.1): the second length scale's factorization and trace
+        Fl2 = Factorization(x, family, theta, K.D_L2, tol_fact, alpha, o, tree)
+        t_l2, _ = peel_trace(lambda X: 0.5 * (F.solve(Fl2.apply(X)) + Fl2.apply(F.solve(X))),
+                             tree, tol_peel, seed=seed)
+        quadk.append(float(a @ Fl2.apply(a)))
+        trace.append(t_l2)
+        out.update(Fl2=Fl2)
+    quadk = np.array(quadk)
+    trace = np.array(trace)
     g = 0.5 * quadk - 0.5 * trace
     out.update(g=g, quadk=quadk, trace=trace, Fl=Fl, info_l=info_l, info_nug=info_nug)
     return out

@@ -34,7 +34,7 @@ import numpy as np
 from scipy import linalg
 
 from . import kernels as K
-from .dense import cov_matrix
+from .dense import cov_matrix, params
 
 
 def profile_loglik_dense(x, z, family, theta, alpha=0.0):
@@ -50,7 +50,8 @@ def profile_loglik_dense(x, z, family, theta, alpha=0.0):
 
 
 def profile_score_dense(x, z, family, theta, alpha=0.0):
-    """Gradient of Eq. (prof), as printed, for theta = (l, s2, nug).
+    """Gradient of Eq. (prof), as printed, for theta = (l, s2, nug) (or the
+    anisotropic (l1, s2, nug, l2)).
 
     Returns dict with g (3,), quadk (gamma^T Sigma_k gamma, gamma = A^-1 z),
     trace (Tr(Sigma^-1 Sigma_k)), lt, qt, logdet."""
@@ -60,10 +61,11 @@ def profile_score_dense(x, z, family, theta, alpha=0.0):
     lt, qt, logdet = profile_loglik_dense(x, z, family, theta, alpha)
     A = S + np.ones((n, n))
     gamma = linalg.cho_solve(linalg.cho_factor(A, lower=True), z)
-    g = np.zeros(3)
-    quadk = np.zeros(3)
-    trace = np.zeros(3)
-    for k, which in enumerate((K.D_L, K.D_S2, K.D_NUG)):
+    p = len(params(theta))
+    g = np.zeros(p)
+    quadk = np.zeros(p)
+    trace = np.zeros(p)
+    for k, which in enumerate(params(theta)):
         Sk = cov_matrix(x, family, theta, which, alpha)
         quadk[k] = float(gamma @ (Sk @ gamma))
         trace[k] = float(np.sum(Sinv * Sk))
