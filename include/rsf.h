@@ -68,8 +68,9 @@ typedef enum {
 } rsf_family;
 
 /* Matrix selector: Sigma or one of its theta-derivatives (Sec. 1, below
- * Eq. (gradient)). */
-typedef enum { RSF_SIGMA = 0, RSF_D_L = 1, RSF_D_S2 = 2, RSF_D_NUG = 3 } rsf_which;
+ * Eq. (gradient)).  RSF_D_L2 (the second length scale) exists for
+ * anisotropic kernels only; RSF_D_L is then the derivative in l1. */
+typedef enum { RSF_SIGMA = 0, RSF_D_L = 1, RSF_D_S2 = 2, RSF_D_NUG = 3, RSF_D_L2 = 4 } rsf_which;
 
 /* Operations of rsf_solve (Sec. 2.3.2): F^-1, F, F^1/2, (F^1/2)^T, F^-1/2,
  * (F^-1/2)^T.  Only RSF_OP_APPLY is defined for derivative factorizations. */
@@ -78,9 +79,18 @@ typedef enum {
   RSF_OP_INV_SQRT = 4, RSF_OP_INV_SQRT_T = 5
 } rsf_op;
 
+/* Kernel description.  theta (host) is (l, s2, nug): length scale, variance,
+ * nugget.  With anisotropic != 0 it is (l1, s2, nug, l2) and the family is
+ * evaluated at unit length scale on the scaled distance of Sec. 5.1,
+ * ||x - y||_theta^2 = (x1 - y1)^2 / l1^2 + (x2 - y2)^2 / l2^2 (Eqs. (specrq)
+ * and (specmatern) are RSF_RQ with alpha = 1/2 and RSF_MATERN32, s2 = 1).
+ * Scores then have p = 4 components (l1, s2, nug, l2), otherwise p = 3
+ * (l, s2, nug).  The quadtree and proxy annulus stay in the points' own
+ * coordinates. */
 typedef struct {
-  int family;    /* rsf_family */
-  double alpha;  /* RQ shape parameter (ignored otherwise) */
+  int family;       /* rsf_family */
+  double alpha;     /* RQ shape parameter (ignored otherwise) */
+  int anisotropic;  /* 0: isotropic theta (3 entries); 1: (l1, s2, nug, l2) */
 } rsf_kernel;
 
 /* Tuning knobs.  n_occ and n_prox default to the paper's 64 and 256 (Sec. 5);
@@ -293,14 +303,18 @@ rsf_status gp_loglik(rsf_handle F, const double* z, double* alpha_out,
 /* Score (Algorithm 1, loop over theta) given F ~ Sigma and alpha = F^-1 z:
  * builds F_l ~ dSigma/dl on F's tree, peels Tr(F^-1) and
  * Tr((F^-1 F_l + F_l F^-1)/2), and uses Sigma = s2 Sigma_s2 + nug I for the
- * variance component.  score (host, 3) = (g_l, g_s2, g_nug); terms (host, 6,
- * or NULL) = (quad_l, quad_s2, quad_nug, trace_l, trace_s2, trace_nug). */
+ * variance component.  score (host, p) = (g_l, g_s2, g_nug); terms (host, 2p,
+ * or NULL) = (quad_l, quad_s2, quad_nug, trace_l, trace_s2, trace_nug).  For
+ * an anisotropic kernel (p = 4) F_l2 ~ dSigma/dl2 is built and peeled as
+ * well: score = (g_l1, g_s2, g_nug, g_l2), terms = (quads of l1, s2, nug, l2;
+ * traces of l1, s2, nug, l2). */
 rsf_status gp_score(rsf_handle F, const double* alpha, double tol_fact,
                     double tol_peel, const rsf_opts* opts, double* score,
                     double* terms);
 
 /* Algorithm 1 end to end: tree, F, loglik and (when score != NULL) the
- * score.  points, z device; loglik, score (3), terms (6, or NULL) host. */
+ * score.  points, z device; loglik, score (p), terms (2p, or NULL) host,
+ * p as for gp_score. */
 rsf_status gp_loglik_and_score(const double* points, const double* z, int64_t n,
                                const rsf_kernel* kernel, const double* theta,
                                double tol_fact, double tol_peel,
@@ -310,7 +324,7 @@ rsf_status gp_loglik_and_score(const double* points, const double* z, int64_t n,
 /* Algorithm 1 for nsets independent datasets in one forest (see
  * rsf_build_batched for points and offsets; z device, offsets[nsets]
  * entries in the same order as the points).  Per set i: loglik[i] and, when
- * score != NULL, score[3 i .. 3 i + 2] and terms[6 i .. 6 i + 5] (host), each
+ * score != NULL, score[p i .. p i + p - 1] and terms[2p i .. 2p i + 2p - 1] (host), each
  * exactly what gp_loglik_and_score returns for that set alone up to the
  * peeling's test matrices (shared by all sets). */
 rsf_status gp_loglik_and_score_batched(int nsets, const int64_t* offsets,
@@ -332,10 +346,10 @@ rsf_status gp_loglik_and_score_batched(int nsets, const int64_t* offsets,
  * by Sherman-Morrison; the traces are peeled exactly as in gp_score.  The
  * paper's model has unit variance in Sigma (theta = (l, 1, nug)); any s2 is
  * accepted and gt_s2 is the derivative in it.  points, z device; loglik (1),
- * score (3, or NULL for lt alone) and terms (10, or NULL) host: terms =
- * (gamma^T Sigma_k gamma for k = l, s2, nug; Tr(Sigma^-1 Sigma_k) for the
- * same k (zero when score is NULL); z^T gamma; log|F|; 1^T Sigma^-1 z;
- * 1^T Sigma^-1 1).  Synchronises. */
+ * score (p, as for gp_score; or NULL for lt alone) and terms (2p + 4, or
+ * NULL) host: terms = (gamma^T Sigma_k gamma for the p parameters;
+ * Tr(Sigma^-1 Sigma_k) for the same (zero when score is NULL); z^T gamma;
+ * log|F|; 1^T Sigma^-1 z; 1^T Sigma^-1 1).  Synchronises. */
 rsf_status gp_profile_loglik_and_score(const double* points, const double* z, int64_t n,
                                        const rsf_kernel* kernel, const double* theta,
                                        double tol_fact, double tol_peel,
@@ -344,7 +358,7 @@ rsf_status gp_profile_loglik_and_score(const double* points, const double* z, in
 
 /* gp_profile_loglik_and_score for nsets independent datasets in one forest
  * (points, offsets and z as in gp_loglik_and_score_batched): per set i,
- * loglik[i], score[3 i ..] and terms[10 i ..]; each set has its own mean and
+ * loglik[i], score[p i ..] and terms[(2p + 4) i ..]; each set has its own mean and
  * variance level. */
 rsf_status gp_profile_loglik_and_score_batched(int nsets, const int64_t* offsets,
                                                const double* points, const double* z,

@@ -18,7 +18,7 @@ LIBPATH = os.path.join(HERE, "librsf.so")
 
 # rsf_family, rsf_which, rsf_op (include/rsf.h)
 MATERN12, MATERN32, MATERN52, MATERN1, RQ = 0, 1, 2, 3, 4
-SIGMA, D_L, D_S2, D_NUG = 0, 1, 2, 3
+SIGMA, D_L, D_S2, D_NUG, D_L2 = 0, 1, 2, 3, 4
 OP_INV, OP_APPLY, OP_SQRT, OP_SQRT_T, OP_INV_SQRT, OP_INV_SQRT_T = range(6)
 STATUS = {0: "RSF_OK", 1: "RSF_EINVAL", 2: "RSF_ENOMEM", 3: "RSF_ENOTPD",
           4: "RSF_ENUMERIC", 5: "RSF_ETIMEOUT", 6: "RSF_ECUDA"}
@@ -33,7 +33,7 @@ EXPORTS = ["rsf_opts_default", "rsf_last_error", "rsf_tree_build", "rsf_tree_des
 
 
 class RsfKernel(C.Structure):
-    _fields_ = [("family", C.c_int), ("alpha", C.c_double)]
+    _fields_ = [("family", C.c_int), ("alpha", C.c_double), ("anisotropic", C.c_int)]
 
 
 class RsfOpts(C.Structure):
@@ -146,8 +146,16 @@ def _stream():
 
 
 def _theta(theta):
+    """theta (l, s2, nug) or, anisotropic (Sec. 5.1), (l1, s2, nug, l2)."""
     th = [float(v) for v in (theta.tolist() if isinstance(theta, torch.Tensor) else theta)]
-    return (C.c_double * 3)(*th)
+    if len(th) not in (3, 4):
+        raise ValueError("theta must have 3 entries (l, s2, nug) or 4 (l1, s2, nug, l2)")
+    return (C.c_double * len(th))(*th)
+
+
+def _kernel(family, alpha, theta) -> RsfKernel:
+    """The kernel descriptor; a 4-entry theta selects the anisotropic form."""
+    return RsfKernel(family, alpha, 1 if len(theta) == 4 else 0)
 
 
 def launch_count(reset=False) -> int:
@@ -258,9 +266,10 @@ class Factorization:
                  o: RsfOpts | None = None, offsets=None):
         """offsets (sequence of nsets + 1 ints): points holds nsets independent
         datasets, set i in rows offsets[i]:offsets[i+1] (rsf_build_batched)."""
-        self.kernel = RsfKernel(family, alpha)
+        self.kernel = _kernel(family, alpha, theta)
         self.h = C.c_void_p()
         th = _theta(theta)
+        self.p = len(th)
         if offsets is not None:
             pts = _dev(points_or_tree)
             self.n = pts.shape[0]
@@ -331,10 +340,11 @@ class Factorization:
         return ll.value, q.value, a
 
     def score(self, alpha: torch.Tensor, tol_fact=1e-9, tol_peel=1e-6, o: RsfOpts | None = None):
-        """gp_score: returns (score (3,), terms (6,)) as float64 CPU tensors."""
+        """gp_score: returns (score (p,), terms (2p,)) as float64 CPU tensors,
+        p = 3, or 4 for an anisotropic theta."""
         a = _dev(alpha, (self.n,))
-        g = (C.c_double * 3)()
-        t = (C.c_double * 6)()
+        g = (C.c_double * self.p)()
+        t = (C.c_double * (2 * self.p))()
         _check(lib().gp_score(self.h, a.data_ptr(), tol_fact, tol_peel, C.byref(o) if o else None, g, t))
         return torch.tensor(list(g), dtype=torch.float64), torch.tensor(list(t), dtype=torch.float64)
 
@@ -353,10 +363,11 @@ def loglik_and_score(points, z, family, theta, tol_fact=1e-9, tol_peel=1e-6, alp
     pts = _dev(points)
     n = pts.shape[0]
     zz = _dev(z, (n,))
-    k = RsfKernel(family, alpha)
+    k = _kernel(family, alpha, theta)
+    p = len(theta)
     ll = C.c_double()
-    g = (C.c_double * 3)()
-    t = (C.c_double * 6)()
+    g = (C.c_double * p)()
+    t = (C.c_double * (2 * p))()
     _check(lib().gp_loglik_and_score(pts.data_ptr(), zz.data_ptr(), n, C.byref(k), _theta(theta),
                                      tol_fact, tol_peel, C.byref(o) if o else None, _stream(),
                                      C.byref(ll), g if want_score else None, t if want_score else None))
@@ -382,30 +393,32 @@ def loglik_and_score_batched(points, offsets, z, family, theta, tol_fact=1e-9, t
     zz = _dev(z, (n,))
     off = _offsets(offsets, n)
     k = len(off) - 1
-    kern = RsfKernel(family, alpha)
+    kern = _kernel(family, alpha, theta)
+    p = len(theta)
     ll = (C.c_double * k)()
-    g = (C.c_double * (3 * k))()
-    t = (C.c_double * (6 * k))()
+    g = (C.c_double * (p * k))()
+    t = (C.c_double * (2 * p * k))()
     _check(lib().gp_loglik_and_score_batched(k, off, pts.data_ptr(), zz.data_ptr(), C.byref(kern), _theta(theta),
                                              tol_fact, tol_peel, C.byref(o) if o else None, _stream(), ll,
                                              g if want_score else None, t if want_score else None))
     if not want_score:
         return np.array(list(ll)), None, None
-    return np.array(list(ll)), np.array(list(g)).reshape(k, 3), np.array(list(t)).reshape(k, 6)
+    return np.array(list(ll)), np.array(list(g)).reshape(k, p), np.array(list(t)).reshape(k, 2 * p)
 
 
 def profile_loglik_and_score(points, z, family, theta, tol_fact=1e-9, tol_peel=1e-6, alpha=0.0,
                              o: RsfOpts | None = None, want_score=True):
     """gp_profile_loglik_and_score: the profile log-likelihood of Sec. 5.5
     (mean and variance level profiled out).  Returns (lt, score, terms):
-    score (3,) or None, terms (10,) as documented in the header."""
+    score (p,) or None, terms (2p + 4,) as documented in the header."""
     pts = _dev(points)
     n = pts.shape[0]
     zz = _dev(z, (n,))
-    k = RsfKernel(family, alpha)
+    k = _kernel(family, alpha, theta)
+    p = len(theta)
     ll = C.c_double()
-    g = (C.c_double * 3)()
-    t = (C.c_double * 10)()
+    g = (C.c_double * p)()
+    t = (C.c_double * (2 * p + 4))()
     _check(lib().gp_profile_loglik_and_score(pts.data_ptr(), zz.data_ptr(), n, C.byref(k), _theta(theta),
                                              tol_fact, tol_peel, C.byref(o) if o else None, _stream(),
                                              C.byref(ll), g if want_score else None, t))
@@ -416,21 +429,22 @@ def profile_loglik_and_score(points, z, family, theta, tol_fact=1e-9, tol_peel=1
 def profile_loglik_and_score_batched(points, offsets, z, family, theta, tol_fact=1e-9, tol_peel=1e-6, alpha=0.0,
                                      o: RsfOpts | None = None, want_score=True):
     """gp_profile_loglik_and_score_batched: per-set profile log-likelihoods.
-    Returns numpy arrays (nsets,), (nsets, 3) or None, (nsets, 10)."""
+    Returns numpy arrays (nsets,), (nsets, p) or None, (nsets, 2p + 4)."""
     pts = _dev(points)
     n = pts.shape[0]
     zz = _dev(z, (n,))
     off = _offsets(offsets, n)
     k = len(off) - 1
-    kern = RsfKernel(family, alpha)
+    kern = _kernel(family, alpha, theta)
+    p = len(theta)
     ll = (C.c_double * k)()
-    g = (C.c_double * (3 * k))()
-    t = (C.c_double * (10 * k))()
+    g = (C.c_double * (p * k))()
+    t = (C.c_double * ((2 * p + 4) * k))()
     _check(lib().gp_profile_loglik_and_score_batched(k, off, pts.data_ptr(), zz.data_ptr(), C.byref(kern),
                                                      _theta(theta), tol_fact, tol_peel, C.byref(o) if o else None,
                                                      _stream(), ll, g if want_score else None, t))
-    g = np.array(list(g)).reshape(k, 3) if want_score else None
-    return np.array(list(ll)), g, np.array(list(t)).reshape(k, 10)
+    g = np.array(list(g)).reshape(k, p) if want_score else None
+    return np.array(list(ll)), g, np.array(list(t)).reshape(k, 2 * p + 4)
 
 
 def conditional(points, z, new_points, family, theta, tol=1e-9, alpha=0.0, o: RsfOpts | None = None,
@@ -442,7 +456,7 @@ def conditional(points, z, new_points, family, theta, tol=1e-9, alpha=0.0, o: Rs
     zz = _dev(z, (n,))
     xs = _dev(new_points)
     m = xs.shape[0]
-    kern = RsfKernel(family, alpha)
+    kern = _kernel(family, alpha, theta)
     mean = torch.empty(m, dtype=torch.float64, device=pts.device)
     q, wp, sp, S, wt = 0, None, None, None, None
     if w is not None:

@@ -129,8 +129,11 @@ __global__ void from_tree_kernel(const double* __restrict__ X, int64_t n, int q,
 }
 
 // Scalars slots
-enum { S_QUAD = 0, S_LOGDET, S_LOGLIK, S_AA, S_QL, S_QF, S_TNUG, S_TL, S_G0, S_G1, S_G2,
-       S_T0, S_T1, S_T2, S_T3, S_T4, S_T5, S_ONEA, S_ONEB, S_PQ, S_NSLOTS };
+// S_Q0.. the quadratic terms and S_R0.. the traces of the p score
+// components (l, s2, nug and, anisotropic, l2), S_G0.. the score.
+enum { S_QUAD = 0, S_LOGDET, S_LOGLIK, S_AA, S_QL, S_QF, S_QL2, S_TNUG, S_TL, S_TL2,
+       S_G0, S_G1, S_G2, S_G3, S_Q0, S_Q1, S_Q2, S_Q3, S_R0, S_R1, S_R2, S_R3,
+       S_ONEA, S_ONEB, S_PQ, S_NSLOTS };
 
 // Every point set (one for a plain quadtree, several for batched datasets)
 // has its own block of S_NSLOTS scalars.
@@ -148,18 +151,20 @@ __global__ void loglik_kernel(double* sc, const int64_t* __restrict__ set_off, i
 //   g_l   = (a^T F_l a - Tr_l)/2
 //   g_s2  = ((a^T F a - nug a^T a) - (n - nug Tr(F^-1)))/(2 s2)
 //   g_nug = (a^T a - Tr(F^-1))/2
-__global__ void score_kernel(double* sc, const int64_t* __restrict__ set_off, int nsets, double s2, double nug) {
+//   g_l2  = (a^T F_l2 a - Tr_l2)/2       (anisotropic, p = 4)
+__global__ void score_kernel(double* sc, const int64_t* __restrict__ set_off, int nsets, double s2, double nug,
+                             int p) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nsets) return;
   double* c = sc + (int64_t)i * S_NSLOTS;
   double n = (double)(set_off[i + 1] - set_off[i]);
-  double ql = c[S_QL], qs = (c[S_QF] - nug * c[S_AA]) / s2, qn = c[S_AA];
-  double tl = c[S_TL], ts = (n - nug * c[S_TNUG]) / s2, tn = c[S_TNUG];
-  c[S_T0] = ql; c[S_T1] = qs; c[S_T2] = qn;
-  c[S_T3] = tl; c[S_T4] = ts; c[S_T5] = tn;
-  c[S_G0] = 0.5 * ql - 0.5 * tl;
-  c[S_G1] = 0.5 * qs - 0.5 * ts;
-  c[S_G2] = 0.5 * qn - 0.5 * tn;
+  const double q[4] = {c[S_QL], (c[S_QF] - nug * c[S_AA]) / s2, c[S_AA], c[S_QL2]};
+  const double t[4] = {c[S_TL], (n - nug * c[S_TNUG]) / s2, c[S_TNUG], c[S_TL2]};
+  for (int k = 0; k < p; k++) {
+    c[S_Q0 + k] = q[k];
+    c[S_R0 + k] = t[k];
+    c[S_G0 + k] = 0.5 * q[k] - 0.5 * t[k];
+  }
 }
 
 // Profile likelihood, Sec. 5.5 Eq. (prof), with A = Sigma + 1 1^T per set.
@@ -183,8 +188,8 @@ __global__ void profile_gamma_kernel(const double* __restrict__ a, const double*
 // Eq. (prof) per set with the constant read as n/2 (log n - 1 - log 2 pi):
 //   lt   = -log|F|/2 - n/2 log(z^T gamma) + n/2 (log n - 1 - log 2 pi)
 //   gt_k = -Tr(Sigma^-1 Sigma_k)/2 + n/2 (gamma^T Sigma_k gamma) / (z^T gamma)
-// with gamma's quadratic terms and the traces in S_T0 .. S_T5 (score_kernel).
-__global__ void profile_kernel(double* sc, const int64_t* __restrict__ set_off, int nsets, int with_score) {
+// with gamma's quadratic terms and the traces in S_Q0.., S_R0.. (score_kernel).
+__global__ void profile_kernel(double* sc, const int64_t* __restrict__ set_off, int nsets, int with_score, int p) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nsets) return;
   double* c = sc + (int64_t)i * S_NSLOTS;
@@ -192,7 +197,7 @@ __global__ void profile_kernel(double* sc, const int64_t* __restrict__ set_off, 
   const double qt = c[S_PQ];
   c[S_LOGLIK] = -0.5 * c[S_LOGDET] - 0.5 * n * log(qt) + 0.5 * n * (log(n) - 1.0 - log(2.0 * 3.141592653589793));
   if (with_score)
-    for (int k = 0; k < 3; k++) c[S_G0 + k] = -0.5 * c[S_T3 + k] + 0.5 * n * c[S_T0 + k] / qt;
+    for (int k = 0; k < p; k++) c[S_G0 + k] = -0.5 * c[S_R0 + k] + 0.5 * n * c[S_Q0 + k] / qt;
 }
 
 __global__ void fill_kernel(double* __restrict__ p, int64_t n, double v) {
@@ -264,12 +269,18 @@ static void check_kernel(const rsf_kernel* k, const double* theta) {
             RSF_EINVAL, "unsupported kernel family");
   RSF_CHECK(k->family != RSF_RQ || k->alpha > 0.0, RSF_EINVAL, "RQ needs alpha > 0");
   RSF_CHECK(theta[0] > 0.0 && theta[1] > 0.0 && theta[2] >= 0.0, RSF_EINVAL, "theta must satisfy l > 0, s2 > 0, nug >= 0");
+  RSF_CHECK(k->anisotropic == 0 || k->anisotropic == 1, RSF_EINVAL, "anisotropic must be 0 or 1");
+  RSF_CHECK(!k->anisotropic || theta[3] > 0.0, RSF_EINVAL, "anisotropic theta needs l2 > 0");
 }
+
+// Number of score components: (l, s2, nug), and l2 for anisotropic kernels.
+static int nparams(const rsf_kernel* k) { return k->anisotropic ? 4 : 3; }
 
 static rsf_handle_s* make_handle(std::shared_ptr<rsf_tree_s> tree, const rsf_kernel* kernel, const double* theta,
                                  int which, double tol, const rsf_opts& o) {
   check_kernel(kernel, theta);
-  RSF_CHECK(which >= RSF_SIGMA && which <= RSF_D_S2, RSF_EINVAL, "which must be SIGMA, D_L or D_S2");
+  RSF_CHECK((which >= RSF_SIGMA && which <= RSF_D_S2) || (which == RSF_D_L2 && kernel->anisotropic), RSF_EINVAL,
+            "which must be SIGMA, D_L, D_S2 or (anisotropic kernels) D_L2");
   RSF_CHECK(tol > 0.0 && tol < 1.0, RSF_EINVAL, "tol must be in (0, 1)");
   auto h = std::make_unique<rsf_handle_s>();
   h->tree = tree;
@@ -291,6 +302,8 @@ static rsf_handle_s* make_handle(std::shared_ptr<rsf_tree_s> tree, const rsf_ker
   h->kp.s2 = theta[1];
   h->kp.nug = theta[2];
   h->kp.which = which;
+  h->kp.aniso = kernel->anisotropic;
+  h->kp.l2 = kernel->anisotropic ? theta[3] : theta[0];
   int tk = prof_begin(h->stream);
   factorize(h.get());
   prof_end(tk, h->stream, PROF_FACTOR, h->flops, 0);
@@ -482,30 +495,39 @@ static void score_sets(rsf_handle_s* F, const double* alpha, double tol_fact, do
   const TreeData& T = F->tree_raw->t;
   const int64_t n = T.n;
   const int* perm = T.perm.as<int>();
-  rsf_kernel k{F->kp.family, F->kp.alpha};
-  double theta[3] = {F->kp.l, F->kp.s2, F->kp.nug};
-  std::unique_ptr<rsf_handle_s> Fl(make_handle(F->tree, &k, theta, RSF_D_L, tol_fact, o));
+  rsf_kernel k{F->kp.family, F->kp.alpha, F->kp.aniso};
+  const double theta[4] = {F->kp.l, F->kp.s2, F->kp.nug, F->kp.l2};
   DBuf at, fl, ff;
   at.alloc(sizeof(double) * n, s);
   fl.alloc(sizeof(double) * n, s);
   ff.alloc(sizeof(double) * n, s);
   if (alpha_in_tree) RSF_CUDA(cudaMemcpyAsync(at.as<double>(), alpha, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   else LAUNCH(to_tree_kernel, cdiv(n, 256), 256, 0, s, alpha, n, 1, perm, n, at.as<double>());
-  solve_rows(Fl.get(), RSF_OP_APPLY, at.as<double>(), fl.as<double>(), 1);
   solve_rows(F, RSF_OP_APPLY, at.as<double>(), ff.as<double>(), 1);
   for (int i = 0; i < T.nsets; i++) {
     const int64_t r0 = T.set_off[i], cnt = T.set_off[i + 1] - r0;
     double* c = sc.as<double>() + (int64_t)i * S_NSLOTS;
     dot_into(at.as<double>() + r0, at.as<double>() + r0, cnt, c + S_AA, s);
-    dot_into(at.as<double>() + r0, fl.as<double>() + r0, cnt, c + S_QL, s);
     dot_into(at.as<double>() + r0, ff.as<double>() + r0, cnt, c + S_QF, s);
   }
-  // Tr(F^-1) and Tr(G_l) of every set, peeled together on shared test matrices
-  double* const dtr[2] = {sc.as<double>() + S_TNUG, sc.as<double>() + S_TL};
-  peel_traces(F, Fl.get(), true, tol_peel, o, dtr, (int64_t)S_NSLOTS, nullptr);
+  // one length-scale derivative at a time (l, then l2 when anisotropic), its
+  // factorization freed before the next is built; Tr(F^-1) is peeled with
+  // the first on shared test matrices
+  const int nl = F->kp.aniso ? 2 : 1;
+  for (int d = 0; d < nl; d++) {
+    std::unique_ptr<rsf_handle_s> Fl(make_handle(F->tree, &k, theta, d == 0 ? RSF_D_L : RSF_D_L2, tol_fact, o));
+    solve_rows(Fl.get(), RSF_OP_APPLY, at.as<double>(), fl.as<double>(), 1);
+    for (int i = 0; i < T.nsets; i++) {
+      const int64_t r0 = T.set_off[i], cnt = T.set_off[i + 1] - r0;
+      double* c = sc.as<double>() + (int64_t)i * S_NSLOTS;
+      dot_into(at.as<double>() + r0, fl.as<double>() + r0, cnt, c + (d == 0 ? S_QL : S_QL2), s);
+    }
+    double* const dtr[2] = {d == 0 ? sc.as<double>() + S_TNUG : nullptr, sc.as<double>() + (d == 0 ? S_TL : S_TL2)};
+    peel_traces(F, Fl.get(), d == 0, tol_peel, o, dtr, (int64_t)S_NSLOTS, nullptr);
+    check_status(Fl.get());
+  }
   LAUNCH(score_kernel, cdiv(T.nsets, 32), 32, 0, s, sc.as<double>(), T.set_off_d.as<int64_t>(), T.nsets,
-         F->kp.s2, F->kp.nug);
-  check_status(Fl.get());
+         F->kp.s2, F->kp.nug, F->kp.aniso ? 4 : 3);
 }
 
 // Profile-likelihood scalars of every set into sc (Sec. 5.5): alpha = F^-1 z
@@ -665,14 +687,18 @@ rsf_status gp_score(rsf_handle F, const double* alpha, double tol_fact, double t
   std::vector<double> h((size_t)S_NSLOTS * nsets);
   d2h(h.data(), sc.as<double>(), h.size(), F->stream);
   check_status(F);
-  for (int i = 0; i < 3; i++) {
+  const int p = F->kp.aniso ? 4 : 3;
+  for (int i = 0; i < p; i++) {
     score[i] = 0.0;
     for (int j = 0; j < nsets; j++) score[i] += h[(size_t)j * S_NSLOTS + S_G0 + i];
   }
   if (terms)
-    for (int i = 0; i < 6; i++) {
-      terms[i] = 0.0;
-      for (int j = 0; j < nsets; j++) terms[i] += h[(size_t)j * S_NSLOTS + S_T0 + i];
+    for (int i = 0; i < p; i++) {
+      terms[i] = terms[p + i] = 0.0;
+      for (int j = 0; j < nsets; j++) {
+        terms[i] += h[(size_t)j * S_NSLOTS + S_Q0 + i];
+        terms[p + i] += h[(size_t)j * S_NSLOTS + S_R0 + i];
+      }
     }
   API_END
 }
@@ -691,13 +717,17 @@ static void loglik_and_score_forest(std::shared_ptr<rsf_tree_s> t, const double*
   std::vector<double> h((size_t)S_NSLOTS * T.nsets);
   d2h(h.data(), sc.as<double>(), h.size(), s);
   check_status(F.get());
+  const int p = nparams(kernel);
   for (int i = 0; i < T.nsets; i++) {
     const double* c = h.data() + (size_t)i * S_NSLOTS;
     loglik[i] = c[S_LOGLIK];
     if (score)
-      for (int j = 0; j < 3; j++) score[3 * i + j] = c[S_G0 + j];
+      for (int j = 0; j < p; j++) score[p * i + j] = c[S_G0 + j];
     if (score && terms)
-      for (int j = 0; j < 6; j++) terms[6 * i + j] = c[S_T0 + j];
+      for (int j = 0; j < p; j++) {
+        terms[2 * p * i + j] = c[S_Q0 + j];
+        terms[2 * p * i + p + j] = c[S_R0 + j];
+      }
   }
 }
 
@@ -745,8 +775,8 @@ rsf_status gp_loglik_and_score_batched(int nsets, const int64_t* offsets, const 
 }
 
 // Profile likelihood (Sec. 5.5) on a forest: per-set lt and (score != NULL)
-// its gradient; terms per set (10): gamma^T Sigma_k gamma (3), the traces (3),
-// z^T gamma, log|F|, 1^T Sigma^-1 z, 1^T Sigma^-1 1.
+// its gradient; terms per set (2p + 4): gamma^T Sigma_k gamma (p), the traces
+// (p), z^T gamma, log|F|, 1^T Sigma^-1 z, 1^T Sigma^-1 1.
 static void profile_forest(std::shared_ptr<rsf_tree_s> t, const double* z, const rsf_kernel* kernel,
                            const double* theta, double tol_fact, double tol_peel, const rsf_opts& o, double* loglik,
                            double* score, double* terms) {
@@ -757,22 +787,26 @@ static void profile_forest(std::shared_ptr<rsf_tree_s> t, const double* z, const
   profile_sets(F.get(), z, gt, sc);
   if (score) score_sets(F.get(), gt.as<double>(), tol_fact, tol_peel, o, sc, true);
   LAUNCH(profile_kernel, cdiv(T.nsets, 32), 32, 0, s, sc.as<double>(), T.set_off_d.as<int64_t>(), T.nsets,
-         score ? 1 : 0);
+         score ? 1 : 0, nparams(kernel));
   std::vector<double> h((size_t)S_NSLOTS * T.nsets);
   d2h(h.data(), sc.as<double>(), h.size(), s);
   check_status(F.get());
+  const int p = nparams(kernel);
   for (int i = 0; i < T.nsets; i++) {
     const double* c = h.data() + (size_t)i * S_NSLOTS;
     loglik[i] = c[S_LOGLIK];
     if (score)
-      for (int j = 0; j < 3; j++) score[3 * i + j] = c[S_G0 + j];
+      for (int j = 0; j < p; j++) score[p * i + j] = c[S_G0 + j];
     if (terms) {
-      double* tr = terms + 10 * i;
-      for (int j = 0; j < 6; j++) tr[j] = score ? c[S_T0 + j] : 0.0;
-      tr[6] = c[S_PQ];
-      tr[7] = c[S_LOGDET];
-      tr[8] = c[S_ONEA];
-      tr[9] = c[S_ONEB];
+      double* tr = terms + (2 * p + 4) * i;
+      for (int j = 0; j < p; j++) {
+        tr[j] = score ? c[S_Q0 + j] : 0.0;
+        tr[p + j] = score ? c[S_R0 + j] : 0.0;
+      }
+      tr[2 * p] = c[S_PQ];
+      tr[2 * p + 1] = c[S_LOGDET];
+      tr[2 * p + 2] = c[S_ONEA];
+      tr[2 * p + 3] = c[S_ONEB];
     }
   }
 }

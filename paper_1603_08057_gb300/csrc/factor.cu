@@ -127,7 +127,7 @@ __global__ void assemble_id_kernel(const IdBox* __restrict__ boxes, const int* _
       px = B.cx + B.w * proxy[2 * t];
       py = B.cy + B.w * proxy[2 * t + 1];
     }
-    a[i] = kernel_offdiag(kp, sqrt(dist2(px, py, xj, yj)));
+    a[i] = kernel_pair(kp, px, py, xj, yj);
   }
 }
 
@@ -169,7 +169,7 @@ __global__ void assemble_aii_kernel(const AiiBox* __restrict__ boxes, const int*
     int di = I[B.row0 + il];
     double v;
     if (B.leaf) {
-      v = (di == dj) ? kernel_diag(kp) : kernel_offdiag(kp, sqrt(dist2(xt[2 * (int64_t)di], xt[2 * (int64_t)di + 1], xj, yj)));
+      v = (di == dj) ? kernel_diag(kp) : kernel_pair(kp, xt[2 * (int64_t)di], xt[2 * (int64_t)di + 1], xj, yj);
     } else {
       int ci = 0;
       while (ci + 1 < B.nch && B.choff[ci + 1] <= il) ci++;
@@ -177,7 +177,7 @@ __global__ void assemble_aii_kernel(const AiiBox* __restrict__ boxes, const int*
         int li = il - B.choff[ci];
         v = prev[B.chaii[ci] + li + (int64_t)lj * B.chld[ci]];
       } else {
-        v = kernel_offdiag(kp, sqrt(dist2(xt[2 * (int64_t)di], xt[2 * (int64_t)di + 1], xj, yj)));
+        v = kernel_pair(kp, xt[2 * (int64_t)di], xt[2 * (int64_t)di + 1], xj, yj);
       }
     }
     o[p] = v;

@@ -21,7 +21,9 @@ struct KernelParams {
   int family;
   double alpha;
   double l, s2, nug;
-  int which;  // 0 Sigma, 1 d/dl, 2 d/ds2, 3 d/dnug
+  int which;  // 0 Sigma, 1 d/dl (d/dl1), 2 d/ds2, 3 d/dnug, 4 d/dl2
+  int aniso;  // scaled distance of Sec. 5.1 with length scales l (x) and l2 (y)
+  double l2;
 };
 
 // Modified Bessel functions K0(x), K1(x) for x > 0 in fp64, for the Matern
@@ -129,13 +131,35 @@ __device__ __forceinline__ double kernel_offdiag(const KernelParams& kp, double 
 
 __device__ __forceinline__ double kernel_diag(const KernelParams& kp) {
   if (kp.which == 0) return kp.s2 + kp.nug;
-  if (kp.which == 1) return 0.0;
+  if (kp.which == 1 || kp.which == 4) return 0.0;
   return 1.0;
 }
 
 __device__ __forceinline__ double dist2(double ax, double ay, double bx, double by) {
   double dx = __dsub_rn(ax, bx), dy = __dsub_rn(ay, by);
   return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+}
+
+// Off-diagonal entry between points a and b.  Isotropic: the family at the
+// Euclidean distance.  Anisotropic (Sec. 5.1): the family at unit length
+// scale on r = ||a - b||_theta, u = (ax - bx)/l, v = (ay - by)/l2,
+// r^2 = u^2 + v^2; as the correlation depends on r only, its l- and
+// l2-derivatives are k'(r) dr/dl with dr/dl = -u^2/(l r) (and v^2/(l2 r) for
+// l2), and k'(r) = -(unit-length l-derivative)/r, so the entry is the
+// unit-length l-derivative times u^2/(l r^2) (resp. v^2/(l2 r^2)).
+__device__ __forceinline__ double kernel_pair(const KernelParams& kp, double ax, double ay, double bx, double by) {
+  if (!kp.aniso) return kernel_offdiag(kp, sqrt(dist2(ax, ay, bx, by)));
+  if (kp.which == 3) return 0.0;
+  const double u = __dsub_rn(ax, bx) / kp.l, v = __dsub_rn(ay, by) / kp.l2;
+  const double r2 = __dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v));
+  const double r = sqrt(r2);
+  KernelParams k1 = kp;
+  k1.l = 1.0;
+  if (kp.which == 0 || kp.which == 2) return kernel_offdiag(k1, r);
+  if (r2 == 0.0) return 0.0;
+  k1.which = 1;
+  const double w = kp.which == 1 ? u * u / kp.l : v * v / kp.l2;
+  return kernel_offdiag(k1, r) * (w / r2);
 }
 
 // Host view of the quadtree (Sec. 2.1, Remark (tree)); device copies of the

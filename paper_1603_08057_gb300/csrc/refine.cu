@@ -94,6 +94,8 @@ __device__ __forceinline__ df64 d_exp_neg(df64 a) {
 // a = sqrt5 r/l (Sec. 1 Eq. (matern) at half-integer nu).
 struct MaternDF {
   int family;
+  int aniso;    // scale dx by ax and dy by ay (Sec. 5.1; unit length scale in c)
+  df64 ax, ay;
   df64 c;       // a = c r (Matern); 1 / (2 alpha l^2) (rational quadratic)
   df64 s2;
   df64 third;   // 1/3
@@ -196,14 +198,18 @@ __global__ void __launch_bounds__(RT) residual_kernel(const double* __restrict__
           if (jg == i) {
             v = df_from_double(kernel_diag(kp));
           } else {
-            const df64 dx = d_sub(xid, dx_s[jj]);
-            const df64 dy = d_sub(yid, dy_s[jj]);
+            df64 dx = d_sub(xid, dx_s[jj]);
+            df64 dy = d_sub(yid, dy_s[jj]);
+            if (md.aniso) {
+              dx = d_mul(dx, md.ax);
+              dy = d_mul(dy, md.ay);
+            }
             const df64 r2 = df_add(d_mul(dx, dx), d_mul(dy, dy));
             v = md.family == RSF_RQ ? rq_df(md, r2) : matern_df(md, d_sqrt(r2));
           }
           df_mac(acc, v, dv_s[jj]);
         } else {
-          const double k = jg == i ? kernel_diag(kp) : kernel_offdiag(kp, sqrt(dist2(xi, yi, sx[jj], sy[jj])));
+          const double k = jg == i ? kernel_diag(kp) : kernel_pair(kp, xi, yi, sx[jj], sy[jj]);
           const double y = fma(k, sv[jj], -comp);
           const double tsum = acc64 + y;
           comp = (tsum - acc64) - y;
@@ -239,7 +245,7 @@ __global__ void __launch_bounds__(RT) cross_matvec_kernel(const double* __restri
     const int jn = n - jt < RT ? (int)(n - jt) : RT;
     if (i < m)
       for (int jj = 0; jj < jn; jj++) {
-        const double k = kernel_offdiag(kp, sqrt(dist2(xi, yi, sx[jj], sy[jj])));
+        const double k = kernel_pair(kp, xi, yi, sx[jj], sy[jj]);
         const double yk = fma(k, sv[jj], -comp);
         const double tsum = acc + yk;
         comp = (tsum - acc) - yk;
@@ -304,7 +310,11 @@ void kernel_residual(rsf_handle_s* F, const double* zt, const double* xt_vec, do
   MaternDF md{};
   md.family = kp.family;
   const double c = kp.family == RSF_MATERN32 ? std::sqrt(3.0) : kp.family == RSF_MATERN52 ? std::sqrt(5.0) : 1.0;
-  md.c = host_df(kp.family == RSF_RQ ? 1.0 / (2.0 * kp.alpha * kp.l * kp.l) : c / kp.l);
+  const double l = kp.aniso ? 1.0 : kp.l;   // anisotropic: unit length on the scaled differences
+  md.aniso = kp.aniso;
+  md.ax = host_df(kp.aniso ? 1.0 / kp.l : 1.0);
+  md.ay = host_df(kp.aniso ? 1.0 / kp.l2 : 1.0);
+  md.c = host_df(kp.family == RSF_RQ ? 1.0 / (2.0 * kp.alpha * l * l) : c / l);
   md.alpha = kp.family == RSF_RQ ? (int)kp.alpha : 0;
   md.s2 = host_df(kp.s2);
   md.third = host_df(1.0 / 3.0);

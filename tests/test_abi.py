@@ -41,6 +41,7 @@ def test_library_builds_loads_and_exports_every_symbol():
     assert (o.precision, o.trace_form, o.refine, o.probes) == (binding.PREC_MIXED, binding.TRACE_SYM, -1, 64)
     # sizes of the C structs (x86-64 and aarch64 alike): the field lists match rsf.h
     assert ctypes.sizeof(o) == 72 and ctypes.sizeof(binding.RsfInfo) == 80
+    assert ctypes.sizeof(binding.RsfKernel) == 24 and binding.RsfKernel.anisotropic.offset == 16
     # the hook setter rejects a half-set pair without touching the GPU
     alloc = binding._ALLOC_FN(lambda n, s, c: None)
     assert binding.lib().rsf_set_allocator(alloc, binding._FREE_FN(), None) == 1
