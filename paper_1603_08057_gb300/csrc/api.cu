@@ -205,6 +205,25 @@ __global__ void fill_kernel(double* __restrict__ p, int64_t n, double v) {
   if (i < n) p[i] = v;
 }
 
+// Two tree-order vectors a, b <-> one n x 2 row-major block X (the layout of
+// solve_rows' right-hand sides): X[2i] = a[i], X[2i + 1] = b[i].
+__global__ void pack2_kernel(const double* __restrict__ a, const double* __restrict__ b, int64_t n,
+                             double* __restrict__ X) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    X[2 * i] = a[i];
+    X[2 * i + 1] = b[i];
+  }
+}
+__global__ void unpack2_kernel(const double* __restrict__ X, int64_t n, double* __restrict__ a,
+                               double* __restrict__ b) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    a[i] = X[2 * i];
+    b[i] = X[2 * i + 1];
+  }
+}
+
 // Conditional samples (Remark conditional): S(:, j) = mean + Y(0:m, j) - P(0:m, j)
 __global__ void cond_combine_kernel(const double* __restrict__ mean, const double* __restrict__ Y, int64_t ldy,
                                     const double* __restrict__ P, int64_t ldp, int64_t m, int q,
@@ -539,26 +558,35 @@ static void profile_sets(rsf_handle_s* F, const double* z, DBuf& gt, DBuf& sc) {
   const TreeData& T = F->tree_raw->t;
   const int64_t n = T.n;
   const int* perm = T.perm.as<int>();
-  DBuf X, Y;
+  // x = [z | 1] and y = [alpha | beta] as tree-order columns; P, Q hold the
+  // row-major n x 2 blocks the solves take
+  DBuf X, Y, P, Q;
   X.alloc(sizeof(double) * 2 * n, s);
   Y.alloc(sizeof(double) * 2 * n, s);
+  P.alloc(sizeof(double) * 2 * n, s);
+  Q.alloc(sizeof(double) * 2 * n, s);
   gt.alloc(sizeof(double) * n, s);
   sc.alloc(sizeof(double) * S_NSLOTS * T.nsets, s);
   sc.zero();
   double* x = X.as<double>();
   double* y = Y.as<double>();
-  LAUNCH(to_tree_kernel, cdiv(n, 256), 256, 0, s, z, n, 1, perm, n, x);
-  LAUNCH(fill_kernel, cdiv(n, 256), 256, 0, s, x + n, n, 1.0);
-  solve_rows(F, RSF_OP_INV, x, y, 2);
+  const int nb = (int)cdiv(n, 256);
+  LAUNCH(to_tree_kernel, nb, 256, 0, s, z, n, 1, perm, n, x);
+  LAUNCH(fill_kernel, nb, 256, 0, s, x + n, n, 1.0);
+  LAUNCH(pack2_kernel, nb, 256, 0, s, x, x + n, n, P.as<double>());
+  solve_rows(F, RSF_OP_INV, P.as<double>(), Q.as<double>(), 2);
+  LAUNCH(unpack2_kernel, nb, 256, 0, s, Q.as<double>(), n, y, y + n);
   const int sweeps = refine_sweeps(F);
   if (sweeps > 0) {
-    DBuf R, D;
+    DBuf R;
     R.alloc(sizeof(double) * 2 * n, s);
-    D.alloc(sizeof(double) * 2 * n, s);
+    double* r = R.as<double>();
     for (int k = 0; k < sweeps; k++) {
-      for (int c = 0; c < 2; c++) kernel_residual(F, x + c * n, y + c * n, R.as<double>() + c * n);
-      solve_rows(F, RSF_OP_INV, R.as<double>(), D.as<double>(), 2);
-      add_into(y, D.as<double>(), 2 * n, s);
+      for (int c = 0; c < 2; c++) kernel_residual(F, x + c * n, y + c * n, r + c * n);
+      LAUNCH(pack2_kernel, nb, 256, 0, s, r, r + n, n, P.as<double>());
+      solve_rows(F, RSF_OP_INV, P.as<double>(), Q.as<double>(), 2);
+      LAUNCH(unpack2_kernel, nb, 256, 0, s, Q.as<double>(), n, r, r + n);
+      add_into(y, r, 2 * n, s);
     }
   }
   for (int i = 0; i < T.nsets; i++) {
@@ -568,8 +596,8 @@ static void profile_sets(rsf_handle_s* F, const double* z, DBuf& gt, DBuf& sc) {
     dot_into(x + n + r0, y + n + r0, cnt, c + S_ONEB, s);
     dot_into(x + r0, y + r0, cnt, c + S_QUAD, s);
   }
-  LAUNCH(profile_gamma_kernel, cdiv(n, 256), 256, 0, s, y, y + n, n, T.set_off_d.as<int64_t>(), T.nsets,
-         sc.as<double>(), gt.as<double>());
+  LAUNCH(profile_gamma_kernel, nb, 256, 0, s, y, y + n, n, T.set_off_d.as<int64_t>(), T.nsets, sc.as<double>(),
+         gt.as<double>());
   for (int i = 0; i < T.nsets; i++) {
     const int64_t r0 = T.set_off[i], cnt = T.set_off[i + 1] - r0;
     dot_into(x + r0, gt.as<double>() + r0, cnt, sc.as<double>() + (int64_t)i * S_NSLOTS + S_PQ, s);
