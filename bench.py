@@ -175,7 +175,8 @@ FAMILY_NAMES = {WL.MATERN12: "matern12 nu=1/2", WL.MATERN32: "matern32 nu=3/2", 
 def workload_config(name, n=None):
     wl = dict(WL.WORKLOADS[name])
     n = n or wl["n"]
-    pts = "uniform+4 clusters (sigma 0.03)" if wl["points"] == "mixture" else "uniform in [0,1]^2"
+    pts = {"mixture": "uniform+4 clusters (sigma 0.03)", "uniform": "uniform in [0,1]^2",
+           "grid": "sqrt(n) x sqrt(n) grid of [0,100]^2, anisotropic theta = (l1, s2, nug, l2)"}[wl["points"]]
     fam = FAMILY_NAMES[wl["family"]] + (f" alpha={wl['alpha']:g}" if wl["family"] == WL.RQ else "")
     return wl, {"workload": f"{fam} {wl['points']} n={n}", "n": n, "points": pts,
                 "theta": list(wl["theta"]), "tol_fact": wl["tol_fact"], "tol_peel": wl["tol_peel"],
@@ -183,7 +184,7 @@ def workload_config(name, n=None):
 
 
 def theta_at(th0, i):
-    return (th0[0] * (1 + 1e-3 * (i % 7)), th0[1], th0[2])
+    return (th0[0] * (1 + 1e-3 * (i % 7)),) + tuple(th0[1:])
 
 
 # --------------------------------------------------------------- CPU oracle
@@ -409,15 +410,16 @@ def run_gpu(args):
         ll_m, g_m, t_m = results[-1]
         ref = (ll_o, g_o.numpy(), t_o.numpy()) if oname == "fp64" else (ll_m, g_m.numpy(), t_m.numpy())
         cmp_ = (ll_m, g_m.numpy(), t_m.numpy()) if oname == "fp64" else (ll_o, g_o.numpy(), t_o.numpy())
-        scale = 0.5 * np.abs(ref[2][:3]) + 0.5 * np.abs(ref[2][3:])
+        p = len(th0)
+        scale = 0.5 * np.abs(ref[2][:p]) + 0.5 * np.abs(ref[2][p:])
         g_rel = [rel(a, b) for a, b in zip(cmp_[1], ref[1])]
         g_scl = [float(abs(a - b) / s) for a, b, s in zip(cmp_[1], ref[1], scale)]
         other = {"form": oname, "steps": 1, "value": 1e3 / ms_o, "unit": UNIT, "ms_per_step": ms_o,
                  "theta": list(theta_at(th0, args.steps - 1)),
                  "mixed_vs_fp64": {"loglik_rel": rel(cmp_[0], ref[0]),
                                    "score_rel": g_rel, "score_rel_term_scale": g_scl,
-                                   "quad_terms_rel": [rel(a, b) for a, b in zip(cmp_[2][:3], ref[2][:3])],
-                                   "trace_terms_rel": [rel(a, b) for a, b in zip(cmp_[2][3:], ref[2][3:])],
+                                   "quad_terms_rel": [rel(a, b) for a, b in zip(cmp_[2][:p], ref[2][:p])],
+                                   "trace_terms_rel": [rel(a, b) for a, b in zip(cmp_[2][p:], ref[2][p:])],
                                    "gates": {"loglik_1e-6": rel(cmp_[0], ref[0]) <= 1e-6,
                                              "score_1e-3": all(e <= 1e-3 for e in g_rel)}}}
 
@@ -441,7 +443,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
         e2e = {"value": k_e2e / te, "unit": UNIT, "h2d_bytes_per_step": int(hp.numel() * 8 + hz.numel() * 8),
-               "d2h_bytes_per_step": 10 * 8, "steps": k_e2e,
+               "d2h_bytes_per_step": (1 + 3 * len(th0)) * 8, "steps": k_e2e,
                "theta": "the first %d of the timed steps' theta values" % k_e2e}
 
     if rank != 0:

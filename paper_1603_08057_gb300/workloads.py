@@ -91,6 +91,15 @@ WORKLOADS = {
     "rq2_uniform_n1048576": dict(
         n=1048576, points="uniform", seed_points=7, seed_z=8, family=RQ,
         alpha=2.0, theta=(0.02, 1.0, 1e-2), tol_fact=1e-9, tol_peel=1e-6),
+    # the paper's gridded experiments (Sec. 5.1, 5.3): sqrt(n) x sqrt(n) grid
+    # of [0, 100]^2, anisotropic theta = [10, 7] as (l1, s2, nug, l2) with unit
+    # variance and noise 1e-4, eps_fact = eps_peel / 1000
+    "matern32_grid_aniso_n262144": dict(
+        n=262144, points="grid", seed_points=0, seed_z=11, family=MATERN32,
+        alpha=0.0, theta=(10.0, 1.0, 1e-4, 7.0), tol_fact=1e-9, tol_peel=1e-6),
+    "rq_half_grid_aniso_n262144": dict(
+        n=262144, points="grid", seed_points=0, seed_z=12, family=RQ,
+        alpha=0.5, theta=(10.0, 1.0, 1e-4, 7.0), tol_fact=1e-9, tol_peel=1e-6),
 }
 
 
@@ -99,4 +108,9 @@ def make_points(kind: str, n: int, seed: int) -> np.ndarray:
         return uniform(n, seed)
     if kind == "mixture":
         return mixture(n, seed)
+    if kind == "grid":
+        side = int(round(n ** 0.5))
+        if side * side != n:
+            raise ValueError("a grid workload needs a square point count")
+        return grid(side)
     raise ValueError(f"unknown point distribution {kind!r}")
