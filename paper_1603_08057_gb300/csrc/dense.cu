@@ -618,8 +618,20 @@ void QRBatch::run(double* pool, DevStatus* st, int level, cudaStream_t s) {
     RSF_CUDA(cudaEventSynchronize(e1));
     float ms = 0.f;
     RSF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    fprintf(stderr, "[rsf] qr batch (level %d): %d problems, %lld columns, %lld rows, %d steps max, %.2f ms\n", level,
-            nprob, (long long)ncols, (long long)nrows, maxsteps, ms);
+    // fp64 flops of the run: per problem and step j < k, the pivot column's
+    // norm (m - j) and, per remaining column, a dot and an update (4 (m - j))
+    std::vector<QRState> sth(nprob);
+    std::vector<QRProb> pph(nprob);
+    d2h(sth.data(), state.as<QRState>(), nprob, s);
+    d2h(pph.data(), prob.as<QRProb>(), nprob, s);
+    sync(s);
+    double fl = 0.0;
+    for (int i = 0; i < nprob; i++)
+      for (int j = 0; j < sth[i].k; j++) fl += 2.0 * (pph[i].m - j) * (1.0 + 2.0 * (pph[i].c - j - 1));
+    fprintf(stderr,
+            "[rsf] qr batch (level %d): %d problems, %lld columns, %lld rows, %d steps max, %.2f ms, %.3g flop, "
+            "%.3f TFLOP/s\n",
+            level, nprob, (long long)ncols, (long long)nrows, maxsteps, ms, fl, fl / (ms * 1e9));
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
   }
