@@ -225,6 +225,14 @@ rsf_status rsf_tree_build(const double* points, int64_t n, const rsf_opts* opts,
                           void* stream, rsf_tree* out);
 void rsf_tree_destroy(rsf_tree t);
 
+/* The tree's point order and box table (Sec. 2.1): *n_out points and
+ * *nbox_out boxes (host); when perm and boxes are not NULL also perm (host,
+ * n ints: tree position -> input index) and boxes (host, nbox x 6 ints,
+ * row-major: level, first tree position, point count, parent box (-1 for a
+ * root), child slot (0 SW, 1 SE, 2 NW, 3 NE), point set).  Boxes are numbered
+ * breadth first, the roots of all sets first.  Synchronises. */
+rsf_status rsf_tree_export(rsf_tree t, int64_t* n_out, int* nbox_out, int* perm, int* boxes);
+
 /* RSF of Sigma (which = RSF_SIGMA, Cholesky of the diagonal blocks) or of a
  * derivative matrix dSigma/dtheta_k (which = RSF_D_L / RSF_D_S2; diagonal
  * blocks kept for application, Remark (indefinite)).  tol is the relative ID

@@ -29,7 +29,8 @@ EXPORTS = ["rsf_opts_default", "rsf_last_error", "rsf_tree_build", "rsf_tree_des
            "rsf_launch_count", "rsf_profile_enable", "rsf_profile_read", "rsf_destroy",
            "rsf_solve_noalloc", "rsf_set_allocator", "rsf_build_batched", "rsf_logdet_sets",
            "gp_loglik_and_score_batched", "rsf_selftest_wait_limit", "rsf_selftest_gemm",
-           "gp_profile_loglik_and_score", "gp_profile_loglik_and_score_batched", "gp_conditional"]
+           "gp_profile_loglik_and_score", "gp_profile_loglik_and_score_batched", "gp_conditional",
+           "rsf_tree_export"]
 
 
 class RsfKernel(C.Structure):
@@ -78,6 +79,7 @@ def lib():
         L.rsf_opts_default.restype = None
         L.rsf_tree_build.argtypes = [vp, i64, C.POINTER(RsfOpts), vp, C.POINTER(vp)]
         L.rsf_tree_destroy.argtypes = [vp]
+        L.rsf_tree_export.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int), vp, vp]
         L.rsf_tree_destroy.restype = None
         L.rsf_build.argtypes = [vp, i64, C.POINTER(RsfKernel), dp, ip, C.c_double,
                                 C.POINTER(RsfOpts), vp, C.POINTER(vp)]
@@ -251,6 +253,16 @@ class Tree:
         self.h = C.c_void_p()
         _check(lib().rsf_tree_build(self.points.data_ptr(), self.n, C.byref(o) if o else None,
                                     _stream(), C.byref(self.h)))
+
+    def export(self):
+        """rsf_tree_export: (perm (n,), boxes (nbox, 6): level, start, count,
+        parent, slot, set) as numpy int arrays."""
+        n, nb = C.c_int64(), C.c_int()
+        _check(lib().rsf_tree_export(self.h, C.byref(n), C.byref(nb), None, None))
+        perm = np.empty(n.value, dtype=np.int32)
+        boxes = np.empty((nb.value, 6), dtype=np.int32)
+        _check(lib().rsf_tree_export(self.h, C.byref(n), C.byref(nb), perm.ctypes.data, boxes.ctypes.data))
+        return perm, boxes
 
     def __del__(self):
         if getattr(self, "h", None) and _lib is not None:

@@ -421,6 +421,25 @@ rsf_status rsf_tree_build(const double* points, int64_t n, const rsf_opts* opts,
   API_END
 }
 
+rsf_status rsf_tree_export(rsf_tree t, int64_t* n_out, int* nbox_out, int* perm, int* boxes) {
+  API_BEGIN
+  RSF_CHECK(t && n_out && nbox_out, RSF_EINVAL, "tree, n_out and nbox_out must not be NULL");
+  const TreeData& T = t->t;
+  *n_out = T.n;
+  *nbox_out = (int)T.level.size();
+  if (perm) {
+    d2h(perm, T.perm.as<int>(), T.n, T.stream);
+    sync(T.stream);
+  }
+  if (boxes)
+    for (size_t b = 0; b < T.level.size(); b++) {
+      int* r = boxes + 6 * b;
+      r[0] = T.level[b]; r[1] = T.start[b]; r[2] = T.count[b];
+      r[3] = T.parent[b]; r[4] = T.slot[b]; r[5] = T.box_set[b];
+    }
+  API_END
+}
+
 void rsf_tree_destroy(rsf_tree t) {
   if (!t) return;
   std::lock_guard<std::mutex> lk(g_tree_mu);

@@ -17,7 +17,6 @@
 // The host only sizes the levels (one readback of the ranks per level).
 #include <algorithm>
 #include <cmath>
-#include <unordered_map>
 
 #include "internal.cuh"
 
@@ -48,6 +47,109 @@ struct NearBox {
   int u0, nu;        // unit range
   int64_t out0;      // offset of the near list
 };
+
+// Candidate units of every box of a level, on the device.  The cells of the
+// box's level within ext = ceil(r_near + 1/2) cells whose square comes
+// closer than r_near * w to the box centre are looked up (the box there, or
+// the coarser leaf covering the cell; a coarser non-leaf means an empty
+// region); each distinct box found other than the box itself is a unit.
+// Boxes of one level are contiguous in breadth-first order, which is ascending
+// in (set, Morton code of the cell), so a cell is found by binary search in
+// its level's range of box codes.
+struct NearIn {
+  double cx, cy, w, lox, loy;
+  int set, ix, iy, box;
+};
+struct BoxCodes {
+  const unsigned long long* code;   // per box: set << 48 | Morton code of (ix, iy)
+  const int* lev0;                  // first box of every level (L + 2 entries)
+  const char* leaf;
+  const int* start;
+  const int* count;
+  const int* level;
+};
+constexpr int NEAR_MAX_UNITS = 64;
+
+__device__ __forceinline__ unsigned long long cell_code(int set, unsigned gx, unsigned gy, int lev) {
+  unsigned long long c = 0;
+  for (int b = lev - 1; b >= 0; b--)
+    c = (c << 2) | ((unsigned long long)((gy >> b) & 1u) << 1) | (unsigned long long)((gx >> b) & 1u);
+  return ((unsigned long long)set << 48) | c;
+}
+
+__device__ int find_box(const BoxCodes& K, int set, unsigned gx, unsigned gy, int lv) {
+  const unsigned long long key = cell_code(set, gx, gy, lv);
+  int lo = K.lev0[lv], hi = K.lev0[lv + 1];
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (K.code[mid] < key) lo = mid + 1;
+    else hi = mid;
+  }
+  return (lo < K.lev0[lv + 1] && K.code[lo] == key) ? lo : -1;
+}
+
+// write == 0: units and candidate rows per box into nunits, ncand;
+// write == 1: the units themselves from u0[i] on.
+__global__ void near_units_kernel(const NearIn* __restrict__ in, int nb, int lev, double r_near, BoxCodes K,
+                                  const int64_t* __restrict__ row0, const int* __restrict__ cl,
+                                  int* __restrict__ nunits, int64_t* __restrict__ ncand,
+                                  const int* __restrict__ u0, Unit* __restrict__ units, int write,
+                                  int* __restrict__ overflow) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nb) return;
+  const NearIn B = in[i];
+  const double R = __dmul_rn(r_near, B.w);
+  const int ext = (int)ceil(r_near + 0.5);
+  const int side = 1 << lev;
+  int seen[NEAR_MAX_UNITS];
+  int nseen = 0, nu = 0;
+  int64_t cand = 0;
+  for (int dy = -ext; dy <= ext; dy++) {
+    for (int dx = -ext; dx <= ext; dx++) {
+      const int gx = B.ix + dx, gy = B.iy + dy;
+      if (gx < 0 || gy < 0 || gx >= side || gy >= side) continue;
+      const double x0 = __dadd_rn(B.lox, __dmul_rn((double)gx, B.w));
+      const double y0 = __dadd_rn(B.loy, __dmul_rn((double)gy, B.w));
+      const double ddx = fmax(0.0, fmax(__dsub_rn(x0, B.cx), __dsub_rn(B.cx, __dadd_rn(x0, B.w))));
+      const double ddy = fmax(0.0, fmax(__dsub_rn(y0, B.cy), __dsub_rn(B.cy, __dadd_rn(y0, B.w))));
+      if (__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)) >= __dmul_rn(R, R)) continue;
+      int found = -1;
+      for (int lv = lev; lv >= 0 && found < 0; lv--)
+        found = find_box(K, B.set, (unsigned)gx >> (lev - lv), (unsigned)gy >> (lev - lv), lv);
+      if (found < 0 || found == B.box) continue;
+      const int flev = K.level[found];
+      if (flev != lev && !K.leaf[found]) continue;   // empty region
+      bool dup = false;
+      for (int k = 0; k < nseen; k++) dup |= seen[k] == found;
+      if (dup) continue;
+      if (nseen == NEAR_MAX_UNITS) {
+        atomicExch(overflow, 1);
+        continue;
+      }
+      seen[nseen++] = found;
+      Unit u;
+      if (flev == lev) {
+        const int fi = found - K.lev0[lev];
+        u.off = row0[fi];
+        u.count = cl[fi];
+        u.kind = 1;
+      } else {
+        u.off = K.start[found];
+        u.count = K.count[found];
+        u.kind = 0;
+      }
+      if (u.count > 0) {
+        if (write) units[u0[i] + nu] = u;
+        nu++;
+        cand += u.count;
+      }
+    }
+  }
+  if (!write) {
+    nunits[i] = nu;
+    ncand[i] = cand;
+  }
+}
 
 // One CTA per box: ordered compaction of the candidates within the radius.
 __global__ void __launch_bounds__(256) near_kernel(const NearBox* __restrict__ nbx, const Unit* __restrict__ units,
@@ -329,13 +431,36 @@ void factorize(rsf_handle_s* h) {
   upload(dproxy, ptab, s);
   DBuf rowmap;
   rowmap.alloc(sizeof(int) * n, s);
-  // per-level grid hash for neighbour lookup: key (set, ix, iy) -> box; boxes
-  // of different point sets are never neighbours
-  auto cell_key = [](int set, int gx, int gy) {
-    return ((uint64_t)(uint32_t)set << 48) | ((uint64_t)(uint32_t)gx << 24) | (uint64_t)(uint32_t)gy;
-  };
-  std::vector<std::unordered_map<uint64_t, int>> grid(L + 1);
-  for (int b = 0; b < nboxes; b++) grid[T.level[b]][cell_key(T.box_set[b], T.ix[b], T.iy[b])] = b;
+  // box codes for the device near-field lookup (boxes of different point
+  // sets are never neighbours: the set sits above the cell code)
+  DBuf dcode, dlev0, dbleaf, dbstart, dbcount, dblevel;
+  {
+    std::vector<unsigned long long> code(nboxes);
+    std::vector<int> lev0(L + 2, 0);
+    for (int b = 0; b < nboxes; b++) {
+      unsigned long long c = 0;
+      for (int bit = T.level[b] - 1; bit >= 0; bit--)
+        c = (c << 2) | ((unsigned long long)((T.iy[b] >> bit) & 1) << 1) | (unsigned long long)((T.ix[b] >> bit) & 1);
+      code[b] = ((unsigned long long)T.box_set[b] << 48) | c;
+      lev0[T.level[b] + 1]++;
+    }
+    for (int l = 0; l <= L; l++) lev0[l + 1] += lev0[l];
+    for (int l = 0; l <= L; l++)
+      RSF_CHECK(T.by_level[l].empty() || (T.by_level[l].front() == lev0[l] && T.by_level[l].back() == lev0[l + 1] - 1),
+                RSF_ECUDA, "box table: levels are not contiguous");
+    for (int b = 1; b < nboxes; b++)
+      RSF_CHECK(T.level[b] != T.level[b - 1] || code[b] > code[b - 1], RSF_ECUDA,
+                "box table: a level is not in ascending cell order");
+    std::vector<char> leafv(T.is_leaf.begin(), T.is_leaf.end());
+    upload(dcode, code, s);
+    upload(dlev0, lev0, s);
+    upload(dbleaf, leafv, s);
+    upload(dbstart, T.start, s);
+    upload(dbcount, T.count, s);
+    upload(dblevel, T.level, s);
+  }
+  const BoxCodes bcodes{dcode.as<unsigned long long>(), dlev0.as<int>(), dbleaf.as<char>(), dbstart.as<int>(),
+                        dbcount.as<int>(), dblevel.as<int>()};
 
   std::vector<int> box2idx(nboxes, -1);   // index of a box within its level
   DBuf prevAII;                           // A_II pool of the level below (children's X_SS)
@@ -402,10 +527,11 @@ void factorize(rsf_handle_s* h) {
     std::vector<int> rowbox(Lv.nrows);
     for (int i = 0; i < nb; i++)
       for (int64_t r = Lv.row0[i]; r < Lv.row0[i + 1]; r++) rowbox[r] = i;
-    DBuf drowbox, drow0, dleaf;
+    DBuf drowbox, drow0, dleaf, dcl;
     upload(drowbox, rowbox, s);
     upload(drow0, Lv.row0, s);
     upload(dleaf, Lv.leafbox, s);
+    upload(dcl, Lv.c, s);
 
     // ---- ID (A2-A4), skipped at the root
     Lv.k.assign(nb, 0);
@@ -415,61 +541,50 @@ void factorize(rsf_handle_s* h) {
     QRBatch qb;
     DBuf qrpool, near, nnear;
     if (lev > 0) {
-      // near-field candidate units (host, from the box table)
-      std::vector<Unit> units;
+      // near-field candidate units, enumerated on the device
       std::vector<NearBox> nbx(nb);
       std::vector<int64_t> cand(nb, 0);
       int64_t near_total = 0;
-      for (int i = 0; i < nb; i++) {
-        int b = Lv.box[i];
-        double w = T.w[b];
-        double R = o.r_near * w;
-        nbx[i].cx = T.cx[b];
-        nbx[i].cy = T.cy[b];
-        nbx[i].r2 = R * R;
-        nbx[i].u0 = (int)units.size();
-        int ext = (int)std::ceil(o.r_near + 0.5);
-        std::vector<int> seen;
-        for (int dy = -ext; dy <= ext; dy++) {
-          for (int dx = -ext; dx <= ext; dx++) {
-            int gx = T.ix[b] + dx, gy = T.iy[b] + dy;
-            if (gx < 0 || gy < 0 || gx >= (1 << lev) || gy >= (1 << lev)) continue;
-            // distance from the centre to the cell square
-            const int bs = T.box_set[b];
-            double x0 = T.set_lo[2 * bs] + gx * w, y0 = T.set_lo[2 * bs + 1] + gy * w;
-            double ddx = std::max(0.0, std::max(x0 - T.cx[b], T.cx[b] - (x0 + w)));
-            double ddy = std::max(0.0, std::max(y0 - T.cy[b], T.cy[b] - (y0 + w)));
-            if (ddx * ddx + ddy * ddy >= R * R) continue;
-            // the box covering this cell: same level, or a coarser leaf
-            int found = -1;
-            for (int lv = lev; lv >= 0; lv--) {
-              int sh = lev - lv;
-              auto it = grid[lv].find(cell_key(bs, gx >> sh, gy >> sh));
-              if (it != grid[lv].end()) {
-                found = it->second;
-                break;
-              }
-            }
-            if (found < 0 || found == b) continue;
-            if (T.level[found] != lev && !T.is_leaf[found]) continue;  // empty region
-            if (std::find(seen.begin(), seen.end(), found) != seen.end()) continue;
-            seen.push_back(found);
-            Unit u;
-            if (T.level[found] == lev) {
-              int fi = box2idx[found];
-              u.off = Lv.row0[fi]; u.count = Lv.c[fi]; u.kind = 1;
-            } else {
-              u.off = T.start[found]; u.count = T.count[found]; u.kind = 0;
-            }
-            if (u.count > 0) {
-              units.push_back(u);
-              cand[i] += u.count;
-            }
-          }
+      DBuf dunits;
+      {
+        std::vector<NearIn> nin(nb);
+        for (int i = 0; i < nb; i++) {
+          const int b = Lv.box[i], bs = T.box_set[b];
+          nin[i] = NearIn{T.cx[b], T.cy[b], T.w[b], T.set_lo[2 * bs], T.set_lo[2 * bs + 1], bs, T.ix[b], T.iy[b], b};
         }
-        nbx[i].nu = (int)units.size() - nbx[i].u0;
-        nbx[i].out0 = near_total;
-        near_total += cand[i];
+        DBuf dnin, dnu, dcand, du0, dovf;
+        upload(dnin, nin, s);
+        dnu.alloc(sizeof(int) * nb, s);
+        dcand.alloc(sizeof(int64_t) * nb, s);
+        dovf.alloc(sizeof(int), s);
+        dovf.zero();
+        LAUNCH(near_units_kernel, cdiv(nb, 128), 128, 0, s, dnin.as<NearIn>(), nb, lev, o.r_near, bcodes,
+               drow0.as<int64_t>(), dcl.as<int>(), dnu.as<int>(), dcand.as<int64_t>(), nullptr, nullptr, 0,
+               dovf.as<int>());
+        std::vector<int> nu(nb);
+        int ovf = 0;
+        d2h(nu.data(), dnu.as<int>(), nb, s);
+        d2h(cand.data(), dcand.as<int64_t>(), nb, s);
+        d2h(&ovf, dovf.as<int>(), 1, s);
+        sync(s);
+        RSF_CHECK(!ovf, RSF_EINVAL, "near field: too many neighbour boxes (r_near too large)");
+        std::vector<int> u0(nb + 1, 0);
+        for (int i = 0; i < nb; i++) {
+          u0[i + 1] = u0[i] + nu[i];
+          nbx[i].cx = T.cx[Lv.box[i]];
+          nbx[i].cy = T.cy[Lv.box[i]];
+          const double R = o.r_near * T.w[Lv.box[i]];
+          nbx[i].r2 = R * R;
+          nbx[i].u0 = u0[i];
+          nbx[i].nu = nu[i];
+          nbx[i].out0 = near_total;
+          near_total += cand[i];
+        }
+        upload(du0, u0, s);
+        dunits.alloc(sizeof(Unit) * std::max(1, u0[nb]), s);
+        LAUNCH(near_units_kernel, cdiv(nb, 128), 128, 0, s, dnin.as<NearIn>(), nb, lev, o.r_near, bcodes,
+               drow0.as<int64_t>(), dcl.as<int>(), nullptr, nullptr, du0.as<int>(), dunits.as<Unit>(), 1,
+               dovf.as<int>());
       }
       // QR problems: A = [near; proxy] x c, ld = cand + n_prox
       std::vector<QRProb> qp(nb);
@@ -494,8 +609,7 @@ void factorize(rsf_handle_s* h) {
       near.alloc(sizeof(int) * std::max<int64_t>(1, near_total), s);
       nnear.alloc(sizeof(int) * nb, s);
       {
-        DBuf dunits, dnbx;
-        upload(dunits, units, s);
+        DBuf dnbx;
         upload(dnbx, nbx, s);
         LAUNCH(near_kernel, nb, 256, 0, s, dnbx.as<NearBox>(), dunits.as<Unit>(), I.as<int>(),
                T.xt.as<double>(), near.as<int>(), nnear.as<int>(), qb.d_prob(), o.n_prox);

@@ -175,7 +175,7 @@ struct TreeData {
   std::vector<char> is_leaf;
   std::vector<double> cx, cy, w;
   std::vector<std::vector<int>> by_level;
-  std::vector<int> leafpos;      // host: per tree position, index in its leaf (built lazily)
+  DBuf leafpos_d;                // device: per tree position, index in its leaf
   int max_leaf = 0;
   // independent point sets (batched datasets): set i holds tree positions
   // [set_off[i], set_off[i+1]) and has its own root square

@@ -1136,8 +1136,7 @@ void peel_traces(rsf_handle_s* F, rsf_handle_s* Fk, bool want0, double tol, cons
 
   // ---- extraction: H = (G - sum_m G^(m)) E, trace of the leaf blocks
   const int nl = std::max(1, T.max_leaf);
-  DBuf dlp;
-  upload(dlp, T.leafpos, s);
+  const DBuf& dlp = T.leafpos_d;
   DBuf E, H[2];
   E.alloc(sizeof(double) * n64 * nl, s);
   for (int oi : ops) H[oi].alloc(sizeof(double) * n64 * nl, s);

@@ -1,20 +1,19 @@
-// Quadtree construction (Sec. 2.1, Remark (tree)).
+// Quadtree construction (Sec. 2.1, Remark (tree)), all on the device.
 //
-// Device: bounding box reduction, quantised coordinates and Morton keys
-// (D = 24 bits per axis, y bit above x bit, so child slots are SW, SE, NW,
-// NE), a stable radix sort of (key, index) -- ties keep the original index
-// order -- and the gather of the coordinates into tree order.  Host: the box
-// table (split while a box holds more than n_occ points), derived from the
-// sorted keys with binary searches; it is small (O(n / n_occ) boxes) and the
-// host needs it to size every level.
+// Bounding box reduction, quantised coordinates and Morton keys (D = 24 bits
+// per axis, y bit above x bit, so child slots are SW, SE, NW, NE), a stable
+// least-significant-digit radix sort of (key, index) written here (8-bit
+// digits; ties keep the original index order), the gather of the coordinates
+// into tree order, and the box table: a breadth-first split of every box that
+// holds more than n_occ points, by binary searches of its children's key
+// ranges, in one single-CTA kernel.  The host receives the finished table
+// (O(n / n_occ) boxes), which it needs to size every level.
 //
 // A forest of independent point sets (batched datasets) is built the same
 // way: every set gets its own root square, its set index sits above the 48
 // Morton bits of the key, so one radix sort groups the sets (in order) and
 // orders each set's points; every box records its set.  Boxes of different
 // sets never interact.
-#include <cub/device/device_radix_sort.cuh>
-
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -88,6 +87,222 @@ __global__ void gather_points_kernel(const double* __restrict__ pts, const int* 
   iperm[o] = (int)i;
 }
 
+// ------------------------------------------------------------ radix sort
+// Stable LSD radix sort of (64-bit key, int index) pairs, 8-bit digits.  Per
+// pass: per-tile digit counts (tile = RS_THREADS x RS_ROUNDS elements, in
+// index order), an exclusive scan of the digit-major count table (digit d of
+// tile b at d * ntiles + b), and a scatter in which every element's place is
+// its tile's start for its digit plus its rank among the tile's earlier
+// elements with the same digit (rounds of RS_THREADS consecutive elements;
+// within a round, warps in order and lanes in order).
+constexpr int RS_THREADS = 256;
+constexpr int RS_ROUNDS = 8;
+constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;
+constexpr int RS_WARPS = RS_THREADS / 32;
+
+__global__ void __launch_bounds__(RS_THREADS) radix_count_kernel(const unsigned long long* __restrict__ keys,
+                                                                 int64_t n, int shift, int ntiles,
+                                                                 unsigned int* __restrict__ counts) {
+  __shared__ unsigned int h[256];
+  const int t = threadIdx.x;
+  h[t] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+  for (int r = 0; r < RS_ROUNDS; r++) {
+    const int64_t i = base + (int64_t)r * RS_THREADS + t;
+    if (i < n) atomicAdd(&h[(unsigned)(keys[i] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  counts[(int64_t)t * ntiles + blockIdx.x] = h[t];
+}
+
+// Exclusive scan of m counts in place, one CTA of 1024 threads (each scans a
+// contiguous chunk, then the chunk totals are scanned).
+__global__ void __launch_bounds__(1024) radix_scan_kernel(unsigned int* __restrict__ c, int64_t m) {
+  __shared__ unsigned int part[1024];
+  const int t = threadIdx.x;
+  const int64_t per = (m + 1023) / 1024;
+  const int64_t b = (int64_t)t * per, e = b + per < m ? b + per : m;
+  unsigned int sum = 0;
+  for (int64_t i = b; i < e; i++) sum += c[i];
+  part[t] = sum;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {   // inclusive Hillis-Steele scan of the chunk totals
+    unsigned int v = t >= o ? part[t - o] : 0u;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  unsigned int run = t > 0 ? part[t - 1] : 0u;
+  for (int64_t i = b; i < e; i++) {
+    const unsigned int v = c[i];
+    c[i] = run;
+    run += v;
+  }
+}
+
+__global__ void __launch_bounds__(RS_THREADS) radix_scatter_kernel(
+    const unsigned long long* __restrict__ kin, const int* __restrict__ vin, int64_t n, int shift, int ntiles,
+    const unsigned int* __restrict__ offs, unsigned long long* __restrict__ kout, int* __restrict__ vout) {
+  __shared__ unsigned int run[256];              // elements of each digit placed by earlier rounds
+  __shared__ unsigned int wcnt[RS_WARPS][256];   // this round: per warp and digit counts, then offsets
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  run[t] = offs[(int64_t)t * ntiles + blockIdx.x];
+  const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int r = 0; r < RS_ROUNDS; r++) {
+    for (int k = 0; k < RS_WARPS; k++) wcnt[k][t] = 0;
+    __syncthreads();
+    const int64_t i = base + (int64_t)r * RS_THREADS + t;
+    const bool valid = i < n;
+    unsigned long long key = 0ull;
+    int val = 0;
+    unsigned d = 256u;   // no digit for elements past the end
+    if (valid) {
+      key = kin[i];
+      val = vin[i];
+      d = (unsigned)(key >> shift) & 255u;
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const unsigned rank = __popc(peers & lt);
+    if (valid && rank == 0) wcnt[w][d] = __popc(peers);
+    __syncthreads();
+    {   // thread t owns digit t: offsets of the warps within the round
+      unsigned acc = run[t];
+      for (int k = 0; k < RS_WARPS; k++) {
+        const unsigned c = wcnt[k][t];
+        wcnt[k][t] = acc;
+        acc += c;
+      }
+      run[t] = acc;
+    }
+    __syncthreads();
+    if (valid) {
+      const unsigned pos = wcnt[w][d] + rank;
+      kout[pos] = key;
+      vout[pos] = val;
+    }
+    __syncthreads();
+  }
+}
+
+// Sorts (keys, vals) by the low end_bit bits of the keys; the result ends in
+// (keys, vals) (ping-pong through the two scratch arrays).
+static void radix_sort_pairs(DBuf& keys, DBuf& vals, DBuf& keys2, DBuf& vals2, int64_t n, int end_bit,
+                             cudaStream_t s) {
+  const int ntiles = (int)cdiv(n, RS_TILE);
+  DBuf counts;
+  counts.alloc(sizeof(unsigned int) * 256 * (int64_t)ntiles, s);
+  for (int shift = 0; shift < end_bit; shift += 8) {
+    LAUNCH(radix_count_kernel, ntiles, RS_THREADS, 0, s, keys.as<unsigned long long>(), n, shift, ntiles,
+           counts.as<unsigned int>());
+    LAUNCH(radix_scan_kernel, 1, 1024, 0, s, counts.as<unsigned int>(), (int64_t)256 * ntiles);
+    LAUNCH(radix_scatter_kernel, ntiles, RS_THREADS, 0, s, keys.as<unsigned long long>(), vals.as<int>(), n, shift,
+           ntiles, counts.as<unsigned int>(), keys2.as<unsigned long long>(), vals2.as<int>());
+    std::swap(keys, keys2);
+    std::swap(vals, vals2);
+  }
+}
+
+// ------------------------------------------------------------- box table
+// Breadth-first quadtree over the sorted keys, by one CTA: the roots of all
+// sets first, then level by level the children (slots in Morton order) of
+// every box of the previous level that holds more than n_occ points (and is
+// above the deepest level); a child is the run of positions whose 2-bit digit
+// at that level equals its slot, found by binary search in its parent's
+// range.  Boxes get consecutive ids in that order.  Output per box: level,
+// start, count, parent, slot, ix, iy, set; *nbox_out the number of boxes, or
+// -1 when cap was too small.
+struct BoxRow {
+  int level, start, count, parent, slot, ix, iy, set;
+};
+
+__global__ void __launch_bounds__(1024) box_table_kernel(const unsigned long long* __restrict__ keys,
+                                                         const int64_t* __restrict__ set_off, int nsets, int n_occ,
+                                                         int cap, BoxRow* __restrict__ box, int* __restrict__ nbox_out) {
+  __shared__ int s_run, s_tot[32];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  if (nsets > cap) {
+    if (t == 0) *nbox_out = -1;
+    return;
+  }
+  for (int i = t; i < nsets; i += 1024)
+    box[i] = BoxRow{0, (int)set_off[i], (int)(set_off[i + 1] - set_off[i]), -1, 0, 0, 0, i};
+  __syncthreads();
+  int f0 = 0, f1 = nsets;   // the previous level's boxes
+  int nb = nsets;
+  for (int lev = 0; lev < DEPTH_BITS && f1 > f0; lev++) {
+    const int shift = 2 * (DEPTH_BITS - lev - 1);
+    if (t == 0) s_run = 0;
+    __syncthreads();
+    for (int c0 = f0; c0 < f1; c0 += 1024) {   // chunks of parents, in order
+      const int b = c0 + t;
+      int bounds[5] = {0, 0, 0, 0, 0};
+      int made = 0;
+      BoxRow P{};
+      if (b < f1) {
+        P = box[b];
+        if (P.count > n_occ) {
+          for (int sl = 0; sl <= 4; sl++) {
+            int lo = P.start, hi = P.start + P.count;
+            while (lo < hi) {
+              const int mid = (lo + hi) >> 1;
+              if ((int)((keys[mid] >> shift) & 3ull) < sl) lo = mid + 1;
+              else hi = mid;
+            }
+            bounds[sl] = lo;
+          }
+          for (int sl = 0; sl < 4; sl++) made += bounds[sl + 1] > bounds[sl];
+        }
+      }
+      // exclusive scan of "made" over the chunk (warp shuffles, then warps)
+      int inc = made;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += v;
+      }
+      if (lane == 31) s_tot[w] = inc;
+      __syncthreads();
+      if (w == 0) {
+        int v = s_tot[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+          const int u = __shfl_up_sync(0xffffffffu, v, o);
+          if (lane >= o) v += u;
+        }
+        s_tot[lane] = v;   // inclusive over warps
+      }
+      __syncthreads();
+      const int before = (w > 0 ? s_tot[w - 1] : 0) + inc - made;
+      const int id0 = nb + s_run + before;
+      if (made > 0 && id0 + made <= cap) {
+        int k = 0;
+        for (int sl = 0; sl < 4; sl++)
+          if (bounds[sl + 1] > bounds[sl])
+            box[id0 + k++] = BoxRow{lev + 1, bounds[sl], bounds[sl + 1] - bounds[sl], b, sl,
+                                    2 * P.ix + (sl & 1), 2 * P.iy + (sl >> 1), P.set};
+      }
+      __syncthreads();
+      if (t == 0) s_run += s_tot[31];
+      __syncthreads();
+    }
+    f0 = nb;
+    nb += s_run;
+    f1 = nb;
+    if (nb > cap) break;
+    __syncthreads();
+  }
+  if (t == 0) *nbox_out = nb > cap ? -1 : nb;
+}
+
+// Index of every tree position within its leaf.
+__global__ void leafpos_kernel(const BoxRow* __restrict__ box, const char* __restrict__ leaf, int nbox,
+                               int* __restrict__ leafpos) {
+  const int b = blockIdx.x;
+  if (b >= nbox || !leaf[b]) return;
+  const BoxRow B = box[b];
+  for (int i = threadIdx.x; i < B.count; i += blockDim.x) leafpos[B.start + i] = i;
+}
+
 std::shared_ptr<rsf_tree_s> build_forest(const double* points, const std::vector<int64_t>& set_off,
                                          const rsf_opts& o, cudaStream_t s) {
   const int nsets = (int)set_off.size() - 1;
@@ -159,23 +374,11 @@ std::shared_ptr<rsf_tree_s> build_forest(const double* points, const std::vector
   bad.zero();
   LAUNCH(keys_kernel, cdiv(n, 256), 256, 0, s, points, n, doff.as<int64_t>(), nsets, dgeom.as<double>(),
          keys.as<unsigned long long>(), idx.as<int>(), bad.as<int>());
-  size_t tmp_bytes = 0;
-  const int end_bit = 2 * DEPTH_BITS + set_bits;
-  RSF_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, keys.as<unsigned long long>(),
-                                           keys2.as<unsigned long long>(), idx.as<int>(), idx2.as<int>(),
-                                           (int)n, 0, end_bit, s));
-  DBuf tmp;
-  tmp.alloc(std::max<size_t>(tmp_bytes, 16), s);
-  RSF_CUDA(cub::DeviceRadixSort::SortPairs(tmp.p, tmp_bytes, keys.as<unsigned long long>(),
-                                           keys2.as<unsigned long long>(), idx.as<int>(), idx2.as<int>(),
-                                           (int)n, 0, end_bit, s));
-  g_launches += 4;  // the radix sort's own passes (approximate count)
-  std::vector<unsigned long long> hk(n);
-  d2h(hk.data(), keys2.as<unsigned long long>(), n, s);
+  radix_sort_pairs(keys, idx, keys2, idx2, n, 2 * DEPTH_BITS + set_bits, s);
   int hbad = 0;
   d2h(&hbad, bad.as<int>(), 1, s);
   // tree-order coordinates
-  T.perm = std::move(idx2);
+  T.perm = std::move(idx);
   T.xt.alloc(sizeof(double) * 2 * n, s);
   T.iperm.alloc(sizeof(int) * n, s);
   LAUNCH(gather_points_kernel, cdiv(n, 256), 256, 0, s, points, T.perm.as<int>(), n,
@@ -183,46 +386,50 @@ std::shared_ptr<rsf_tree_s> build_forest(const double* points, const std::vector
   sync(s);
   RSF_CHECK(!hbad, RSF_EINVAL, "points contain NaN or Inf");
 
-  // Box table, breadth first (same rule as the quadtree description above);
-  // the roots of all sets first, so the levels stay contiguous.
-  auto add_box = [&](int lev, int st, int ct, int par, int sl, int bx, int by, int set) {
-    T.level.push_back(lev); T.start.push_back(st); T.count.push_back(ct);
-    T.parent.push_back(par); T.slot.push_back(sl); T.ix.push_back(bx); T.iy.push_back(by);
-    T.box_set.push_back(set);
-    T.children.push_back({-1, -1, -1, -1});
-    return (int)T.level.size() - 1;
-  };
-  std::vector<int> frontier;
-  for (int i = 0; i < nsets; i++)
-    frontier.push_back(add_box(0, (int)set_off[i], (int)(set_off[i + 1] - set_off[i]), -1, 0, 0, 0, i));
-  int lev = 0;
-  while (!frontier.empty()) {
-    std::vector<int> next;
-    for (int b : frontier) {
-      if (T.count[b] <= o.n_occ || lev >= DEPTH_BITS) continue;
-      int s0 = T.start[b], c0 = T.count[b];
-      int shift = 2 * (DEPTH_BITS - lev - 1);
-      int bounds[5];
-      for (int sl = 0; sl <= 4; sl++) {
-        // first position in [s0, s0+c0) whose 2-bit digit at this level >= sl
-        int lo = s0, hi = s0 + c0;
-        while (lo < hi) {
-          int mid = (lo + hi) >> 1;
-          if ((int)((hk[mid] >> shift) & 3ull) < sl) lo = mid + 1; else hi = mid;
-        }
-        bounds[sl] = lo;
+  // box table on the device; the capacity starts near the usual count
+  // (about n / n_occ boxes per level of splitting) and grows on overflow
+  std::vector<BoxRow> rows;
+  {
+    int64_t cap = nsets + 8 * (n / (o.n_occ + 1) + 1) + 1024;
+    const int64_t cap_max = nsets + 4 * (int64_t)DEPTH_BITS * (n / (o.n_occ + 1) + 1);
+    DBuf dbox, dnb;
+    dnb.alloc(sizeof(int), s);
+    for (;;) {
+      const int64_t c = std::min(cap, cap_max);
+      RSF_CHECK(c < (int64_t)1 << 31, RSF_EINVAL, "too many boxes");
+      dbox.alloc(sizeof(BoxRow) * c, s);
+      LAUNCH(box_table_kernel, 1, 1024, 0, s, keys.as<unsigned long long>(), doff.as<int64_t>(), nsets, o.n_occ,
+             (int)c, dbox.as<BoxRow>(), dnb.as<int>());
+      int nbh = 0;
+      d2h(&nbh, dnb.as<int>(), 1, s);
+      sync(s);
+      if (nbh >= 0) {
+        rows.resize(nbh);
+        d2h(rows.data(), dbox.as<BoxRow>(), nbh, s);
+        sync(s);
+        break;
       }
-      for (int sl = 0; sl < 4; sl++) {
-        if (bounds[sl + 1] > bounds[sl]) {
-          int c = add_box(lev + 1, bounds[sl], bounds[sl + 1] - bounds[sl], b, sl,
-                          2 * T.ix[b] + (sl & 1), 2 * T.iy[b] + (sl >> 1), T.box_set[b]);
-          T.children[b][sl] = c;
-          next.push_back(c);
-        }
-      }
+      RSF_CHECK(c < cap_max, RSF_ECUDA, "box table: capacity bound exceeded");
+      cap *= 4;
     }
-    frontier.swap(next);
-    lev++;
+    const int nbox = (int)rows.size();
+    T.level.resize(nbox); T.start.resize(nbox); T.count.resize(nbox); T.parent.resize(nbox);
+    T.slot.resize(nbox); T.ix.resize(nbox); T.iy.resize(nbox); T.box_set.resize(nbox);
+    T.children.assign(nbox, {-1, -1, -1, -1});
+    for (int b = 0; b < nbox; b++) {
+      const BoxRow& r = rows[b];
+      T.level[b] = r.level; T.start[b] = r.start; T.count[b] = r.count; T.parent[b] = r.parent;
+      T.slot[b] = r.slot; T.ix[b] = r.ix; T.iy[b] = r.iy; T.box_set[b] = r.set;
+      if (r.parent >= 0) T.children[r.parent][r.slot] = b;
+    }
+    // per-position index within its leaf, on the device
+    std::vector<char> leaf(nbox);
+    for (int b = 0; b < nbox; b++)
+      leaf[b] = T.children[b][0] < 0 && T.children[b][1] < 0 && T.children[b][2] < 0 && T.children[b][3] < 0;
+    DBuf dleaf;
+    upload(dleaf, leaf, s);
+    T.leafpos_d.alloc(sizeof(int) * n, s);
+    LAUNCH(leafpos_kernel, nbox, 128, 0, s, dbox.as<BoxRow>(), dleaf.as<char>(), nbox, T.leafpos_d.as<int>());
   }
   int nbox = (int)T.level.size();
   T.is_leaf.resize(nbox);
@@ -240,10 +447,6 @@ std::shared_ptr<rsf_tree_s> build_forest(const double* points, const std::vector
   }
   T.by_level.assign(T.L + 1, {});
   for (int b = 0; b < nbox; b++) T.by_level[T.level[b]].push_back(b);
-  T.leafpos.assign(n, 0);
-  for (int b = 0; b < nbox; b++)
-    if (T.is_leaf[b])
-      for (int i = 0; i < T.count[b]; i++) T.leafpos[T.start[b] + i] = i;
   upload(T.box_set_d, T.box_set, s);
   upload(T.set_off_d, T.set_off, s);
   return tr;
