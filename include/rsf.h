@@ -192,9 +192,12 @@ rsf_status rsf_selftest_wait_limit(void* stream);
  * arrays A, B, C; op(X) = X^T when ta / tb is nonzero; op(A) is m x k, op(B)
  * k x n) with one of the batched-GEMM engines that the solves and the
  * peeling use: 0 fp64 on the CUDA cores, 1 df64 operands multiplied on the
- * tensor cores (bf16 slices, exact fp32 accumulation; batches with fewer
- * than 64 rows fall back to engine 2), 2 df64 arithmetic on the CUDA cores.
- * Operands are copied and, for engines 1 and 2, rounded to df64 pairs first,
+ * tensor cores (bf16 slices cut once per operand into work buffers, exact
+ * fp32 accumulation over superblocks of 384 terms; batches with fewer than
+ * 64 rows fall back to engine 2), 2 df64 arithmetic on the CUDA cores, 3 the
+ * tensor-core engine that slices inside the GEMM kernel (K-blocks of 64
+ * terms, no work buffers; the allocation-free solve uses it).
+ * Operands are copied and, for engines 1 to 3, rounded to df64 pairs first,
  * so the result carries that rounding (~2^-48 relative per operand).
  * Synchronises the stream. */
 rsf_status rsf_selftest_gemm(int engine, int m, int n, int k, int ta, int tb, double alpha,

@@ -215,7 +215,8 @@ def selftest_wait_limit() -> None:
 def selftest_gemm(engine: int, A: torch.Tensor, B: torch.Tensor, C: torch.Tensor | None = None,
                   ta=False, tb=False, alpha=1.0, beta=0.0) -> torch.Tensor:
     """rsf_selftest_gemm: alpha op(A) op(B) + beta C with batched-GEMM engine
-    `engine` (0 fp64, 1 tensor cores on df64 operands, 2 df64 CUDA cores) for
+    `engine` (0 fp64, 1 tensor cores on pre-sliced df64 operands, 2 df64 CUDA
+    cores, 3 tensor cores slicing inside the kernel) for
     float64 CUDA matrices in torch's row-major layout.  A row-major matrix is
     the column-major transpose, so the library computes the column-major
     C^T = op(B)^T op(A)^T, whose memory is the row-major C."""

@@ -242,6 +242,38 @@ void GemmBatch::build(const std::vector<GemmDesc>& d, cudaStream_t s) {
   upload(desc, d, s);
   upload(prefix, pre, s);
   upload(ntile_tc, nttc, s);
+  // plan of the pre-sliced tensor-core engine
+  std::vector<TcDescPlan> dp(nprob);
+  std::vector<TcEntryPlan> ep(nttc.size());
+  tc_pi = tc_qi = tc_pa = tc_qa = tc_pe = tc_qe = tc_bblk = tc_be = tc_pib = 0;
+  for (int i = 0; i < nprob; i++) {
+    const int K = std::max(0, d[i].K);
+    TcDescPlan& q = dp[i];
+    q.nch = cdiv(K, TC_KC);
+    q.nsb = cdiv(K, TC_SBK);
+    q.pi = tc_pi; q.qi = tc_qi; q.pa = tc_pa; q.qa = tc_qa; q.pe = tc_pe; q.qe = tc_qe;
+    if (d[i].M >= 0) {
+      const int64_t mt = cdiv(d[i].M, TC_BM);
+      tc_pi += mt * q.nsb;
+      tc_pa += mt * q.nch;
+      tc_pe += mt * TC_BM * q.nsb;
+    } else {
+      tc_qi += q.nsb;
+      tc_qa += q.nch;
+      tc_qe += (int64_t)TC_BM * q.nsb;
+    }
+  }
+  for (size_t e = 0; e < nttc.size(); e++) {
+    const TcDescPlan& q = dp[nttc[e].x];
+    ep[e] = TcEntryPlan{tc_bblk, tc_be, tc_pib};
+    tc_bblk += q.nch;
+    tc_be += (int64_t)TC_BN * q.nsb;
+    tc_pib += q.nsb;
+  }
+  tc_dplan_h = std::move(dp);
+  tc_eplan_h = std::move(ep);
+  tc_dplan.release();
+  tc_eplan.release();
 }
 
 void GemmBatch::run(const GemmBases& b, cudaStream_t s) const {
@@ -252,8 +284,10 @@ void GemmBatch::run(const GemmBases& b, cudaStream_t s) const {
   dim3 grid(ntilesN, cdiv(M, BM));
   RSF_CHECK(grid.y <= 65535, RSF_EINVAL, "gemm: M too large");
   int tok = prof_begin(s);
-  const bool tensor = b.df == 1 && M >= TC_MIN_M;
-  if (tensor)
+  const bool tensor = (b.df == 1 || b.df == 3) && M >= TC_MIN_M;
+  if (tensor && b.df == 1)
+    tc_gemm_pre_run(*this, b, M, s);
+  else if (tensor)
     tc_gemm_run(*this, b, M, s);
   else if (b.df)
     LAUNCH(gemm_kernel<true>, grid, GT, 0, s, desc.as<GemmDesc>(), prefix.as<int>(), nprob, b);

@@ -33,8 +33,13 @@ struct GemmDesc {
                    // of a row-major multi-RHS block
 };
 
-// Output-tile width (columns) of the tensor-core GEMM kernel.
+// Output-tile shape (rows, columns) of the tensor-core GEMM kernels, the K
+// chunk of one stage and the superblock of K terms summed in the tensor
+// memory between two epilogues of the pre-sliced engine.
+constexpr int TC_BM = 128;
 constexpr int TC_BN = 64;
+constexpr int TC_KC = 16;
+constexpr int TC_SBK = 384;
 
 // Index of the problem owning tile `tile` given the per-problem tile prefix.
 __device__ __forceinline__ int find_prob(const int* prefix, int nprob, int tile) {
@@ -53,14 +58,39 @@ struct GemmBases {
   int ld;      // used where desc.lda/ldc < 0
   double alpha_scale;  // multiplies every desc.alpha
   int df;              // nonzero: operands and result are df64 pairs (df64.cuh),
-                       // multiplied on the tensor cores (1, tcgemm.cu) or in
-                       // df64 arithmetic on the CUDA cores (2)
+                       // multiplied on the tensor cores (1: pre-sliced operands
+                       // in work buffers; 3: sliced inside the GEMM kernel, no
+                       // work buffers; tcgemm.cu) or in df64 arithmetic on the
+                       // CUDA cores (2)
   const int* kidx;     // K index list of descriptors with gatherK
+};
+
+// Plan of the pre-sliced tensor-core engine (tcgemm.cu) for one descriptor:
+// its K in 16-term chunks (nch) and 384-term superblocks (nsb), and the
+// offsets before it of its slicing work items (pi + qi * mtL), A slice
+// blocks (pa + qa * mtL) and A exponents (pe + qe * mtL), where mtL is the
+// launch's number of 128-row tiles (the q parts count descriptors whose M
+// is the launch's).
+struct TcDescPlan {
+  int nch, nsb;
+  int64_t pi, qi, pa, qa, pe, qe;
+};
+// The same for one (descriptor, 64-column tile) entry: offsets of its B
+// slice blocks, B exponents and slicing work items.
+struct TcEntryPlan {
+  int64_t bblk, be, pib;
 };
 
 // Device-resident batch of GEMM problems with its tile prefix.
 struct GemmBatch {
   DBuf desc, prefix, ntile_tc;
+  // TcDescPlan per descriptor, TcEntryPlan per ntile_tc entry: built with the
+  // batch, uploaded at the first launch on the pre-sliced engine
+  mutable DBuf tc_dplan, tc_eplan;
+  mutable std::vector<TcDescPlan> tc_dplan_h;
+  mutable std::vector<TcEntryPlan> tc_eplan_h;
+  // totals of the plans (fixed part, launch-M part per M-tile)
+  int64_t tc_pi = 0, tc_qi = 0, tc_pa = 0, tc_qa = 0, tc_pe = 0, tc_qe = 0, tc_bblk = 0, tc_be = 0, tc_pib = 0;
   int nprob = 0;
   int ntilesN = 0;   // sum over problems of ceil(N / BN)
   int ntilesN_tc = 0; // the same for the TC_BN-column tiles of the tensor-core
@@ -77,6 +107,9 @@ struct GemmBatch {
 // the launch's largest M; tc_status_take returns and clears the engine's
 // device status (RSF_ETIMEOUT when a bounded wait gave up).
 void tc_gemm_run(const GemmBatch& g, const GemmBases& b, int M, cudaStream_t s);
+// Pre-sliced tensor-core engine (tcgemm.cu): slices every operand once into
+// stream-ordered work buffers, then multiplies; the default for df64 batches.
+void tc_gemm_pre_run(const GemmBatch& g, const GemmBases& b, int M, cudaStream_t s);
 int tc_status_take();
 void gemm_selftest(int engine, int m, int n, int k, int ta, int tb, double alpha, const double* A, int lda,
                    const double* B, int ldb, double beta, double* C, int ldc, cudaStream_t s);

@@ -58,7 +58,7 @@ void level_gemm(const GemmBatch& g, double* X, double* pool, int q, double alpha
   b.p[0] = X; b.p[1] = nullptr; b.p[2] = pool; b.p[3] = nullptr;
   b.sc[0] = q; b.sc[1] = q; b.sc[2] = 1; b.sc[3] = 1;
   b.M = q; b.ld = q; b.alpha_scale = alpha;
-  b.df = df;
+  b.df = df == 1 ? 3 : df;   // the tensor-core engine without work buffers
   g.run(b, s);
 }
 }  // namespace
@@ -144,7 +144,7 @@ void solve_noalloc(rsf_handle_s* h, double* B, int64_t ldb, int nrhs, int op) {
       b.p[0] = from_tmp ? tmp : x; b.p[1] = from_tmp ? x : tmp; b.p[2] = F; b.p[3] = nullptr;
       b.sc[0] = q; b.sc[1] = q; b.sc[2] = 1; b.sc[3] = 1;
       b.M = q; b.ld = q; b.alpha_scale = 1.0;
-      b.df = df;
+      b.df = df == 1 ? 3 : df;
       Lv.gMid[v].run(b, s);
     };
     auto copy_to_tmp = [&]() {

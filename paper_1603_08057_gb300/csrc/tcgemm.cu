@@ -527,6 +527,400 @@ __global__ void __launch_bounds__(tc::NTHREADS, 1)
   }
 }
 
+// ================================================= pre-sliced engine
+// The same products with the slicing taken out of the GEMM: a slicing kernel
+// cuts every operand element once into its S bf16 slices, already in the
+// shared-memory stage layout (one A block = the S slices of 128 rows x 16
+// terms, 28,672 bytes; one B block = 64 columns x 16 terms, 14,336 bytes),
+// with one exponent per row of op(A) (column of op(B)) and superblock of
+// TC_SBK = 384 terms.  The GEMM kernel then copies whole blocks into its
+// stages with bulk asynchronous copies (one loader thread, completion on the
+// stage's mbarrier) and sums a whole superblock of 24 chunks in the tensor
+// memory before one epilogue: the integer sums of a diagonal stay exact
+// (384 terms of at most 37,765 units stay below 2^24), so the exponents'
+// coarser range only moves where the last slice's grid falls (2^-49 of the
+// row's and column's largest value over the superblock instead of over 64
+// terms).  Every element is sliced once instead of once per output tile
+// that reads it, and the epilogue runs once per 384 terms instead of per 64.
+namespace tc6 {
+constexpr int CPS = TC_SBK / tc::KC;              // chunks per superblock
+constexpr int A_BLK = tc::S * tc::A_SLICE;        // bytes of one A chunk block
+constexpr int B_BLK = tc::S * tc::B_SLICE;
+constexpr int NTHREADS = tc::NPROD + 64;          // + the MMA warp + the loader warp
+constexpr int SLICE_THREADS = 128;
+static_assert(TC_SBK % tc::KC == 0 && TC_SBK % 64 == 0 && TC_SBK <= 444, "superblock of exact sums");
+static_assert(TC_BM == tc::BM && TC_KC == tc::KC, "tile shape");
+}  // namespace tc6
+
+// op(A)[gm, gk] of a descriptor (gm, gk in range) as a df64 pair
+__device__ __forceinline__ float2 tc_load_a(const GemmDesc& d, const GemmBases& b, const double* A, int lda, int gm,
+                                            int gk) {
+  const double* p = d.gatherK ? A + gm + (int64_t)b.kidx[d.kofs + gk] * lda
+                              : (d.ta ? A + gk + (int64_t)gm * lda : A + gm + (int64_t)gk * lda);
+  return *reinterpret_cast<const float2*>(p);
+}
+// op(B)[gk, gn] (in range and not masked)
+__device__ __forceinline__ float2 tc_load_b(const GemmDesc& d, const GemmBases& b, const double* Bm, int ldb, int gk,
+                                            int gn) {
+  const double* p = d.gatherK  ? Bm + (b.kidx[d.kofs + gk] - d.kb0) + (int64_t)gn * ldb
+                    : d.gatherN ? Bm + (b.kidx[d.nofs + gn] - d.nb0) + (int64_t)gk * ldb
+                    : d.tb      ? Bm + gn + (int64_t)gk * ldb
+                                : Bm + gk + (int64_t)gn * ldb;
+  return *reinterpret_cast<const float2*>(p);
+}
+
+// One work item per block: (descriptor, 128-row tile, superblock) of op(A)
+// with one thread per row, or ((descriptor, 64-column tile) entry,
+// superblock) of op(B) with one thread per column.  Pass 1 finds the
+// exponent, pass 2 writes the slices chunk by chunk (zeros past K, past the
+// rows or columns, and in the masked triangle of op(B)).
+__global__ void __launch_bounds__(tc6::SLICE_THREADS) tc_slice_kernel(
+    const GemmDesc* __restrict__ descs, const TcDescPlan* __restrict__ dplan, int nprob, const int2* __restrict__ ntile,
+    const TcEntryPlan* __restrict__ eplan, int nent, int mtL, int64_t itemsA, int64_t items, GemmBases bases,
+    uint8_t* __restrict__ abuf, int* __restrict__ ea, uint8_t* __restrict__ bbuf, int* __restrict__ eb) {
+  using namespace tc;
+  const int t = threadIdx.x;
+  for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+    if (item < itemsA) {
+      int lo = 0, hi = nprob - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (dplan[mid].pi + dplan[mid].qi * mtL <= item) lo = mid;
+        else hi = mid - 1;
+      }
+      const TcDescPlan q = dplan[lo];
+      const GemmDesc d = descs[lo];
+      const int64_t local = item - (q.pi + q.qi * mtL);
+      const int mt = (int)(local / q.nsb), sb = (int)(local % q.nsb);
+      const int M = d.M >= 0 ? d.M : bases.M, K = d.K;
+      const int lda = d.lda >= 0 ? d.lda : bases.ld;
+      const double* A = base_ptr(bases, d.abase) + d.a * base_scale(bases, d.abase) + d.m0;
+      const int gm = mt * BM + t;
+      const bool ok = gm < M;
+      const int k0 = sb * TC_SBK, k1 = min(K, k0 + TC_SBK);
+      float mx = 0.f;
+      if (ok)
+        for (int k = k0; k < k1; k++) mx = fmaxf(mx, fabsf(tc_load_a(d, bases, A, lda, gm, k).x));
+      const int e = block_exponent(mx);
+      ea[q.pe + q.qe * mtL + (int64_t)gm * q.nsb + sb] = e;
+      const float sc = pow2f(-e);
+      for (int ch = k0 / KC; ch * KC < k1; ch++) {
+        uint8_t* blk = abuf + (q.pa + q.qa * mtL + (int64_t)mt * q.nch + ch) * (int64_t)tc6::A_BLK;
+#pragma unroll
+        for (int g = 0; g < 2; g++) {
+          float hh[8], ll[8];
+#pragma unroll
+          for (int i = 0; i < 8; i++) {
+            const int k = ch * KC + g * 8 + i;
+            const float2 v = (ok && k < k1) ? tc_load_a(d, bases, A, lda, gm, k) : make_float2(0.f, 0.f);
+            hh[i] = v.x * sc;
+            ll[i] = v.y * sc;
+          }
+          slice_store(hh, ll, blk + g * A_LBO + (t >> 3) * 128 + (t & 7) * 16, A_SLICE);
+        }
+      }
+    } else {
+      const int64_t bi = item - itemsA;
+      int lo = 0, hi = nent - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (eplan[mid].pib <= bi) lo = mid;
+        else hi = mid - 1;
+      }
+      if (t >= TC_BN) continue;
+      const TcEntryPlan p = eplan[lo];
+      const int2 en = ntile[lo];
+      const GemmDesc d = descs[en.x];
+      const TcDescPlan q = dplan[en.x];
+      const int sb = (int)(bi - p.pib);
+      const int N = d.N, K = d.K;
+      const int ldb = d.ldb >= 0 ? d.ldb : bases.ld;
+      const double* Bm = base_ptr(bases, d.bbase) + d.b * base_scale(bases, d.bbase);
+      const int gn = en.y + t;
+      const bool ok = gn < N;
+      const bool masktri = d.triB != 0 && !d.gatherK && !d.gatherN;
+      const int k0 = sb * TC_SBK, k1 = min(K, k0 + TC_SBK);
+      auto val = [&](int k) -> float2 {
+        if (!ok || k >= k1 || (masktri && ((d.triB == 1 && k < gn) || (d.triB == 2 && k > gn))))
+          return make_float2(0.f, 0.f);
+        return tc_load_b(d, bases, Bm, ldb, k, gn);
+      };
+      float mx = 0.f;
+      for (int k = k0; k < k1; k++) mx = fmaxf(mx, fabsf(val(k).x));
+      const int e = block_exponent(mx);
+      eb[p.be + (int64_t)t * q.nsb + sb] = e;
+      const float sc = pow2f(-e);
+      for (int ch = k0 / KC; ch * KC < k1; ch++) {
+        uint8_t* blk = bbuf + (p.bblk + ch) * (int64_t)tc6::B_BLK;
+#pragma unroll
+        for (int g = 0; g < 2; g++) {
+          float hh[8], ll[8];
+#pragma unroll
+          for (int i = 0; i < 8; i++) {
+            const float2 v = val(ch * KC + g * 8 + i);
+            hh[i] = v.x * sc;
+            ll[i] = v.y * sc;
+          }
+          slice_store(hh, ll, blk + g * B_LBO + (t >> 3) * 128 + (t & 7) * 16, B_SLICE);
+        }
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// The GEMM on pre-sliced operands.  Warps 0-7 run the epilogues (one per
+// superblock of the tile: TMEM lane r, 32 columns each, as in the engine
+// above), warp 8 lane 0 issues the MMAs, warp 9 lane 0 the bulk copies of
+// the A and B blocks of every chunk into the three stages.
+__global__ void __launch_bounds__(tc6::NTHREADS, 1)
+    tc_gemm_pre_kernel(const GemmDesc* __restrict__ descs, const TcDescPlan* __restrict__ dplan,
+                       const int2* __restrict__ ntile, const TcEntryPlan* __restrict__ eplan, int ntilesN,
+                       int mtiles, int mtL, GemmBases bases, const uint8_t* __restrict__ abuf,
+                       const int* __restrict__ ea, const uint8_t* __restrict__ bbuf, const int* __restrict__ eb) {
+  using namespace tc;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  float2* sC = reinterpret_cast<float2*>(sm + NST * STAGE);   // [BN][BM]: C(row, col) at col * BM + row
+  uint8_t* aux = sm + NST * STAGE + CBUF;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(aux);
+  // bars: full[NST], empty[NST], accf, acce, drain
+  uint32_t* sTmem = reinterpret_cast<uint32_t*>(bars + 2 * NST + 3);
+  volatile int* sAbort = reinterpret_cast<volatile int*>(sTmem + 1);
+  const uint32_t bFull = su32(bars), bEmpty = su32(bars + NST), bAccF = su32(bars + 2 * NST),
+                 bAccE = su32(bars + 2 * NST + 1), bDrain = su32(bars + 2 * NST + 2);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool producer = warp < PW;
+  const bool mma_thread = warp == PW && lane == 0;
+  const bool load_thread = warp == PW + 1 && lane == 0;
+  if (tid == 0) {
+    for (int i = 0; i < NST; i++) {
+      mbar_init(bFull + 8 * i, 1);
+      mbar_init(bEmpty + 8 * i, 1);
+    }
+    mbar_init(bAccF, 1);
+    mbar_init(bAccE, NPROD);
+    mbar_init(bDrain, 1);
+    *sAbort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == PW) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(sTmem)),
+                 "n"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *sTmem;
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                         ((uint32_t)(BM >> 4) << 24);
+  const int r = tid & (BM - 1), kh = (tid >> 7) & 1;
+  const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+
+  uint32_t chunk_ctr = 0, blk_ctr = 0;
+  bool issued = false;          // the MMA thread issued MMAs (drained on abort)
+  int last_use[NST];            // the loader's last use of every stage (-1: none)
+#pragma unroll
+  for (int i = 0; i < NST; i++) last_use[i] = -1;
+  const int ntiles = ntilesN * mtiles;
+  for (int tile = blockIdx.x; tile < ntiles && !*sAbort; tile += gridDim.x) {
+    const int tn = tile / mtiles, tm = tile - tn * mtiles;
+    const int2 pn = ntile[tn];
+    const GemmDesc d = descs[pn.x];
+    const int M = d.M >= 0 ? d.M : bases.M;
+    const int N = d.N, K = d.K;
+    const int n0 = pn.y;
+    const int m0 = tm * BM;
+    if (m0 >= M || n0 >= N) continue;
+    if (d.lowC && n0 > m0 + BM - 1) continue;
+    const TcDescPlan q = dplan[pn.x];
+    const TcEntryPlan pe = eplan[tn];
+    const int ldc = d.ldc >= 0 ? d.ldc : bases.ld;
+    double* __restrict__ C = base_ptr(bases, d.cbase) + d.c * base_scale(bases, d.cbase) + d.m0;
+    int k0 = 0, k1 = K;
+    if (d.triB == 1) k0 = min(n0, K);
+    if (d.triB == 2) k1 = min(K, n0 + BN);
+    const int ch0 = k0 / KC, ch1 = k1 > k0 ? (k1 + KC - 1) / KC : ch0;
+    const int sb0 = ch0 / tc6::CPS, nunits = ch1 > ch0 ? (ch1 - 1) / tc6::CPS - sb0 + 1 : 0;
+    const int nvalid = min(BN, N - n0);
+    const double alpha = d.alpha * bases.alpha_scale, beta = d.beta;
+    const int gm = m0 + r;
+    const bool rowok = gm < M;
+    const int64_t ablk0 = q.pa + q.qa * mtL + (int64_t)tm * q.nch;
+
+    for (int u = 0; u < nunits && !*sAbort; u++, blk_ctr++) {
+      const int sb = sb0 + u;
+      const int cA = max(ch0, sb * tc6::CPS), cB = min(ch1, (sb + 1) * tc6::CPS), nch = cB - cA;
+      if (load_thread) {
+        // ---- bulk copies of the unit's chunks into the stages
+        for (int c = 0; c < nch; c++) {
+          const uint32_t cc = chunk_ctr + c;
+          const int stage = cc % NST;
+          const uint32_t use = cc / NST;
+          if (use > 0 && !mbar_wait(bEmpty + 8 * stage, (use - 1) & 1, sAbort)) {
+            *sAbort = 1;
+            break;
+          }
+          const uint32_t full = bFull + 8 * stage;
+          const uint32_t dA = su32(sm + stage * STAGE);
+          mbar_expect_tx(full, (uint32_t)(tc6::A_BLK + tc6::B_BLK));
+          bulk_g2s(dA, abuf + (ablk0 + cA + c) * (int64_t)tc6::A_BLK, tc6::A_BLK, full);
+          bulk_g2s(dA + tc6::A_BLK, bbuf + (pe.bblk + cA + c) * (int64_t)tc6::B_BLK, tc6::B_BLK, full);
+          last_use[stage] = (int)use;
+        }
+      } else if (mma_thread) {
+        // ---- MMAs of the unit: all slice products with s + t < S, summed
+        // over its chunks in the S diagonal accumulators
+        if (blk_ctr > 0 && !mbar_wait(bAccE, (blk_ctr - 1) & 1, sAbort)) {
+          *sAbort = 1;
+          break;
+        }
+        tc_fence_after();
+        uint32_t inited = 0;
+        for (int c = 0; c < nch; c++) {
+          const uint32_t cc = chunk_ctr + c;
+          const int stage = cc % NST;
+          if (!mbar_wait(bFull + 8 * stage, (cc / NST) & 1, sAbort)) {
+            *sAbort = 1;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t aBase = su32(sm + stage * STAGE), bBase = aBase + S * A_SLICE;
+#pragma unroll
+          for (int s1 = 0; s1 < S; s1++) {
+            const uint64_t ad = smem_desc(aBase + s1 * A_SLICE, A_LBO, 128);
+#pragma unroll
+            for (int t1 = 0; t1 < S - s1; t1++) {
+              const int dd = s1 + t1;
+              const uint64_t bd = smem_desc(bBase + t1 * B_SLICE, B_LBO, 128);
+              mma_bf16(tmem + dd * BN, ad, bd, idesc, (inited >> dd) & 1u);
+              inited |= 1u << dd;
+            }
+          }
+          issued = true;
+          mma_commit(bEmpty + 8 * stage);
+        }
+        if (*sAbort) break;
+        mma_commit(bAccF);
+      } else if (producer) {
+        // ---- epilogue of the unit: C values by asynchronous copies while
+        // the MMAs run; the first unit writes alpha v + beta C, later units
+        // add alpha v
+        const bool first = u == 0;
+        const bool rd = !first || beta != 0.0;
+        if (rd) {
+#pragma unroll 4
+          for (int j = 0; j < 32; j++) {
+            const int col = kh * 32 + j, gn = n0 + col;
+            const bool ok = rowok && gn < N && !(d.lowC && gm < gn);
+            const int64_t cnn = ok ? (d.gatherN ? (int64_t)bases.kidx[d.nofs + gn] : (int64_t)gn) : 0;
+            const double* src = ok ? C + gm + cnn * ldc : C;
+            const uint32_t dst = su32(sC + col * BM + r);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst), "l"(src), "r"(ok ? 8 : 0)
+                         : "memory");
+          }
+          asm volatile("cp.async.commit_group;\n" ::: "memory");
+        }
+        const int eA = ea[q.pe + q.qe * mtL + (int64_t)gm * q.nsb + sb];
+        if (!mbar_wait(bAccF, blk_ctr & 1, sAbort)) {
+          *sAbort = 1;
+          break;
+        }
+        tc_fence_after();
+        if (rd) asm volatile("cp.async.wait_all;\n" ::: "memory");
+        const float scr = pow2f(eA);
+#pragma unroll
+        for (int q8 = 0; q8 < 4; q8++) {
+          const int col = kh * 32 + q8 * 8;
+          if (col < nvalid) {
+            float D[S][8];
+#pragma unroll
+            for (int dd = 0; dd < S; dd++) tmem_ld8(tl + dd * BN + col, D[dd]);
+            tmem_ld_wait();
+#pragma unroll
+            for (int j2 = 0; j2 < 8; j2++) {
+              const int gn = n0 + col + j2;
+              if (!rowok || gn >= N || (d.lowC && gm < gn)) continue;
+              float hi = D[S - 1][j2], lo = 0.f;
+#pragma unroll
+              for (int dd = S - 2; dd >= 0; dd--) {
+                const float x = D[dd][j2];
+                const float sm2 = __fadd_rn(hi, x);
+                const float v = __fsub_rn(sm2, hi);
+                lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(sm2, v)), __fsub_rn(x, v)));
+                hi = sm2;
+              }
+              const float scn = pow2f(eb[pe.be + (int64_t)(col + j2) * q.nsb + sb]);
+              df64 t = df_fast_two_sum(hi, lo);
+              t.hi = (t.hi * scr) * scn;
+              t.lo = (t.lo * scr) * scn;
+              t = df_scale(t, (float)alpha);
+              const float2 oc = sC[(col + j2) * BM + r];
+              df64 o = {oc.x, oc.y};
+              if (first && beta != 1.0) o = df_scale(o, (float)beta);
+              if (rd) t = df_add(t, o);
+              const int64_t cnn = d.gatherN ? (int64_t)bases.kidx[d.nofs + gn] : (int64_t)gn;
+              *reinterpret_cast<float2*>(C + gm + cnn * ldc) = make_float2(t.hi, t.lo);
+            }
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(bAccE);
+      }
+      chunk_ctr += nch;
+    }
+    if (*sAbort) break;
+    if (producer && nunits == 0 && beta != 1.0 && rowok) {
+      // no K terms (empty or masked range): C = beta C
+      for (int j2 = 0; j2 < 32; j2++) {
+        const int gn = n0 + kh * 32 + j2;
+        if (gn >= N || (d.lowC && gm < gn)) continue;
+        const int64_t cnn = d.gatherN ? (int64_t)bases.kidx[d.nofs + gn] : (int64_t)gn;
+        float2* pc2 = reinterpret_cast<float2*>(C + gm + cnn * ldc);
+        df64 o = {0.f, 0.f};
+        if (beta != 0.0) {
+          const float2 v = *pc2;
+          o = df_scale({v.x, v.y}, (float)beta);
+        }
+        *pc2 = make_float2(o.hi, o.lo);
+      }
+    }
+  }
+
+  // ---- teardown: on abort record the timeout, let this CTA's bulk copies
+  // land and drain its MMAs before the tensor memory is freed
+  if (*sAbort && tid == 0) report(&g_tc_status, RSF_ETIMEOUT, -1, blockIdx.x, 0);
+  if (load_thread) {
+    volatile int never = 0;
+    for (int i = 0; i < NST; i++)
+      if (last_use[i] >= 0) mbar_wait(bFull + 8 * i, (uint32_t)last_use[i] & 1u, &never);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == PW) {
+    if (lane == 0 && *sAbort && issued) {
+      mma_commit(bDrain);
+      volatile int never = 0;
+      mbar_wait(bDrain, 0, &never);
+    }
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TMEM_COLS));
+  }
+}
+
 // ------------------------------------------------------------------ host
 static int tc_sm_count() {
   static int cnt[64] = {0};
@@ -536,6 +930,7 @@ static int tc_sm_count() {
   if (!cnt[dev]) {
     RSF_CUDA(cudaDeviceGetAttribute(&cnt[dev], cudaDevAttrMultiProcessorCount, dev));
     RSF_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM));
+    RSF_CUDA(cudaFuncSetAttribute(tc_gemm_pre_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM));
   }
   return cnt[dev];
 }
@@ -549,6 +944,36 @@ void tc_gemm_run(const GemmBatch& g, const GemmBases& b, int M, cudaStream_t s) 
   const int grid = (int)std::min<int64_t>(ntiles, (int64_t)tc_sm_count());
   LAUNCH(tc_gemm_kernel, grid, tc::NTHREADS, tc::SMEM, s, g.desc.as<GemmDesc>(), g.ntile_tc.as<int2>(), g.ntilesN_tc,
          mtiles, b);
+}
+
+void tc_gemm_pre_run(const GemmBatch& g, const GemmBases& b, int M, cudaStream_t s) {
+  const int mtiles = cdiv(M, tc::BM);
+  const int64_t ntiles = (int64_t)g.ntilesN_tc * mtiles;
+  if (ntiles == 0) return;
+  RSF_CHECK(ntiles < (1ll << 31), RSF_EINVAL, "tensor-core gemm: too many tiles");
+  const int sms = tc_sm_count();
+  if (!g.tc_dplan.p && !g.tc_dplan_h.empty()) {
+    upload(g.tc_dplan, g.tc_dplan_h, s);
+    upload(g.tc_eplan, g.tc_eplan_h, s);
+  }
+  const int mtL = g.anyLaunchM ? cdiv(std::max(b.M, 0), tc::BM) : 0;
+  const int64_t itemsA = g.tc_pi + g.tc_qi * mtL, items = itemsA + g.tc_pib;
+  const int64_t ablk = g.tc_pa + g.tc_qa * mtL, nea = g.tc_pe + g.tc_qe * mtL;
+  if (items == 0) return;
+  // the slices and exponents of this launch (stream-ordered work buffers)
+  DBuf abuf, bbuf, eab, ebb;
+  abuf.alloc((size_t)std::max<int64_t>(1, ablk) * tc6::A_BLK, s);
+  bbuf.alloc((size_t)std::max<int64_t>(1, g.tc_bblk) * tc6::B_BLK, s);
+  eab.alloc(sizeof(int) * std::max<int64_t>(1, nea), s);
+  ebb.alloc(sizeof(int) * std::max<int64_t>(1, g.tc_be), s);
+  const int sgrid = (int)std::min<int64_t>(items, (int64_t)sms * 16);
+  LAUNCH(tc_slice_kernel, sgrid, tc6::SLICE_THREADS, 0, s, g.desc.as<GemmDesc>(), g.tc_dplan.as<TcDescPlan>(),
+         g.nprob, g.ntile_tc.as<int2>(), g.tc_eplan.as<TcEntryPlan>(), g.ntilesN_tc, mtL, itemsA, items, b,
+         abuf.as<uint8_t>(), eab.as<int>(), bbuf.as<uint8_t>(), ebb.as<int>());
+  const int grid = (int)std::min<int64_t>(ntiles, (int64_t)sms);
+  LAUNCH(tc_gemm_pre_kernel, grid, tc6::NTHREADS, tc::SMEM, s, g.desc.as<GemmDesc>(), g.tc_dplan.as<TcDescPlan>(),
+         g.ntile_tc.as<int2>(), g.tc_eplan.as<TcEntryPlan>(), g.ntilesN_tc, mtiles, mtL, b, abuf.as<uint8_t>(),
+         eab.as<int>(), bbuf.as<uint8_t>(), ebb.as<int>());
 }
 
 // One column-major GEMM through a batch engine, for the self-check entry
