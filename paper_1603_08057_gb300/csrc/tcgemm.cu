@@ -227,11 +227,12 @@ __global__ void __launch_bounds__(tc::NTHREADS, 1)
   float* sPartA = reinterpret_cast<float*>(sExpB + 2 * BN); // [NPROD]
   float* sPartB = sPartA + NPROD;                           // [NPROD]
   uint64_t* bars = reinterpret_cast<uint64_t*>(sPartB + NPROD);
-  // bars: full[NST], empty[NST], accf, acce, drain
-  uint32_t* sTmem = reinterpret_cast<uint32_t*>(bars + 2 * NST + 3);
+  // bars: full[NST], empty[NST], accf, acce, drain, prod
+  uint32_t* sTmem = reinterpret_cast<uint32_t*>(bars + 2 * NST + 4);
   volatile int* sAbort = reinterpret_cast<volatile int*>(sTmem + 1);
   const uint32_t bFull = su32(bars), bEmpty = su32(bars + NST), bAccF = su32(bars + 2 * NST),
-                 bAccE = su32(bars + 2 * NST + 1), bDrain = su32(bars + 2 * NST + 2);
+                 bAccE = su32(bars + 2 * NST + 1), bDrain = su32(bars + 2 * NST + 2),
+                 bProd = su32(bars + 2 * NST + 3);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool producer = warp < PW;
@@ -243,6 +244,7 @@ __global__ void __launch_bounds__(tc::NTHREADS, 1)
     mbar_init(bAccF, 1);
     mbar_init(bAccE, NPROD);
     mbar_init(bDrain, 1);
+    mbar_init(bProd, NPROD);
     *sAbort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -341,7 +343,13 @@ __global__ void __launch_bounds__(tc::NTHREADS, 1)
         for (int i = 0; i < 16; i++) mb = fmaxf(mb, fabsf(bv[i].x));
         sPartA[tid] = ma;
         sPartB[tid] = mb;
-        asm volatile("bar.sync 1, %0;" ::"n"(NPROD) : "memory");
+        // every producer's partial maxima (a bounded wait: a barrier that
+        // another producer's abort could leave forever short is not used)
+        mbar_arrive(bProd);
+        if (!mbar_wait(bProd, blk_ctr & 1, sAbort)) {
+          *sAbort = 1;
+          break;
+        }
         const int eA = block_exponent(fmaxf(sPartA[r], sPartA[r + BM]));
         const int eB = block_exponent(fmaxf(fmaxf(sPartB[cb], sPartB[cb + BN]),
                                             fmaxf(sPartB[cb + 2 * BN], sPartB[cb + 3 * BN])));
@@ -599,8 +607,17 @@ __global__ void __launch_bounds__(tc6::SLICE_THREADS) tc_slice_kernel(
       const bool ok = gm < M;
       const int k0 = sb * TC_SBK, k1 = min(K, k0 + TC_SBK);
       float mx = 0.f;
-      if (ok)
-        for (int k = k0; k < k1; k++) mx = fmaxf(mx, fabsf(tc_load_a(d, bases, A, lda, gm, k).x));
+      if (ok) {
+        int k = k0;
+        for (; k + 8 <= k1; k += 8) {
+          float v[8];
+#pragma unroll
+          for (int i = 0; i < 8; i++) v[i] = fabsf(tc_load_a(d, bases, A, lda, gm, k + i).x);
+#pragma unroll
+          for (int i = 0; i < 8; i++) mx = fmaxf(mx, v[i]);
+        }
+        for (; k < k1; k++) mx = fmaxf(mx, fabsf(tc_load_a(d, bases, A, lda, gm, k).x));
+      }
       const int e = block_exponent(mx);
       ea[q.pe + q.qe * mtL + (int64_t)gm * q.nsb + sb] = e;
       const float sc = pow2f(-e);
@@ -620,6 +637,9 @@ __global__ void __launch_bounds__(tc6::SLICE_THREADS) tc_slice_kernel(
         }
       }
     } else {
+      // op(B): column c = t mod 64; the two thread halves take the first and
+      // second half of the superblock's chunks and share the exponent
+      __shared__ float s_mx[tc6::SLICE_THREADS];
       const int64_t bi = item - itemsA;
       int lo = 0, hi = nent - 1;
       while (lo < hi) {
@@ -627,7 +647,6 @@ __global__ void __launch_bounds__(tc6::SLICE_THREADS) tc_slice_kernel(
         if (eplan[mid].pib <= bi) lo = mid;
         else hi = mid - 1;
       }
-      if (t >= TC_BN) continue;
       const TcEntryPlan p = eplan[lo];
       const int2 en = ntile[lo];
       const GemmDesc d = descs[en.x];
@@ -636,21 +655,33 @@ __global__ void __launch_bounds__(tc6::SLICE_THREADS) tc_slice_kernel(
       const int N = d.N, K = d.K;
       const int ldb = d.ldb >= 0 ? d.ldb : bases.ld;
       const double* Bm = base_ptr(bases, d.bbase) + d.b * base_scale(bases, d.bbase);
-      const int gn = en.y + t;
+      const int c = t & (TC_BN - 1), half = t / TC_BN;
+      const int gn = en.y + c;
       const bool ok = gn < N;
       const bool masktri = d.triB != 0 && !d.gatherK && !d.gatherN;
       const int k0 = sb * TC_SBK, k1 = min(K, k0 + TC_SBK);
+      const int nchs = (k1 - k0 + KC - 1) / KC, hch = (nchs + 1) / 2;
+      const int c0 = k0 / KC + (half ? hch : 0), c1 = k0 / KC + (half ? nchs : hch);
       auto val = [&](int k) -> float2 {
         if (!ok || k >= k1 || (masktri && ((d.triB == 1 && k < gn) || (d.triB == 2 && k > gn))))
           return make_float2(0.f, 0.f);
         return tc_load_b(d, bases, Bm, ldb, k, gn);
       };
       float mx = 0.f;
-      for (int k = k0; k < k1; k++) mx = fmaxf(mx, fabsf(val(k).x));
-      const int e = block_exponent(mx);
-      eb[p.be + (int64_t)t * q.nsb + sb] = e;
+      for (int ch = c0; ch < c1; ch++) {
+        float v[16];
+#pragma unroll
+        for (int i = 0; i < 16; i++) v[i] = fabsf(val(ch * KC + i).x);
+#pragma unroll
+        for (int i = 0; i < 16; i++) mx = fmaxf(mx, v[i]);
+      }
+      s_mx[t] = mx;
+      __syncthreads();
+      const int e = block_exponent(fmaxf(s_mx[c], s_mx[c + TC_BN]));
+      __syncthreads();   // s_mx is rewritten by the block's next item
+      if (half == 0) eb[p.be + (int64_t)c * q.nsb + sb] = e;
       const float sc = pow2f(-e);
-      for (int ch = k0 / KC; ch * KC < k1; ch++) {
+      for (int ch = c0; ch < c1; ch++) {
         uint8_t* blk = bbuf + (p.bblk + ch) * (int64_t)tc6::B_BLK;
 #pragma unroll
         for (int g = 0; g < 2; g++) {
@@ -661,7 +692,7 @@ __global__ void __launch_bounds__(tc6::SLICE_THREADS) tc_slice_kernel(
             hh[i] = v.x * sc;
             ll[i] = v.y * sc;
           }
-          slice_store(hh, ll, blk + g * B_LBO + (t >> 3) * 128 + (t & 7) * 16, B_SLICE);
+          slice_store(hh, ll, blk + g * B_LBO + (c >> 3) * 128 + (c & 7) * 16, B_SLICE);
         }
       }
     }
@@ -694,11 +725,13 @@ __global__ void __launch_bounds__(tc6::NTHREADS, 1)
   float2* sC = reinterpret_cast<float2*>(sm + NST * STAGE);   // [BN][BM]: C(row, col) at col * BM + row
   uint8_t* aux = sm + NST * STAGE + CBUF;
   uint64_t* bars = reinterpret_cast<uint64_t*>(aux);
-  // bars: full[NST], empty[NST], accf, acce, drain
-  uint32_t* sTmem = reinterpret_cast<uint32_t*>(bars + 2 * NST + 3);
+  // bars: full[NST], empty[NST], accf, acce, drain, prod
+  uint32_t* sTmem = reinterpret_cast<uint32_t*>(bars + 2 * NST + 4);
   volatile int* sAbort = reinterpret_cast<volatile int*>(sTmem + 1);
+  int* sExpB = reinterpret_cast<int*>(aux + 256);            // [2][BN] by unit parity
   const uint32_t bFull = su32(bars), bEmpty = su32(bars + NST), bAccF = su32(bars + 2 * NST),
-                 bAccE = su32(bars + 2 * NST + 1), bDrain = su32(bars + 2 * NST + 2);
+                 bAccE = su32(bars + 2 * NST + 1), bDrain = su32(bars + 2 * NST + 2),
+                 bProd = su32(bars + 2 * NST + 3);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool producer = warp < PW;
@@ -712,6 +745,7 @@ __global__ void __launch_bounds__(tc6::NTHREADS, 1)
     mbar_init(bAccF, 1);
     mbar_init(bAccE, NPROD);
     mbar_init(bDrain, 1);
+    mbar_init(bProd, NPROD);
     *sAbort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -820,6 +854,16 @@ __global__ void __launch_bounds__(tc6::NTHREADS, 1)
         // add alpha v
         const bool first = u == 0;
         const bool rd = !first || beta != 0.0;
+        // the unit's column exponents, staged once (double-buffered by unit
+        // parity; a producer writes unit u + 2's copy only after every
+        // producer has arrived for unit u + 1, i.e. finished unit u)
+        const int eb2 = (int)(blk_ctr & 1);
+        if (tid < BN) sExpB[eb2 * BN + tid] = eb[pe.be + (int64_t)tid * q.nsb + sb];
+        mbar_arrive(bProd);
+        if (!mbar_wait(bProd, blk_ctr & 1, sAbort)) {
+          *sAbort = 1;
+          break;
+        }
         if (rd) {
 #pragma unroll 4
           for (int j = 0; j < 32; j++) {
@@ -862,7 +906,7 @@ __global__ void __launch_bounds__(tc6::NTHREADS, 1)
                 lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(sm2, v)), __fsub_rn(x, v)));
                 hi = sm2;
               }
-              const float scn = pow2f(eb[pe.be + (int64_t)(col + j2) * q.nsb + sb]);
+              const float scn = pow2f(sExpB[eb2 * BN + col + j2]);
               df64 t = df_fast_two_sum(hi, lo);
               t.hi = (t.hi * scr) * scn;
               t.lo = (t.lo * scr) * scn;
