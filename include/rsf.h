@@ -196,9 +196,8 @@ rsf_status rsf_selftest_wait_limit(void* stream);
  * fp32 accumulation over superblocks of 384 terms; batches with fewer than
  * 64 rows fall back to engine 2), 2 df64 arithmetic on the CUDA cores, 3 the
  * tensor-core engine that slices inside the GEMM kernel (K-blocks of 64
- * terms, no work buffers; the allocation-free solve uses it), 4 engine 1 with
- * the six slices per operand that the peeling's products use.
- * Operands are copied and, for engines 1 to 4, rounded to df64 pairs first,
+ * terms, no work buffers; the allocation-free solve uses it).
+ * Operands are copied and, for engines 1 to 3, rounded to df64 pairs first,
  * so the result carries that rounding (~2^-48 relative per operand).
  * Synchronises the stream. */
 rsf_status rsf_selftest_gemm(int engine, int m, int n, int k, int ta, int tb, double alpha,

@@ -216,8 +216,7 @@ def selftest_gemm(engine: int, A: torch.Tensor, B: torch.Tensor, C: torch.Tensor
                   ta=False, tb=False, alpha=1.0, beta=0.0) -> torch.Tensor:
     """rsf_selftest_gemm: alpha op(A) op(B) + beta C with batched-GEMM engine
     `engine` (0 fp64, 1 tensor cores on pre-sliced df64 operands, 2 df64 CUDA
-    cores, 3 tensor cores slicing inside the kernel, 4 engine 1 with six
-    slices per operand) for
+    cores, 3 tensor cores slicing inside the kernel) for
     float64 CUDA matrices in torch's row-major layout.  A row-major matrix is
     the column-major transpose, so the library computes the column-major
     C^T = op(B)^T op(A)^T, whose memory is the row-major C."""

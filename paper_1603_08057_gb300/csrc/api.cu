@@ -392,7 +392,7 @@ rsf_status rsf_selftest_wait_limit(void* stream) {
 rsf_status rsf_selftest_gemm(int engine, int m, int n, int k, int ta, int tb, double alpha, const double* A,
                              int lda, const double* B, int ldb, double beta, double* C, int ldc, void* stream) {
   API_BEGIN
-  RSF_CHECK(engine >= 0 && engine <= 4, RSF_EINVAL, "engine must be 0 .. 4");
+  RSF_CHECK(engine >= 0 && engine <= 3, RSF_EINVAL, "engine must be 0, 1, 2 or 3");
   RSF_CHECK(m >= 1 && n >= 1 && k >= 0 && A && B && C, RSF_EINVAL, "need m, n >= 1, k >= 0 and non-NULL arrays");
   RSF_CHECK(lda >= (ta ? k : m) && lda >= 1 && ldb >= (tb ? n : k) && ldb >= 1 && ldc >= m, RSF_EINVAL,
             "leading dimensions too small");

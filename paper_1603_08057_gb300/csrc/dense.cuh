@@ -63,12 +63,7 @@ struct GemmBases {
                        // work buffers; tcgemm.cu) or in df64 arithmetic on the
                        // CUDA cores (2)
   const int* kidx;     // K index list of descriptors with gatherK
-  int tc_slices;       // pre-sliced tensor-core engine: bf16 slices per operand
-                       // (7, the default when 0: fp64-class products; 6 for
-                       // the peeling's products, 2^-42 of the largest terms)
 };
-// Slices per operand of the peeling's tensor-core products.
-constexpr int TC_PEEL_SLICES = 6;
 
 // Plan of the pre-sliced tensor-core engine (tcgemm.cu) for one descriptor:
 // its K in 16-term chunks (nch) and 384-term superblocks (nsb), and the

@@ -237,8 +237,6 @@ struct rsf_handle_s {
   int df = 0;                          // solve factors: 0 fp64; df64 pairs multiplied on the
                                        // tensor cores (1) or on the CUDA cores (2)
   cudaStream_t stream = nullptr;
-  int tc_slices = 7;                   // bf16 slices of its tensor-core solve products (the
-                                       // peeling lowers it for the duration of a trace)
   int device = -1;                     // CUDA device current when the handle was built
   std::vector<rsf::LevelData> levels;  // index = tree level (0 = root)
   rsf::DBuf status;                    // DevStatus

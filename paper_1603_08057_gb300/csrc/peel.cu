@@ -293,7 +293,6 @@ void run_gemm(const std::vector<GemmDesc>& d, double* p0, double* p1, double* p2
   b.sc[0] = sc0; b.sc[1] = sc1; b.sc[2] = sc2; b.sc[3] = sc3;
   b.alpha_scale = 1.0;
   b.df = df;
-  b.tc_slices = TC_PEEL_SLICES;
   gb.run(b, s);
 }
 
@@ -314,7 +313,6 @@ void apply_level(const PLevel& P, const double* X, double* Y, int nc, DBuf& tmp,
   b.sc[0] = nc; b.sc[1] = nc; b.sc[2] = 1; b.sc[3] = nc;
   b.M = nc; b.ld = nc; b.alpha_scale = 1.0;
   b.df = df;
-  b.tc_slices = TC_PEEL_SLICES;
   P.gP.run(b, s);
   P.gQ.run(b, s);
   P.gY.run(b, s);
@@ -352,7 +350,6 @@ void apply_level_sparse(const PLevel& P, const double* X, double* Y, int qc, con
     b.sc[0] = b.sc[1] = b.sc[2] = b.sc[3] = 1;
     b.alpha_scale = 1.0;
     b.df = df;
-    b.tc_slices = TC_PEEL_SLICES;
     b.kidx = d_slotlist;
     gb.run(b, s);
   }
@@ -361,7 +358,6 @@ void apply_level_sparse(const PLevel& P, const double* X, double* Y, int qc, con
   b.sc[0] = nc; b.sc[1] = nc; b.sc[2] = 1; b.sc[3] = nc;
   b.M = nc; b.ld = nc; b.alpha_scale = 1.0;
   b.df = df;
-  b.tc_slices = TC_PEEL_SLICES;
   P.gQ.run(b, s);
   // Y(rows of slot s, column block k)^T -= Q_a(block k)^T Ucat_a(rows, :)^T for
   // k != s only: a box's own-slot samples are never used, and rows outside
@@ -468,28 +464,8 @@ static void hutch_traces(rsf_handle_s* F, rsf_handle_s* Fk, bool want0, const rs
   }
 }
 
-// For the duration of a trace: the handles' solve products take the
-// peeling's slice count (its tolerance needs far less than fp64-class
-// products), restored on every exit.
-struct PeelSlices {
-  rsf_handle_s* h[2];
-  int saved[2];
-  PeelSlices(rsf_handle_s* a, rsf_handle_s* b) : h{a, b}, saved{0, 0} {
-    for (int i = 0; i < 2; i++)
-      if (h[i]) {
-        saved[i] = h[i]->tc_slices;
-        h[i]->tc_slices = TC_PEEL_SLICES;
-      }
-  }
-  ~PeelSlices() {
-    for (int i = 1; i >= 0; i--)
-      if (h[i]) h[i]->tc_slices = saved[i];
-  }
-};
-
 void peel_traces(rsf_handle_s* F, rsf_handle_s* Fk, bool want0, double tol, const rsf_opts& o,
                  double* const d_out[2], int64_t d_stride, double* h_sets) {
-  PeelSlices slices_guard(F, Fk == F ? nullptr : Fk);
   if (o.trace_form == RSF_TRACE_HUTCH) {
     hutch_traces(F, Fk, want0, o, d_out, d_stride, h_sets);
     return;

@@ -89,10 +89,9 @@ __global__ void copy_ranges_kernel(const int64_t* __restrict__ rr, int nrr, int 
 }
 
 static void run_level_gemm(const GemmBatch& g, double* X, double* tmp, double* pool, int q, double alpha,
-                           cudaStream_t s, int df, int slices) {
+                           cudaStream_t s, int df) {
   GemmBases b{};
   b.df = df;
-  b.tc_slices = slices;
   b.p[0] = X; b.p[1] = tmp; b.p[2] = pool; b.p[3] = nullptr;
   b.sc[0] = q; b.sc[1] = q; b.sc[2] = 1; b.sc[3] = 1;
   b.M = q; b.ld = q; b.alpha_scale = alpha;
@@ -195,8 +194,8 @@ void solve_rows(rsf_handle_s* h, int op, const double* in, double* out, int q, i
         restrict_batch(Lv.hSR_Et, Lv.boxRSE, sp->slot[l], sp->qc, s, r2);
         g1 = &r1; g2 = &r2;
       }
-      run_level_gemm(*g1, Xl(l), tmp.as<double>(), F, q, -1.0, s, df, h->tc_slices);
-      run_level_gemm(*g2, Xl(l), tmp.as<double>(), F, q, -1.0, s, df, h->tc_slices);
+      run_level_gemm(*g1, Xl(l), tmp.as<double>(), F, q, -1.0, s, df);
+      run_level_gemm(*g2, Xl(l), tmp.as<double>(), F, q, -1.0, s, df);
     } else if (up == 2) {
       const GemmBatch* g1 = &Lv.gSR_Tt;
       const GemmBatch* g2 = &Lv.gRS_E;
@@ -205,8 +204,8 @@ void solve_rows(rsf_handle_s* h, int op, const double* in, double* out, int q, i
         restrict_batch(Lv.hRS_E, Lv.boxRSE, sp->slot[l], sp->qc, s, r2);
         g1 = &r1; g2 = &r2;
       }
-      run_level_gemm(*g1, Xl(l), tmp.as<double>(), F, q, 1.0, s, df, h->tc_slices);
-      run_level_gemm(*g2, Xl(l), tmp.as<double>(), F, q, 1.0, s, df, h->tc_slices);
+      run_level_gemm(*g1, Xl(l), tmp.as<double>(), F, q, 1.0, s, df);
+      run_level_gemm(*g2, Xl(l), tmp.as<double>(), F, q, 1.0, s, df);
     }
   }
   // block-diagonal middle factor on the R rows of every level
@@ -227,7 +226,6 @@ void solve_rows(rsf_handle_s* h, int op, const double* in, double* out, int q, i
       b.sc[0] = q; b.sc[1] = q; b.sc[2] = 1; b.sc[3] = 1;
       b.M = q; b.ld = q; b.alpha_scale = 1.0;
       b.df = df;
-      b.tc_slices = h->tc_slices;
       if (sparse) {
         GemmBatch r;
         restrict_batch(Lv.hMid[v], Lv.boxMid[v], sp->slot[l], sp->qc, s, r);
@@ -271,8 +269,8 @@ void solve_rows(rsf_handle_s* h, int op, const double* in, double* out, int q, i
         g1 = &r1; g2 = &r2;
       }
       const double a = down == 1 ? -1.0 : 1.0;
-      run_level_gemm(*g1, Xl(l), tmp.as<double>(), F, q, a, s, df, h->tc_slices);
-      run_level_gemm(*g2, Xl(l), tmp.as<double>(), F, q, a, s, df, h->tc_slices);
+      run_level_gemm(*g1, Xl(l), tmp.as<double>(), F, q, a, s, df);
+      run_level_gemm(*g2, Xl(l), tmp.as<double>(), F, q, a, s, df);
     }
     double* child = (l < L) ? Xl(l + 1) : nullptr;
     LAUNCH(scatter_rows_kernel, cdiv(Lv.nrows, 8), 256, 0, s, Lv.src.as<int>(), Lv.nrows, q, Xl(l), child, out, cvt);

@@ -188,12 +188,11 @@ __device__ __forceinline__ float slice_magic(int j) {
   return 1.5f * pow2f(16 - 7 * j);
 }
 
-// The NS slices of 8 consecutive k of one row: slice j as 8 bf16 (16 bytes,
+// The S slices of 8 consecutive k of one row: slice j as 8 bf16 (16 bytes,
 // one core-matrix row) at dst + j * slice_bytes.
-template <int NS = tc::S>
 __device__ __forceinline__ void slice_store(float (&hh)[8], const float (&ll)[8], uint8_t* dst, int slice_bytes) {
 #pragma unroll
-  for (int j = 0; j < NS; j++) {
+  for (int j = 0; j < tc::S; j++) {
     const float mg = slice_magic(j);
     float s8[8];
 #pragma unroll
@@ -553,9 +552,8 @@ __global__ void __launch_bounds__(tc::NTHREADS, 1)
 // that reads it, and the epilogue runs once per 384 terms instead of per 64.
 namespace tc6 {
 constexpr int CPS = TC_SBK / tc::KC;              // chunks per superblock
-// bytes of one A / B chunk block and of one stage with NS slices
-template <int NS> constexpr int a_blk() { return NS * tc::A_SLICE; }
-template <int NS> constexpr int b_blk() { return NS * tc::B_SLICE; }
+constexpr int A_BLK = tc::S * tc::A_SLICE;        // bytes of one A chunk block
+constexpr int B_BLK = tc::S * tc::B_SLICE;
 constexpr int NTHREADS = tc::NPROD + 64;          // + the MMA warp + the loader warp
 constexpr int SLICE_THREADS = 128;
 static_assert(TC_SBK % tc::KC == 0 && TC_SBK % 64 == 0 && TC_SBK <= 444, "superblock of exact sums");
@@ -584,7 +582,6 @@ __device__ __forceinline__ float2 tc_load_b(const GemmDesc& d, const GemmBases& 
 // superblock) of op(B) with one thread per column.  Pass 1 finds the
 // exponent, pass 2 writes the slices chunk by chunk (zeros past K, past the
 // rows or columns, and in the masked triangle of op(B)).
-template <int NS>
 __global__ void __launch_bounds__(tc6::SLICE_THREADS) tc_slice_kernel(
     const GemmDesc* __restrict__ descs, const TcDescPlan* __restrict__ dplan, int nprob, const int2* __restrict__ ntile,
     const TcEntryPlan* __restrict__ eplan, int nent, int mtL, int64_t itemsA, int64_t items, GemmBases bases,
@@ -625,7 +622,7 @@ __global__ void __launch_bounds__(tc6::SLICE_THREADS) tc_slice_kernel(
       ea[q.pe + q.qe * mtL + (int64_t)gm * q.nsb + sb] = e;
       const float sc = pow2f(-e);
       for (int ch = k0 / KC; ch * KC < k1; ch++) {
-        uint8_t* blk = abuf + (q.pa + q.qa * mtL + (int64_t)mt * q.nch + ch) * (int64_t)tc6::a_blk<NS>();
+        uint8_t* blk = abuf + (q.pa + q.qa * mtL + (int64_t)mt * q.nch + ch) * (int64_t)tc6::A_BLK;
 #pragma unroll
         for (int g = 0; g < 2; g++) {
           float hh[8], ll[8];
@@ -636,7 +633,7 @@ __global__ void __launch_bounds__(tc6::SLICE_THREADS) tc_slice_kernel(
             hh[i] = v.x * sc;
             ll[i] = v.y * sc;
           }
-          slice_store<NS>(hh, ll, blk + g * A_LBO + (t >> 3) * 128 + (t & 7) * 16, A_SLICE);
+          slice_store(hh, ll, blk + g * A_LBO + (t >> 3) * 128 + (t & 7) * 16, A_SLICE);
         }
       }
     } else {
@@ -685,7 +682,7 @@ __global__ void __launch_bounds__(tc6::SLICE_THREADS) tc_slice_kernel(
       if (half == 0) eb[p.be + (int64_t)c * q.nsb + sb] = e;
       const float sc = pow2f(-e);
       for (int ch = c0; ch < c1; ch++) {
-        uint8_t* blk = bbuf + (p.bblk + ch) * (int64_t)tc6::b_blk<NS>();
+        uint8_t* blk = bbuf + (p.bblk + ch) * (int64_t)tc6::B_BLK;
 #pragma unroll
         for (int g = 0; g < 2; g++) {
           float hh[8], ll[8];
@@ -695,7 +692,7 @@ __global__ void __launch_bounds__(tc6::SLICE_THREADS) tc_slice_kernel(
             hh[i] = v.x * sc;
             ll[i] = v.y * sc;
           }
-          slice_store<NS>(hh, ll, blk + g * B_LBO + (c >> 3) * 128 + (c & 7) * 16, B_SLICE);
+          slice_store(hh, ll, blk + g * B_LBO + (c >> 3) * 128 + (c & 7) * 16, B_SLICE);
         }
       }
     }
@@ -717,15 +714,12 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
 // superblock of the tile: TMEM lane r, 32 columns each, as in the engine
 // above), warp 8 lane 0 issues the MMAs, warp 9 lane 0 the bulk copies of
 // the A and B blocks of every chunk into the three stages.
-template <int NS>
 __global__ void __launch_bounds__(tc6::NTHREADS, 1)
     tc_gemm_pre_kernel(const GemmDesc* __restrict__ descs, const TcDescPlan* __restrict__ dplan,
                        const int2* __restrict__ ntile, const TcEntryPlan* __restrict__ eplan, int ntilesN,
                        int mtiles, int mtL, GemmBases bases, const uint8_t* __restrict__ abuf,
                        const int* __restrict__ ea, const uint8_t* __restrict__ bbuf, const int* __restrict__ eb) {
   using namespace tc;
-  constexpr int ABLK = tc6::a_blk<NS>(), BBLK = tc6::b_blk<NS>(), STG = ABLK + BBLK;
-  static_assert(NS * BN <= TMEM_COLS && NST * STG <= NST * STAGE, "slices of the stages and accumulators");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   float2* sC = reinterpret_cast<float2*>(sm + NST * STAGE);   // [BN][BM]: C(row, col) at col * BM + row
@@ -814,10 +808,10 @@ __global__ void __launch_bounds__(tc6::NTHREADS, 1)
             break;
           }
           const uint32_t full = bFull + 8 * stage;
-          const uint32_t dA = su32(sm + stage * STG);
-          mbar_expect_tx(full, (uint32_t)STG);
-          bulk_g2s(dA, abuf + (ablk0 + cA + c) * (int64_t)ABLK, ABLK, full);
-          bulk_g2s(dA + ABLK, bbuf + (pe.bblk + cA + c) * (int64_t)BBLK, BBLK, full);
+          const uint32_t dA = su32(sm + stage * STAGE);
+          mbar_expect_tx(full, (uint32_t)(tc6::A_BLK + tc6::B_BLK));
+          bulk_g2s(dA, abuf + (ablk0 + cA + c) * (int64_t)tc6::A_BLK, tc6::A_BLK, full);
+          bulk_g2s(dA + tc6::A_BLK, bbuf + (pe.bblk + cA + c) * (int64_t)tc6::B_BLK, tc6::B_BLK, full);
           last_use[stage] = (int)use;
         }
       } else if (mma_thread) {
@@ -837,12 +831,12 @@ __global__ void __launch_bounds__(tc6::NTHREADS, 1)
             break;
           }
           tc_fence_after();
-          const uint32_t aBase = su32(sm + stage * STG), bBase = aBase + ABLK;
+          const uint32_t aBase = su32(sm + stage * STAGE), bBase = aBase + S * A_SLICE;
 #pragma unroll
-          for (int s1 = 0; s1 < NS; s1++) {
+          for (int s1 = 0; s1 < S; s1++) {
             const uint64_t ad = smem_desc(aBase + s1 * A_SLICE, A_LBO, 128);
 #pragma unroll
-            for (int t1 = 0; t1 < NS - s1; t1++) {
+            for (int t1 = 0; t1 < S - s1; t1++) {
               const int dd = s1 + t1;
               const uint64_t bd = smem_desc(bBase + t1 * B_SLICE, B_LBO, 128);
               mma_bf16(tmem + dd * BN, ad, bd, idesc, (inited >> dd) & 1u);
@@ -895,17 +889,17 @@ __global__ void __launch_bounds__(tc6::NTHREADS, 1)
         for (int q8 = 0; q8 < 4; q8++) {
           const int col = kh * 32 + q8 * 8;
           if (col < nvalid) {
-            float D[NS][8];
+            float D[S][8];
 #pragma unroll
-            for (int dd = 0; dd < NS; dd++) tmem_ld8(tl + dd * BN + col, D[dd]);
+            for (int dd = 0; dd < S; dd++) tmem_ld8(tl + dd * BN + col, D[dd]);
             tmem_ld_wait();
 #pragma unroll
             for (int j2 = 0; j2 < 8; j2++) {
               const int gn = n0 + col + j2;
               if (!rowok || gn >= N || (d.lowC && gm < gn)) continue;
-              float hi = D[NS - 1][j2], lo = 0.f;
+              float hi = D[S - 1][j2], lo = 0.f;
 #pragma unroll
-              for (int dd = NS - 2; dd >= 0; dd--) {
+              for (int dd = S - 2; dd >= 0; dd--) {
                 const float x = D[dd][j2];
                 const float sm2 = __fadd_rn(hi, x);
                 const float v = __fsub_rn(sm2, hi);
@@ -980,8 +974,7 @@ static int tc_sm_count() {
   if (!cnt[dev]) {
     RSF_CUDA(cudaDeviceGetAttribute(&cnt[dev], cudaDevAttrMultiProcessorCount, dev));
     RSF_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM));
-    RSF_CUDA(cudaFuncSetAttribute(tc_gemm_pre_kernel<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM));
-    RSF_CUDA(cudaFuncSetAttribute(tc_gemm_pre_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM));
+    RSF_CUDA(cudaFuncSetAttribute(tc_gemm_pre_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM));
   }
   return cnt[dev];
 }
@@ -997,8 +990,7 @@ void tc_gemm_run(const GemmBatch& g, const GemmBases& b, int M, cudaStream_t s) 
          mtiles, b);
 }
 
-template <int NS>
-static void tc_gemm_pre_run_ns(const GemmBatch& g, const GemmBases& b, int M, cudaStream_t s) {
+void tc_gemm_pre_run(const GemmBatch& g, const GemmBases& b, int M, cudaStream_t s) {
   const int mtiles = cdiv(M, tc::BM);
   const int64_t ntiles = (int64_t)g.ntilesN_tc * mtiles;
   if (ntiles == 0) return;
@@ -1014,23 +1006,18 @@ static void tc_gemm_pre_run_ns(const GemmBatch& g, const GemmBases& b, int M, cu
   if (items == 0) return;
   // the slices and exponents of this launch (stream-ordered work buffers)
   DBuf abuf, bbuf, eab, ebb;
-  abuf.alloc((size_t)std::max<int64_t>(1, ablk) * tc6::a_blk<NS>(), s);
-  bbuf.alloc((size_t)std::max<int64_t>(1, g.tc_bblk) * tc6::b_blk<NS>(), s);
+  abuf.alloc((size_t)std::max<int64_t>(1, ablk) * tc6::A_BLK, s);
+  bbuf.alloc((size_t)std::max<int64_t>(1, g.tc_bblk) * tc6::B_BLK, s);
   eab.alloc(sizeof(int) * std::max<int64_t>(1, nea), s);
   ebb.alloc(sizeof(int) * std::max<int64_t>(1, g.tc_be), s);
   const int sgrid = (int)std::min<int64_t>(items, (int64_t)sms * 16);
-  LAUNCH(tc_slice_kernel<NS>, sgrid, tc6::SLICE_THREADS, 0, s, g.desc.as<GemmDesc>(), g.tc_dplan.as<TcDescPlan>(),
+  LAUNCH(tc_slice_kernel, sgrid, tc6::SLICE_THREADS, 0, s, g.desc.as<GemmDesc>(), g.tc_dplan.as<TcDescPlan>(),
          g.nprob, g.ntile_tc.as<int2>(), g.tc_eplan.as<TcEntryPlan>(), g.ntilesN_tc, mtL, itemsA, items, b,
          abuf.as<uint8_t>(), eab.as<int>(), bbuf.as<uint8_t>(), ebb.as<int>());
   const int grid = (int)std::min<int64_t>(ntiles, (int64_t)sms);
-  LAUNCH(tc_gemm_pre_kernel<NS>, grid, tc6::NTHREADS, tc::SMEM, s, g.desc.as<GemmDesc>(), g.tc_dplan.as<TcDescPlan>(),
+  LAUNCH(tc_gemm_pre_kernel, grid, tc6::NTHREADS, tc::SMEM, s, g.desc.as<GemmDesc>(), g.tc_dplan.as<TcDescPlan>(),
          g.ntile_tc.as<int2>(), g.tc_eplan.as<TcEntryPlan>(), g.ntilesN_tc, mtiles, mtL, b, abuf.as<uint8_t>(),
          eab.as<int>(), bbuf.as<uint8_t>(), ebb.as<int>());
-}
-
-void tc_gemm_pre_run(const GemmBatch& g, const GemmBases& b, int M, cudaStream_t s) {
-  if (b.tc_slices == 6) tc_gemm_pre_run_ns<6>(g, b, M, s);
-  else tc_gemm_pre_run_ns<7>(g, b, M, s);
 }
 
 // One column-major GEMM through a batch engine, for the self-check entry
@@ -1063,9 +1050,7 @@ void gemm_selftest(int engine, int m, int n, int k, int ta, int tb, double alpha
   GemmBases b{};
   b.p[0] = a.as<double>(); b.p[1] = bb.as<double>(); b.p[2] = c.as<double>(); b.p[3] = nullptr;
   b.sc[0] = b.sc[1] = b.sc[2] = b.sc[3] = 1;
-  b.M = m; b.ld = ldc; b.alpha_scale = 1.0;
-  b.df = engine == 4 ? 1 : engine;            // 4: the pre-sliced engine with the peeling's slices
-  b.tc_slices = engine == 4 ? TC_PEEL_SLICES : 0;
+  b.M = m; b.ld = ldc; b.alpha_scale = 1.0; b.df = engine;
   g.run(b, s);
   if (engine) convert_df64(c.as<double>(), (int64_t)ldc * n, 0, s);
   RSF_CUDA(cudaMemcpyAsync(C, c.p, sizeof(double) * ldc * n, cudaMemcpyDeviceToDevice, s));

@@ -6,11 +6,7 @@ Engines 1 and 3 multiply df64 operands on the tensor cores from exact bf16
 slices (seven per operand, exact fp32 accumulation per diagonal of slice
 products; engine 1 slices every operand once into work buffers with one
 power of two per row and superblock of 384 terms, engine 3 slices inside the
-GEMM per K-block of 64).  Engine 4 is engine 1 with six slices per operand
-(the peeling's products): the dropped slice products and remainders stay
-below ~2.4e-12 of max|A_ik| max|B_kj| per term, which for these normal
-entries (max / mean absolute value ~14) bounds the error by 3e-11 of
-sum_k |A_ik||B_kj|.  Engines 1 and 3 must match the exact product to the df64
+GEMM per K-block of 64).  Their results must match the exact product to the df64
 rounding of the operands: each operand is rounded to a 48-bit significand
 (relative 2^-48 = 3.6e-15) and the slices keep 7 x 7 bits below the block's
 largest power of two, so |C - AB| <= 1e-13 sum_k |A_ik||B_kj| + the same
@@ -55,7 +51,7 @@ SHAPES = [(128, 64, 32), (200, 70, 45), (129, 33, 1), (300, 130, 1000), (1000, 2
           (513, 64, 385), (40, 100, 50), (20, 150, 64)]
 
 
-@pytest.mark.parametrize("engine", [1, 3, 4, 2, 0])
+@pytest.mark.parametrize("engine", [1, 3, 2, 0])
 @pytest.mark.parametrize("shape", SHAPES)
 def test_engine_matches_numpy(B, engine, shape):
     m, n, k = shape
@@ -71,5 +67,5 @@ def test_engine_matches_numpy(B, engine, shape):
         # fp64: k u (the classical bound); tensor cores: 1e-13 (exact within a
         # K-block, one df64 addition per block); df64 on the CUDA cores: its
         # fp32 error accumulator grows with k (measured up to 1.8e-13)
-        bar = {0: 2.3e-16 * max(k, 2), 1: 1e-13, 2: 5e-13, 3: 1e-13, 4: 3e-11}[engine]
+        bar = {0: 2.3e-16 * max(k, 2), 1: 1e-13, 2: 5e-13, 3: 1e-13}[engine]
         assert err <= bar
