@@ -21,7 +21,7 @@ def test_grid_workloads_are_the_papers():
     for name in ("matern32_grid_aniso_n262144", "rq_half_grid_aniso_n262144"):
         wl = W.WORKLOADS[name]
         assert wl["n"] == 512 * 512 and wl["theta"] == (10.0, 1.0, 1e-4, 7.0)
-        assert wl["tol_fact"] == wl["tol_peel"] / 1000
+        assert wl["tol_fact"] == pytest.approx(wl["tol_peel"] / 1000, rel=1e-12)
     x = W.make_points("grid", 64 * 64, 0)
     assert x.min() > 0.0 and x.max() < 100.0
     assert len(np.unique(x[:, 0])) == 64 and len(np.unique(x[:, 1])) == 64
