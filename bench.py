@@ -286,7 +286,7 @@ def roofline_of(B, prof, ms_prof):
     extra = {}
     if kind == "tc":
         bf16, src = bf16_peak_tflops()
-        kname = "tc_gemm_kernel (batched ragged GEMM on tcgen05, df64 operands as exact bf16 slices)"
+        kname = "tc_slice_kernel + tc_gemm_pre_kernel (batched ragged GEMM on tcgen05, df64 operands pre-sliced into exact bf16 slices)"
         bound, peak = "tensor", bf16 / TC_PRODUCTS
         psrc = (f"dense bf16 tensor peak {bf16:.0f} TFLOP/s from {src}, divided by the {TC_PRODUCTS} bf16 slice "
                 f"multiply-adds ({TC_SLICES} slices per operand, products with s + t < {TC_SLICES}) that make one "
