@@ -62,3 +62,24 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(binding, "_lib", None)
     with pytest.raises(RuntimeError, match="missing"):
         binding.lib()
+
+
+def test_argument_errors_of_the_later_entry_points_need_no_gpu():
+    # NULL or out-of-range arguments are rejected with RSF_EINVAL (1) before
+    # any device work, and rsf_last_error names the problem
+    import ctypes
+    from paper_1603_08057_gb300 import binding
+    L = binding.lib()
+    k = binding.RsfKernel(binding.MATERN32, 0.0, 0)
+    th = (ctypes.c_double * 3)(0.1, 1.0, 0.01)
+    ll = ctypes.c_double()
+    assert L.gp_profile_loglik_and_score(None, None, 10, ctypes.byref(k), th, 1e-9, 1e-6, None, None,
+                                         ctypes.byref(ll), None, None) == 1
+    mean = (ctypes.c_double * 4)()
+    assert L.gp_conditional(None, 10, None, None, 4, ctypes.byref(k), th, 1e-9, None, None, 0, mean, None, 0,
+                            None) == 1
+    n, nb = ctypes.c_int64(), ctypes.c_int()
+    assert L.rsf_tree_export(None, ctypes.byref(n), ctypes.byref(nb), None, None) == 1
+    assert L.rsf_selftest_gemm(9, 1, 1, 1, 0, 0, 1.0, None, 1, None, 1, 0.0, None, 1, None) == 1
+    L.rsf_last_error.restype = ctypes.c_char_p
+    assert b"engine" in L.rsf_last_error()
