@@ -311,7 +311,31 @@ def roofline_of(B, prof, ms_prof):
          "share_of_step": g["ms"] / ms_prof if ms_prof > 0 else None,
          "phases_ms": {B.PROF_NAMES[c]: prof[c]["ms"] for c in prof if prof[c]["launches"] > 0}}
     r.update(extra)
+    r["engines"] = engine_rooflines(B, prof)
     return r
+
+
+def engine_rooflines(B, prof):
+    """Every GEMM engine that ran in the profiled evaluation against its own
+    bound (the tensor-core engine against the bf16 peak / 28, the CUDA-core
+    engines against their derived ALU peaks), and the flop-weighted total of
+    the three: their summed algorithmic flops over their summed time."""
+    bf16, _ = bf16_peak_tflops()
+    rows = []
+    tot_fl = tot_ms = 0.0
+    for cat, name, peak in ((B.PROF_GEMM_TC, "tensor-core GEMM (slicing + products)", bf16 / TC_PRODUCTS),
+                            (B.PROF_GEMM_DF, "df64 CUDA-core GEMM", DF64_PEAK_TFLOPS),
+                            (B.PROF_GEMM, "fp64 GEMM", FP64_PEAK_TFLOPS)):
+        g = prof.get(cat)
+        if not g or g["launches"] <= 0 or g["ms"] <= 0:
+            continue
+        tf = g["flops"] / (g["ms"] / 1e3) / 1e12
+        rows.append({"engine": name, "launches": g["launches"], "ms": g["ms"], "achieved_tflops": tf,
+                     "peak_tflops": peak, "frac": tf / peak})
+        tot_fl += g["flops"]
+        tot_ms += g["ms"]
+    total = {"achieved_tflops": tot_fl / (tot_ms / 1e3) / 1e12, "ms": tot_ms} if tot_ms > 0 else None
+    return {"per_engine": rows, "flop_weighted_total": total}
 
 
 def rel(a, b):
