@@ -77,6 +77,9 @@ def parse():
                         "data drawn at theta (0.05, 1, 1e-2), started from (0.2, 0.5, 0.1)) at --n points "
                         "(default 65,536) for --mle-iters iterations")
     p.add_argument("--mle-iters", type=int, default=30)
+    p.add_argument("--mle-staged", action="store_true",
+                   help="with --mle: tighten the tolerances over three stages (mle.fit_staged) instead of "
+                        "running all iterations at eps_fact 1e-9, eps_peel 1e-6")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-other-form", action="store_true",
@@ -508,13 +511,19 @@ def run_mle(args):
     z = F.solve(torch.tensor(WL.standard_normal(n, 10), dtype=torch.float64, device="cuda"), B.OP_SQRT)
     del F
     torch.cuda.synchronize()
-    th, info = mle.fit(pts, z, B.MATERN1, th0, max_iter=args.mle_iters)
+    if args.mle_staged:
+        th, info = mle.fit_staged(pts, z, B.MATERN1, th0)
+        info["trace"] = [t for st in info["stages"] for t in st["trace"]]
+    else:
+        th, info = mle.fit(pts, z, B.MATERN1, th0, max_iter=args.mle_iters)
     iters = len({tuple(t[0]) for t in info["trace"]})
     line = {"mode": "mle", "workload": f"matern nu=1 mixture n={n}", "n": n, "theta_true": list(th_true),
             "theta0": list(th0), "theta_hat": th, "theta_rel_err": [abs(a - b) / b for a, b in zip(th, th_true)],
             "lbfgs_max_iter": args.mle_iters, "evaluations": info["evals"], "seconds": info["seconds"],
             "s_per_evaluation": info["seconds"] / max(1, info["evals"]), "distinct_thetas": iters,
-            "final_loglik": info["loglik"], "final_score": info["trace"][-1][2] if info["trace"] else None}
+            "final_loglik": info["loglik"], "final_score": info["trace"][-1][2] if info["trace"] else None,
+            "tolerance_stages": ([(st["tol_fact"], st["tol_peel"], st["evals"]) for st in info["stages"]]
+                                 if args.mle_staged else None)}
     print(json.dumps(line), flush=True)
     return 0
 

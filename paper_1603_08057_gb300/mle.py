@@ -84,3 +84,28 @@ def fit_profile(points: torch.Tensor, z: torch.Tensor, family: int, theta0, alph
     info = {"evals": len(trace), "seconds": time.perf_counter() - t0, "loglik": lt,
             "sigma2": float(t[6]) / n, "mu": float(t[8] / t[9]), "trace": trace}
     return theta.tolist(), info
+
+
+# (tol_fact, tol_peel, L-BFGS iterations) per stage: two orders looser, one
+# order looser, then the paper's pairing eps_fact = eps_peel / 1000 (Sec. 5.3).
+DEFAULT_STAGES = ((1e-7, 1e-4, 10), (1e-8, 1e-5, 10), (1e-9, 1e-6, 30))
+
+
+def fit_staged(points: torch.Tensor, z: torch.Tensor, family: int, theta0, stages=DEFAULT_STAGES,
+               alpha: float = 0.0, o: B.RsfOpts | None = None, history_size: int = 10):
+    """Maximum likelihood with the tolerances tightened as the optimization
+    proceeds (the dynamic tolerances the paper suggests in Sec. 6): the
+    L-BFGS of fit runs at each (tol_fact, tol_peel, max_iter) stage in turn,
+    each started from the previous stage's theta, so the early iterations far
+    from the maximizer run on cheaper, looser factorizations and peelings.
+    Returns (theta, info) with info = {"evals", "seconds", "loglik",
+    "stages": [per-stage info of fit, with its tolerances]}; loglik is the
+    last stage's, at its tolerances."""
+    theta = [float(v) for v in theta0]
+    per = []
+    for tol_fact, tol_peel, iters in stages:
+        theta, info = fit(points, z, family, theta, alpha, tol_fact, tol_peel, o, iters, history_size)
+        info = dict(info, tol_fact=tol_fact, tol_peel=tol_peel)
+        per.append(info)
+    return theta, {"evals": sum(i["evals"] for i in per), "seconds": sum(i["seconds"] for i in per),
+                   "loglik": per[-1]["loglik"] if per else None, "stages": per}
