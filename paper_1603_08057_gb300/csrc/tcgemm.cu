@@ -1003,8 +1003,9 @@ void tc_gemm_pre_run(const GemmBatch& g, const GemmBases& b, int M, cudaStream_t
   const int mtL = g.anyLaunchM ? cdiv(std::max(b.M, 0), tc::BM) : 0;
   const int64_t itemsA = g.tc_pi + g.tc_qi * mtL, items = itemsA + g.tc_pib;
   const int64_t ablk = g.tc_pa + g.tc_qa * mtL, nea = g.tc_pe + g.tc_qe * mtL;
-  if (items == 0) return;
-  // the slices and exponents of this launch (stream-ordered work buffers)
+  // the slices and exponents of this launch (stream-ordered work buffers);
+  // when every K is 0 there is nothing to slice, but the GEMM kernel still
+  // runs: its tiles then write C = beta C
   DBuf abuf, bbuf, eab, ebb;
   abuf.alloc((size_t)std::max<int64_t>(1, ablk) * tc6::A_BLK, s);
   bbuf.alloc((size_t)std::max<int64_t>(1, g.tc_bblk) * tc6::B_BLK, s);

@@ -69,3 +69,22 @@ def test_engine_matches_numpy(B, engine, shape):
         # fp32 error accumulator grows with k (measured up to 1.8e-13)
         bar = {0: 2.3e-16 * max(k, 2), 1: 1e-13, 2: 5e-13, 3: 1e-13}[engine]
         assert err <= bar
+
+
+@pytest.mark.parametrize("engine", [1, 3, 2, 0])
+def test_engine_without_k_terms_scales_c(B, engine):
+    # K = 0 through the C ABI: nothing to multiply, C = beta C (df64 engines:
+    # to the rounding of C to a df64 pair)
+    import ctypes
+    m, n = 200, 130
+    rng = np.random.default_rng(7)
+    C0 = rng.standard_normal((n, m))   # row-major n x m = column-major m x n
+    A = torch.zeros(m, dtype=torch.float64, device="cuda")   # lda = m, no columns read
+    Bb = torch.zeros(n, dtype=torch.float64, device="cuda")  # ldb = 1, k = 0 rows per column
+    for beta in (0.0, 0.5, -2.0):
+        C = torch.tensor(C0, dtype=torch.float64, device="cuda")
+        st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        assert B.lib().rsf_selftest_gemm(engine, m, n, 0, 0, 0, 1.0, A.data_ptr(), m, Bb.data_ptr(), 1, beta,
+                                         C.data_ptr(), m, st) == 0
+        got = C.cpu().numpy()
+        assert np.all(np.abs(got - beta * C0) <= 1e-14 * np.abs(C0))
