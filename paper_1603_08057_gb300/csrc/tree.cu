@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(RS_THREADS) radix_scatter_kernel(
     const unsigned long long* __restrict__ kin, const int* __restrict__ vin, int64_t n, int shift, int ntiles,
     const unsigned int* __restrict__ offs, unsigned long long* __restrict__ kout, int* __restrict__ vout) {
   __shared__ unsigned int run[256];              // elements of each digit placed by earlier rounds
-  __shared__ unsigned int wcnt[RS_WARPS][256];   // this round: per warp and digit counts, then offsets
+  __shared__ unsigned int wcnt[RS_WARPS][256];   // this pass of RS_THREADS elements: per warp and digit counts, then offsets
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   run[t] = offs[(int64_t)t * ntiles + blockIdx.x];
   const int64_t base = (int64_t)blockIdx.x * RS_TILE;
